@@ -1,0 +1,296 @@
+"""Pins of the CPU oracle against facts fixed by the paper and by mathematics.
+
+Each test checks the oracle against something other than itself: printed
+values of the paper (tests/golden/), closed forms, textbook eigen-facts,
+brute force on tiny grids, and the inequalities of Section 4.
+"""
+import math
+import os
+
+import numpy as np
+import pytest
+
+import bhcp_inputs as bi
+import oracle as O
+from oracle.qbvm_oracle import solve_original, principal_root
+
+GOLDEN = os.path.join(os.path.dirname(__file__), "golden")
+
+
+def _tiny_grids():
+    return [
+        bi.Grid(1, (8,), 1.0, 0.1, 6),
+        bi.Grid(1, (5,), math.pi, 1.0, 2),          # N = 1: corner meets diagonal
+        bi.Grid(1, (9,), 1.0, 0.3, 17),             # odd N_t
+        bi.Grid(2, (6, 5), 1.0, 0.1, 4),            # unequal M per axis
+        bi.Grid(2, (4, 4), math.pi, 1.0, 8),
+        bi.Grid(3, (4, 3, 5), 1.0, 0.05, 5),
+    ]
+
+
+# ------------------------------------------------------------ spatial operator
+
+@pytest.mark.parametrize("M,L", [(8, 1.0), (13, math.pi), (64, 2.0)])
+def test_laplacian_1d_eigenpairs(M, L):
+    """-Lap_h sin(k pi x/L) = (4/h^2) sin^2(k pi/(2M)) sin(k pi x/L) (textbook)."""
+    A = -O.laplacian_1d(M, L).toarray()
+    ev = np.linalg.eigvalsh(A)
+    np.testing.assert_allclose(np.sort(ev), np.sort(O.dst_eigenvalues(M, L)), rtol=1e-12)
+    x = np.arange(1, M) * L / M
+    for k in (1, M // 2, M - 1):
+        v = np.sin(k * np.pi * x / L)
+        lam = (4 * M * M / L ** 2) * np.sin(k * np.pi / (2 * M)) ** 2
+        np.testing.assert_allclose(A @ v, lam * v, atol=1e-9 * lam)
+
+
+def _stencil_apply(u, h):
+    """Direct 2D/3D finite-difference stencil on a zero-padded array (x last)."""
+    pad = np.pad(u, 1)
+    out = np.zeros_like(u)
+    d = u.ndim
+    core = tuple(slice(1, -1) for _ in range(d))
+    for ax in range(d):
+        hx = h[d - 1 - ax]
+        lo = list(core); lo[ax] = slice(0, -2)
+        hi = list(core); hi[ax] = slice(2, None)
+        out += (pad[tuple(lo)] - 2 * pad[core] + pad[tuple(hi)]) / hx ** 2
+    return out
+
+
+@pytest.mark.parametrize("grid", [g for g in _tiny_grids() if g.dim > 1])
+def test_laplacian_matches_direct_stencil(grid):
+    """Kronecker assembly equals the 5/7-point stencil with x fastest (catches a
+    transposed axis order: the grids have unequal M per axis)."""
+    rng = np.random.default_rng(0)
+    u = rng.standard_normal(grid.shape)
+    Lap = O.laplacian(grid.dim, grid.M, grid.L)
+    np.testing.assert_allclose((Lap @ u.ravel()).reshape(grid.shape), _stencil_apply(u, grid.h), rtol=1e-12, atol=1e-9)
+
+
+@pytest.mark.parametrize("n", [1, 7, 31, 64])
+def test_sine_matrix_orthogonality(n):
+    """DST-I: S^2 = ((n+1)/2) I."""
+    S = O.sine_matrix(n)
+    np.testing.assert_allclose(S @ S, (n + 1) / 2 * np.eye(n), atol=1e-12 * n)
+
+
+# ------------------------------------------------------- omega-circulant part
+
+@pytest.mark.parametrize("nt,omega", [(2, -3.0), (7, -0.25), (16, -1e3), (33, -7.5)])
+def test_c_omega_eigenvalues(nt, omega):
+    """C_omega = V D V^{-1} with d_j = 1 - omega^{1/N_t} theta^j (Section 3.3)."""
+    ev = np.linalg.eigvals(O.c_omega(nt, omega))
+    gam = principal_root(omega, nt)
+    d = 1 - gam * np.exp(2j * np.pi * np.arange(nt) / nt)
+    for v in d:
+        assert np.min(np.abs(ev - v)) < 1e-9 * max(1.0, abs(v))
+
+
+def test_pq_with_alpha_equals_pm_with_tau_alpha():
+    """Section 4: the PinT-QBVM system with alpha equals the PinT-MQBVM system
+    with tau*alpha (same matrix, same right-hand side)."""
+    grid = bi.Grid(2, (6, 6), 1.0, 0.2, 7)
+    a = 3e-3
+    A = O.assemble_pint(grid, O.PQ, a)
+    B = O.assemble_pint(grid, O.PM, grid.tau * a)
+    assert abs(A - B).max() == 0.0
+    g = np.random.default_rng(1).standard_normal(grid.shape)
+    np.testing.assert_array_equal(O.delta_rhs(grid, O.PQ, a, g), O.delta_rhs(grid, O.PM, grid.tau * a, g))
+
+
+# ------------------------------------------------------ closed-form solutions
+
+def _mode_closed_form(grid, form, alpha, kvec, c):
+    """Discrete analogue of eqs. (4.5)/(4.6): for g = c * phi_k the solution is
+    y^n = r^n c / (alpha(1 + tau lam) + r^N) (PQ) resp.
+    r^n c / (alpha(lam + 1/tau) + r^N) (PM), r = 1/(1 + tau lam)."""
+    lam = sum((4 / grid.h[d] ** 2) * math.sin(kvec[d] * math.pi / (2 * grid.M[d])) ** 2 for d in range(grid.dim))
+    tau, N = grid.tau, grid.nt - 1
+    r = 1 / (1 + tau * lam)
+    den = alpha * (1 + tau * lam) + r ** N if form == O.PQ else alpha * (lam + 1 / tau) + r ** N
+    phi = bi.sine_field(grid, [kvec], [1.0])
+    return np.stack([r ** n * c / den * phi for n in range(grid.nt)])
+
+
+@pytest.mark.parametrize("grid", _tiny_grids())
+@pytest.mark.parametrize("form", [O.PQ, O.PM])
+def test_eigenfunction_data_closed_form(grid, form):
+    """g = c sin(k.pi x/L): every oracle reproduces the per-mode closed form."""
+    kvec = tuple(max(1, (m - 1) // 2) for m in grid.M)
+    alpha = 2e-3
+    c = 0.7
+    g = c * bi.sine_field(grid, [kvec], [1.0])
+    F = O.delta_rhs(grid, form, alpha, g)
+    want = _mode_closed_form(grid, form, alpha, kvec, c)
+    scale = np.abs(want).max()
+    for solver in (O.solve_sparse_lu, O.solve_dense, O.solve_pint_three_step, O.solve_spectral):
+        got = solver(grid, form, alpha, F)
+        np.testing.assert_allclose(got, want, atol=1e-10 * scale, err_msg=solver.__name__)
+
+
+@pytest.mark.parametrize("grid", _tiny_grids())
+@pytest.mark.parametrize("form", [O.PQ, O.PM])
+def test_solvers_agree_on_general_rhs(grid, form):
+    """Dense LU (brute force), sparse LU, the three-step diagonalisation and the
+    spectral closed form solve the same general-RHS system."""
+    alpha = 1e-3 if form == O.PQ else 1e-3 * grid.tau
+    F = bi.random_general_rhs(grid, seed=5)
+    ref = O.solve_dense(grid, form, alpha, F)
+    for solver in (O.solve_sparse_lu, O.solve_pint_three_step, O.solve_spectral):
+        assert O.rel_l2(solver(grid, form, alpha, F), ref) < 1e-10, solver.__name__
+    assert O.rel_residual(grid, form, alpha, ref, F) < 1e-12
+
+
+def test_three_step_is_real():
+    grid = bi.Grid(2, (8, 8), 1.0, 0.1, 16)
+    F = bi.random_general_rhs(grid, seed=3)
+    _, imag = O.solve_pint_three_step(grid, O.PQ, 1e-4, F, return_imag=True)
+    assert imag < 1e-9
+
+
+@pytest.mark.parametrize("form", [O.PQ, O.PM])
+def test_solution_satisfies_the_scheme(form):
+    """The solution satisfies the scheme of Sections 3.1/3.2 before it is scaled:
+    backward Euler rows (y^n - y^{n-1})/tau = Lap y^n, and the final condition
+    y^N + alpha (y^0 - tau Lap y^0) = g (PQ) or y^N - alpha(Lap y^0 - y^0/tau) = g (PM),
+    with the Laplacian applied as a direct stencil."""
+    grid = bi.Grid(2, (7, 6), 1.0, 0.2, 9)
+    g = np.random.default_rng(2).standard_normal(grid.shape)
+    alpha = 5e-3
+    y = O.solve_sparse_lu(grid, form, alpha, O.delta_rhs(grid, form, alpha, g))
+    tau = grid.tau
+    for n in range(1, grid.nt):
+        np.testing.assert_allclose((y[n] - y[n - 1]) / tau, _stencil_apply(y[n], grid.h), atol=1e-7)
+    lap0 = _stencil_apply(y[0], grid.h)
+    if form == O.PQ:
+        final = y[-1] + alpha * (y[0] - tau * lap0)
+    else:
+        final = y[-1] - alpha * (lap0 - y[0] / tau)
+    np.testing.assert_allclose(final, g, atol=1e-9)
+
+
+# ------------------------------------------------------- Section 4 inequalities
+
+@pytest.mark.parametrize("form", [O.PQ, O.PM])
+def test_stability_bound(form):
+    """eqs. (4.7)/(4.8): ||y(t_n)|| <= (c/alpha)^{1 - t_n/(T+tau)} ||g||, c = 1 (PQ) or tau (PM)."""
+    grid = bi.Grid(2, (16, 16), 1.0, 0.1, 33)
+    g = np.random.default_rng(4).standard_normal(grid.shape)
+    tau, T = grid.tau, grid.T
+    for alpha in (1e-1, 1e-3, 1e-6):
+        y = O.solve_spectral(grid, form, alpha, O.delta_rhs(grid, form, alpha, g))
+        c = 1.0 if form == O.PQ else tau
+        gn = bi.discrete_l2(g, grid)
+        for n in range(grid.nt):
+            bound = (c / alpha) ** (1 - n * tau / (T + tau)) * gn
+            assert bi.discrete_l2(y[n], grid) <= bound * (1 + 1e-12)
+
+
+def test_noise_free_convergence_as_alpha_shrinks():
+    """With exact discrete data the reconstruction error decreases monotonically
+    to 0 as alpha -> 0 (regularisation error of eq. (4.9) -> 0)."""
+    p = bi.make_c1()
+    grid = p.grid
+    errs = []
+    for alpha in (1e-1, 1e-2, 1e-3, 1e-4, 1e-6, 1e-8):
+        y = O.solve_spectral(grid, O.PQ, alpha, O.delta_rhs(grid, O.PQ, alpha, p.g))
+        errs.append(bi.discrete_l2(y[0] - p.z0, grid))
+    assert all(b < a for a, b in zip(errs, errs[1:]))
+    assert errs[-1] < 1e-4 * bi.discrete_l2(p.z0, grid)   # mode 3: alpha/r^N ~ 7e-5
+
+
+@pytest.mark.parametrize("form", [O.PQ, O.PM])
+def test_theorem_4_1_bound(form):
+    """Theorem 4.1: with alpha = delta/E0 (PQ) or tau delta/E0 (PM),
+    ||y_{alpha,delta}(t) - z(t)|| <= sqrt(2) E0^{1 - t/(T+tau)} delta^{t/(T+tau)},
+    z(t_n) the exact discrete forward solution."""
+    for seed in range(3):
+        p = bi.make_c2(seed=seed, M=32, nt=32)
+        grid = p.grid
+        E0 = bi.discrete_l2(p.z0, grid)
+        alpha = p.delta / E0 if form == O.PQ else grid.tau * p.delta / E0
+        y = O.solve_spectral(grid, form, alpha, O.delta_rhs(grid, form, alpha, p.g_delta))
+        for n in range(0, grid.nt, 5):
+            zn = bi.forward_discrete(grid, p.z0, steps=n)
+            t = n * grid.tau
+            bound = math.sqrt(2) * E0 ** (1 - t / (grid.T + grid.tau)) * p.delta ** (t / (grid.T + grid.tau))
+            assert bi.discrete_l2(y[n] - zn, grid) <= bound
+
+
+# ------------------------------------------------------- printed table values
+
+def _read_table(name):
+    rows = []
+    with open(os.path.join(GOLDEN, name)) as f:
+        for line in f:
+            if line.strip() and not line.startswith("#"):
+                parts = line.split()
+                rows.append((parts[0], int(parts[1]), int(parts[2]), [float(v) for v in parts[3:]]))
+    return rows
+
+
+EPS = [1e-1, 1e-2, 1e-3, 1e-4]
+
+
+def _mean_error_ex2(method, M, N, eps, seeds=3):
+    errs = []
+    for seed in range(seeds):
+        p = bi.make_paper_ex2(M, N, eps, seed=seed)
+        grid = p.grid
+        if method in ("pint-qbvm", "pint-mqbvm"):
+            form = O.PQ if method == "pint-qbvm" else O.PM
+            a = O.alpha_apriori(form, p.delta, grid.tau)
+            y = O.solve_spectral(grid, form, a, O.delta_rhs(grid, form, a, p.g_delta))
+        else:
+            y = solve_original(grid, method, p.delta, p.g_delta)
+        errs.append(bi.discrete_l2(y[0] - p.z0, grid))
+    return float(np.mean(errs))
+
+
+@pytest.mark.parametrize("row", [r for r in _read_table("paper_table2_ex2_pint_errors.txt")
+                                 if r[0].startswith("pint") or r[1] <= 16],      # sparse LU of A_h is slow beyond 16^2
+                         ids=lambda r: f"{r[0]}-{r[1]}")
+def test_table2_example2_errors(row):
+    """Table 2 (Section 5.2): the noise draw is not recoverable, so compare the
+    seed-averaged e_h with a 20% band; a wrong norm reading or a dropped
+    regularisation term moves e_h by 50-500%."""
+    method, M, N, printed = row
+    for eps, want in zip(EPS, printed):
+        got = _mean_error_ex2(method, M, N, eps)
+        assert abs(got - want) <= 0.2 * want, (method, M, eps, got, want)
+
+
+@pytest.mark.parametrize("row", [r for r in _read_table("paper_table1_ex1_pint_errors.txt") if r[1] <= 512],
+                         ids=lambda r: f"{r[0]}-{r[1]}")
+def test_table1_example1_errors(row):
+    """Table 1 (Section 5.1): 1D errors scatter strongly with the noise draw;
+    the seed-averaged e_h stays within 30% of the printed value."""
+    method, M, N, printed = row
+    form = O.PQ if method == "pint-qbvm" else O.PM
+    for eps, want in zip(EPS, printed):
+        errs = []
+        for seed in range(6):
+            p = bi.make_paper_ex1(M, N, eps, seed=seed)
+            grid = p.grid
+            a = O.alpha_apriori(form, p.delta, grid.tau)
+            y = O.solve_spectral(grid, form, a, O.delta_rhs(grid, form, a, p.g_delta))
+            errs.append(bi.discrete_l2(y[0] - p.z0, grid))
+        got = float(np.mean(errs))
+        assert abs(got - want) <= 0.3 * want, (method, M, eps, got, want)
+
+
+def test_planted_mistakes_are_caught():
+    """A dropped tau*Lap term (plain QBVM structure) or a flipped omega sign would
+    break the closed form of test_eigenfunction_data_closed_form; check the
+    pin itself discriminates by perturbing the oracle's matrix on the CPU."""
+    grid = bi.Grid(1, (8,), 1.0, 0.1, 6)
+    alpha = 2e-3
+    g = bi.sine_field(grid, [(3,)], [1.0])
+    F = O.delta_rhs(grid, O.PQ, alpha, g)
+    want = _mode_closed_form(grid, O.PQ, alpha, (3,), 1.0)
+    A = O.assemble_pint(grid, O.PQ, alpha).tolil()
+    Nx = grid.Nx
+    A[0:Nx, (grid.nt - 1) * Nx:] = -A[0:Nx, (grid.nt - 1) * Nx:]      # flip omega's sign
+    import scipy.sparse.linalg as spla
+    bad = spla.spsolve(A.tocsc(), F.ravel()).reshape(grid.full_shape)
+    assert np.abs(bad - want).max() > 1e-3 * np.abs(want).max()
