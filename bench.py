@@ -1,0 +1,410 @@
+#!/usr/bin/env python3
+"""Throughput of the PinT-QBVM / PinT-MQBVM all-at-once direct solve on GB300.
+
+Workload (default): 2D unit square, 255^2 interior points (5-point Laplacian),
+256 time levels, T = 0.1 -- 16 646 400 all-at-once unknowns per solve -- with
+z(., 0) a sum of 16 random decaying sine modes and g_delta the discrete forward
+solution plus 1% Gaussian noise (seeded).  One step solves BOTH formulations
+(PinT-QBVM with alpha = delta, PinT-MQBVM with alpha = tau*delta, the a-priori
+rule of Section 5): 2 x 16 646 400 unknowns.  The right-hand side is given in
+full ("general": f_h of eq. 3.3/3.6 with every level stored and read), or as g
+only ("delta", --rhs delta).
+
+Metric: all-at-once unknowns solved per second (whole job, all ranks).  The
+device-timed value uses CUDA events around each step on the solve stream with
+the inputs resident in HBM and an L2 flush (a 256 MB write) between steps
+outside the timed events.  e2e repeats the step through the same C ABI with
+pinned HOST buffers, so the host<->device copies are inside the timing.
+
+  python bench.py [--gpus N --steps K --warmup W] [--rhs general|delta]
+  python bench.py --impl reference ...     # the CPU FP64 oracle, timed alone
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import math
+import os
+import statistics
+import subprocess
+import sys
+import threading
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+if ROOT not in sys.path:
+    sys.path.insert(0, ROOT)
+
+METRIC = "all-at-once unknowns solved/sec and HBM GB/s fraction at <=1e-10 rel err vs FP64 oracle"
+UNIT = "unknowns/s"
+# FP64 ALU peak derived from the part's unit counts and clock: 152 SMs x 2 FP64
+# operations (DADD, DMUL or DFMA) per clock x 2.07 GHz.
+FP64_PEAK_TOPS = 152 * 2 * 2.07e9 / 1e12
+# DRAM bytes (read + write) per launch from one ncu capture of the current
+# kernels on this workload (profiles/); None once a kernel changes.
+PROFILED_TRAFFIC = {"time_solve": 133.826048e6 + 75.166208e6, "dst_x": 133.250048e6 + 85.027072e6}
+
+
+def _peaks():
+    try:
+        with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as f:
+            d = json.load(f)
+        return float(d["hbm_gbs"]), "measured"
+    except Exception:
+        return 6800.0, "fallback"
+
+
+def parse():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=20)
+    ap.add_argument("--warmup", type=int, default=5)
+    ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
+    ap.add_argument("--rhs", choices=["general", "delta"], default="general")
+    ap.add_argument("--e2e-steps", type=int, default=4)
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    return ap.parse_args()
+
+
+def workload():
+    import bhcp_inputs as bi
+    return bi.make_c2()
+
+
+def _cores_used() -> int:
+    try:
+        from threadpoolctl import threadpool_info
+        n = max((i.get("num_threads", 1) for i in threadpool_info()), default=1)
+        return int(n)
+    except Exception:
+        return os.cpu_count() or 1
+
+
+def cpu_oracle_leg(prob, forms, steps):
+    """Time the CPU FP64 oracle (exact sine-basis solve) as it stands on the
+    host cores; returns (unknowns/s, seconds list, solutions by form)."""
+    import numpy as np
+    import oracle as O
+    grid = prob.grid
+    times, sols = [], {}
+    for i in range(steps):
+        form = forms[i % len(forms)]
+        alpha = O.alpha_apriori(form, prob.delta, grid.tau)
+        F = O.delta_rhs(grid, form, alpha, prob.g_delta)
+        t0 = time.perf_counter()
+        y = O.solve_spectral(grid, form, alpha, F)
+        times.append(time.perf_counter() - t0)
+        sols[form] = y
+    return grid.unknowns / statistics.median(times), times, sols
+
+
+# ------------------------------------------------------------------ clocks
+
+class ClockSampler:
+    """nvidia-smi clocks / throttle reasons sampled every 50 ms while running."""
+
+    FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, index: int):
+        self.index = index
+        self.proc = None
+        self.lines = []
+        self.t = None
+
+    def start(self):
+        try:
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", f"--id={self.index}", f"--query-gpu={self.FIELDS}", "--format=csv,noheader,nounits",
+                 "-lms", "50"], stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+            self.t = threading.Thread(target=self._read, daemon=True)
+            self.t.start()
+        except Exception:
+            self.proc = None
+
+    def _read(self):
+        for line in self.proc.stdout:
+            self.lines.append(line.strip())
+
+    def stop(self) -> dict:
+        if self.proc is None:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except Exception:
+            self.proc.kill()
+        if self.t:
+            self.t.join(timeout=2)
+        sm, smax, reasons = [], [], set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for line in self.lines:
+            parts = [p.strip() for p in line.split(",")]
+            if len(parts) < 9:
+                continue
+            try:
+                sm.append(float(parts[1]))
+                smax.append(float(parts[2]))
+            except ValueError:
+                continue
+            for nm, v in zip(names, parts[5:9]):
+                if v.lower().startswith("active"):
+                    reasons.add(nm)
+        return {"sm_mhz": statistics.median(sm) if sm else None, "sm_max_mhz": max(smax) if smax else None,
+                "reasons": sorted(reasons), "samples": len(sm)}
+
+
+# --------------------------------------------------------------- our arm
+
+def _fft_ops(lm: int) -> float:
+    """FP64 operations per complex element of the radix-4/2 Stockham FFT of
+    length 2^lm: 4 per element in the first radix-4 pass (16 adds per
+    butterfly), 7 in later radix-4 passes (+3 complex twiddle products of 4
+    operations), 4 in the closing radix-2 pass (1 product + 2 complex adds)."""
+    if lm == 0:
+        return 0.0
+    r4, r2 = lm // 2, lm % 2
+    return (4.0 + 7.0 * (r4 - 1) if r4 else 0.0) + 4.0 * r2
+
+
+def kernel_model(name, grid, rhs):
+    """Algorithmic HBM bytes and FP64 operations (DADD, DMUL, DFMA count one each)
+    of one launch of `name` in a full solve, from the kernels' arithmetic:
+
+    time_solve, per real element: 2.5 (omega-scaling) + 2 x FFT(nt/2)/2
+      + 8 (complex divide by d_k + tau Lambda) + 2.5 (unscaling).
+    dst (length M per real column), per real element: 3 (pair pre-processing)
+      + FFT(M)/2 + 2 (column separation) + 1 (prefix sum).
+    Bytes: each pass reads and writes every FP64 value once."""
+    nt, Nx = grid.nt, grid.Nx
+    if name == "time_solve":
+        reads = Nx if rhs == "delta" else nt * Nx
+        byts = 8 * (reads + nt * Nx)
+        ops = (2.5 + _fft_ops(int(math.log2(nt // 2))) + 8.0 + 2.5) * nt * Nx
+        return byts, ops
+    if name.startswith("dst_"):
+        ax = "xyz".index(name[-1])
+        M = grid.M[ax]
+        byts = 16 * nt * Nx
+        ops = (3.0 + _fft_ops(int(math.log2(M))) / 2 + 2.0 + 1.0) * nt * Nx
+        return byts, ops
+    return None, None
+
+
+def our_arm(args, rank, world, device):
+    import numpy as np
+    import torch
+    import paper_2107_06381_gb300 as Q
+
+    Q.build_library()
+    Q.load_library()
+    prob = workload()
+    grid = prob.grid
+    forms = [Q.FORM_PQ, Q.FORM_PM]
+    rhs_kind = Q.RHS_GENERAL if args.rhs == "general" else Q.RHS_DELTA
+    stream = torch.cuda.Stream(device)
+    plans, inputs, outputs = [], [], []
+    for form in forms:
+        alpha = prob.delta if form == Q.FORM_PQ else grid.tau * prob.delta
+        plans.append(Q.Plan(grid.dim, grid.M, grid.L, grid.T, grid.nt, form, alpha, 0.0, Q.FP64, rhs_kind))
+        if rhs_kind == Q.RHS_GENERAL:
+            # f_h of eq. 3.3 / 3.6 stored in full: level 0 = -omega g / tau, others 0
+            omega = -1.0 / alpha if form == Q.FORM_PQ else -grid.tau / alpha
+            F = np.zeros(grid.full_shape)
+            F[0] = -omega / grid.tau * prob.g_delta
+        else:
+            F = prob.g_delta
+        inputs.append(torch.as_tensor(np.ascontiguousarray(F).ravel(), dtype=torch.float64, device=device))
+        outputs.append(torch.empty(grid.unknowns, dtype=torch.float64, device=device))
+    flush = torch.empty(64 * 1024 * 1024, dtype=torch.float32, device=device)    # 256 MB > L2
+
+    def step():
+        for plan, fin, yout in zip(plans, inputs, outputs):
+            plan.solve(fin, yout, stream=stream)
+
+    with torch.cuda.stream(stream):
+        for _ in range(args.warmup):
+            step()
+    torch.cuda.synchronize(device)
+
+    # ---- timed region
+    for plan in plans:
+        plan.profile(True)
+    evs = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(args.steps)]
+    sampler = ClockSampler(device.index if device.index is not None else 0)
+    if world > 1:
+        torch.distributed.barrier()
+    torch.cuda.synchronize(device)
+    sampler.start()
+    with torch.cuda.stream(stream):
+        for i in range(args.steps):
+            evs[i][0].record(stream)
+            step()
+            evs[i][1].record(stream)
+            flush.zero_()                      # L2 flush between steps, outside the events
+    torch.cuda.synchronize(device)
+    clocks = sampler.stop()
+    step_ms = [a.elapsed_time(b) for a, b in evs]
+    total_ms = sum(step_ms)
+    if world > 1:
+        t = torch.tensor([total_ms], dtype=torch.float64, device=device)
+        torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
+        torch.distributed.barrier()
+        total_ms = float(t.item())
+    kstats = {}
+    for plan in plans:
+        for name, (launches, ms) in plan.profile_read().items():
+            a, b = kstats.get(name, (0, 0.0))
+            kstats[name] = (a + launches, b + ms)
+        plan.profile(False)
+    launches_per_solve = plans[0].info.kernels_per_solve
+    unknowns_step = grid.unknowns * len(forms)
+    value = world * unknowns_step * args.steps / (total_ms / 1e3)
+
+    # ---- roofline of the dominant kernel
+    hbm_peak, hbm_src = _peaks()
+    dom = max(kstats.items(), key=lambda kv: kv[1][1])
+    dname, (dl, dms) = dom
+    byts, ops = kernel_model(dname, grid, args.rhs)
+    avg_s = dms / dl / 1e3
+    roof = None
+    if byts is not None:
+        t_hbm = byts / (hbm_peak * 1e9)
+        t_alu = ops / (FP64_PEAK_TOPS * 1e12)
+        traffic = PROFILED_TRAFFIC.get(dname)
+        if t_alu > t_hbm:
+            ach = ops / avg_s / 1e12
+            roof = {"bound": "alu", "kernel": dname, "achieved": round(ach, 4), "peak": round(FP64_PEAK_TOPS, 4),
+                    "unit": "T FP64-op/s (DADD/DMUL/DFMA = 1 op)", "frac": round(ach / FP64_PEAK_TOPS, 4),
+                    "traffic": traffic,
+                    "peak_source": "derived: 152 SMs x 2 FP64 ops/clk x 2.07 GHz",
+                    "hbm_achieved_gbs": round(byts / avg_s / 1e9, 1),
+                    "hbm_frac": round(byts / avg_s / 1e9 / hbm_peak, 4), "hbm_peak_source": hbm_src}
+        else:
+            ach = byts / avg_s / 1e9
+            roof = {"bound": "hbm", "kernel": dname, "achieved": round(ach, 1), "peak": hbm_peak, "unit": "GB/s",
+                    "frac": round(ach / hbm_peak, 4), "traffic": traffic, "peak_source": hbm_src}
+    kernels = {k: {"launches": v[0], "avg_ms": round(v[1] / v[0], 4), "share": round(v[1] / sum(x[1] for x in kstats.values()), 4)}
+               for k, v in sorted(kstats.items(), key=lambda kv: -kv[1][1])}
+
+    # ---- end to end through the C ABI with pinned host buffers
+    host_in = [torch.empty(x.numel(), dtype=torch.float64, pin_memory=True) for x in inputs]
+    host_out = [torch.empty(y.numel(), dtype=torch.float64, pin_memory=True) for y in outputs]
+    for h, d in zip(host_in, inputs):
+        h.copy_(d.cpu())
+    for plan, hi, ho in zip(plans, host_in, host_out):     # warm-up (staging buffers)
+        Q.qbvm_solve(plan.handle, hi.data_ptr(), ho.data_ptr(), False, stream.cuda_stream)
+    e2e_times = []
+    for _ in range(max(1, args.e2e_steps)):
+        if world > 1:
+            torch.distributed.barrier()
+        t0 = time.perf_counter()
+        for plan, hi, ho in zip(plans, host_in, host_out):
+            Q.qbvm_solve(plan.handle, hi.data_ptr(), ho.data_ptr(), False, stream.cuda_stream)
+        e2e_times.append(time.perf_counter() - t0)
+    e2e_s = sum(e2e_times)
+    if world > 1:
+        t = torch.tensor([e2e_s], dtype=torch.float64, device=device)
+        torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
+        e2e_s = float(t.item())
+    e2e = {"value": world * unknowns_step * len(e2e_times) / e2e_s, "unit": UNIT,
+           "h2d_bytes_per_step": sum(x.numel() * 8 for x in inputs),
+           "d2h_bytes_per_step": sum(y.numel() * 8 for y in outputs),
+           "ms_per_step": round(1e3 * e2e_s / len(e2e_times), 3)}
+    # the e2e outputs must equal the device-path outputs
+    torch.cuda.synchronize(device)
+    e2e_match = all(torch.equal(ho, y.cpu()) for ho, y in zip(host_out, outputs))
+
+    # ---- CPU oracle leg (rank 0, N = 1) and accuracy of this run
+    cpu = None
+    rel_err = None
+    if rank == 0 and world == 1 and not args.no_cpu_baseline:
+        cpu_val, cpu_times, sols = cpu_oracle_leg(prob, forms, 2)
+        cpu = {"value": cpu_val, "unit": UNIT, "cores": _cores_used(), "kind": "oracle",
+               "sample": "one full 255^2 x 256 solve per formulation (PinT-QBVM, PinT-MQBVM) by the FP64 "
+                         "sine-basis oracle (dense DST-I matrices + exact per-mode recurrence), median of 2",
+               "seconds": [round(t, 3) for t in cpu_times]}
+        errs = []
+        for form, y in zip(forms, outputs):
+            got = y.cpu().numpy()
+            want = sols[form].ravel()
+            errs.append(float(np.linalg.norm(got - want) / np.linalg.norm(want)))
+        rel_err = max(errs)
+
+    out = {
+        "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
+        "warmup": args.warmup, "ms_per_step": total_ms / args.steps, "higher_is_better": True,
+        "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+        "config": {"workload": f"c2_2d_255sq_x256_{args.rhs}_rhs", "dim": 2, "interior": [255, 255], "nt": 256,
+                   "T": grid.T, "forms": ["pint-qbvm", "pint-mqbvm"], "rhs": args.rhs,
+                   "unknowns_per_solve": grid.unknowns, "solves_per_step": len(forms),
+                   "l2": "flushed between steps (256 MB write outside the timed events); inputs 133 MB/solve",
+                   "parallelism": f"replicas{world}"},
+        "roofline": roof,
+        "kernels": kernels,
+        "e2e": e2e,
+        "e2e_matches_device_path": e2e_match,
+        "gpu_launches": launches_per_solve * len(forms) * args.steps,
+        "clocks": clocks,
+        "cpu_baseline": cpu,
+        "rel_err_vs_oracle": rel_err,
+    }
+    for plan in plans:
+        plan.close()
+    return out
+
+
+# ------------------------------------------------------------ reference arm
+
+def reference_arm(args):
+    """The CPU FP64 oracle as it stands, on this host's cores; one step = one
+    formulation (alternating) of the same workload."""
+    import oracle as O
+    prob = workload()
+    grid = prob.grid
+    forms = [O.PQ, O.PM]
+    for i in range(args.warmup):
+        cpu_oracle_leg(prob, [forms[i % 2]], 1)
+    t0 = time.perf_counter()
+    _, times, _ = cpu_oracle_leg(prob, forms, args.steps)
+    total = time.perf_counter() - t0
+    value = grid.unknowns * args.steps / total
+    cores = _cores_used()
+    sample = ("one full 255^2 x 256 solve per step (PinT-QBVM and PinT-MQBVM alternating) by the FP64 "
+              "sine-basis oracle")
+    return {"impl": "reference", "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": args.gpus,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * total / args.steps,
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
+            "data": "synthetic",
+            "config": {"workload": f"c2_2d_255sq_x256_{args.rhs}_rhs", "dim": 2, "interior": [255, 255], "nt": 256,
+                       "parallelism": "cpu"},
+            "cpu_baseline": {"value": value, "unit": UNIT, "cores": cores, "kind": "oracle", "sample": sample},
+            "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+
+
+def main():
+    args = parse()
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local_rank = int(os.environ.get("LOCAL_RANK", "0"))
+    if args.impl == "reference":
+        if rank != 0:
+            return 0
+        print(json.dumps(reference_arm(args)), flush=True)
+        return 0
+    import torch
+    device = torch.device("cuda", local_rank)
+    torch.cuda.set_device(device)
+    if world > 1:
+        torch.distributed.init_process_group("nccl", device_id=device)
+    out = our_arm(args, rank, world, device)
+    if rank == 0:
+        print(json.dumps(out), flush=True)
+    if world > 1:
+        torch.distributed.destroy_process_group()
+    return 0
+
+
+if __name__ == "__main__":
+    sys.exit(main())

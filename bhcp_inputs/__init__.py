@@ -206,9 +206,16 @@ def make_c1(seed: int = 1) -> Problem:
 
 
 def _decaying_sine_modes(rng, dim: int, count: int, kmax: int):
+    """``count`` distinct wave-number tuples from {1..kmax}^dim, the lowest mode
+    always included and the others drawn with weight 1/|k|^4 (at T = 0.1 a mode
+    with |k|^2 = 40 has decayed by e^{-40}: uniform draws give data ~1e-8)."""
     pool = np.array(np.meshgrid(*[np.arange(1, kmax + 1)] * dim, indexing="ij")).reshape(dim, -1).T
-    idx = rng.choice(len(pool), size=count, replace=False)
-    modes = pool[idx]
+    k2 = (pool.astype(np.float64) ** 2).sum(axis=1)
+    first = int(np.argmin(k2))
+    rest = np.array([i for i in range(len(pool)) if i != first])
+    w = 1.0 / k2[rest] ** 2
+    idx = rng.choice(rest, size=count - 1, replace=False, p=w / w.sum())
+    modes = pool[np.concatenate([[first], idx])]
     amps = rng.uniform(0.5, 1.5, size=count) * rng.choice([-1.0, 1.0], size=count)
     amps = amps / (modes.astype(np.float64) ** 2).sum(axis=1)
     return modes, amps
@@ -216,7 +223,8 @@ def _decaying_sine_modes(rng, dim: int, count: int, kmax: int):
 
 def make_c2(seed: int = 2, M: int = 256, nt: int = 256) -> Problem:
     """2D unit square, (M-1)^2 interior points, nt levels, T=0.1; z0 = 16 random
-    sine modes (k, l) in {1..8}^2 with amplitudes U(0.5,1.5) * sign / (k^2 + l^2);
+    sine modes (k, l) in {1..8}^2 (weighted toward low |k|, (1,1) always present)
+    with amplitudes U(0.5,1.5) * sign / (k^2 + l^2);
     g = discrete forward solution at T; 1% Gaussian noise relative to ||g||."""
     grid = Grid(2, (M, M), 1.0, 0.1, nt)
     rng = np.random.default_rng(seed)

@@ -258,7 +258,7 @@ def _apply_axis(S: np.ndarray, c: np.ndarray, ax: int) -> np.ndarray:
     return np.moveaxis(np.tensordot(S, np.moveaxis(c, ax, 0), axes=(1, 0)), 0, ax)
 
 
-def solve_spectral(grid, form: int, alpha: float, F: np.ndarray) -> np.ndarray:
+def solve_spectral(grid, form: int, alpha: float, F: np.ndarray, levels=None) -> np.ndarray:
     """O3: the exact solution of eq. (3.3)/(3.6) in the sine eigenbasis.
 
     Delta_h = S diag(-Lambda) S^{-1} with dense sine matrices per axis
@@ -271,11 +271,20 @@ def solve_spectral(grid, form: int, alpha: float, F: np.ndarray) -> np.ndarray:
         y^0 = (tau f^0 + omega q^N) / (1 + tau Lambda - omega r^N),
         y^n = r (y^{n-1} + tau f^n).
     No FFT is used anywhere, so this shares nothing with an FFT-based path.
+    ``levels`` (optional) restricts the returned time levels (the inverse DST
+    is then applied to those levels only); F may then also be given as the
+    single level g when it is a delta right-hand side of shape grid.shape.
     """
     tau = grid.tau
     om = omega_of(form, alpha, tau)
     nt = grid.nt
-    Fh = np.asarray(F, dtype=np.float64).reshape(grid.full_shape).copy()
+    F = np.asarray(F, dtype=np.float64)
+    if F.size == grid.Nx:                       # delta right-hand side given as level 0 only
+        F0 = F.reshape((1,) + grid.shape)
+        Fh = np.zeros(grid.full_shape)
+        Fh[0] = F0[0]
+    else:
+        Fh = F.reshape(grid.full_shape).copy()
     lam = np.zeros(grid.shape)
     for d in range(grid.dim):
         M = grid.M[d]
@@ -293,6 +302,8 @@ def solve_spectral(grid, form: int, alpha: float, F: np.ndarray) -> np.ndarray:
     Y[0] = (tau * Fh[0] + om * q) / (1.0 + tau * lam - om * rN)
     for n in range(1, nt):
         Y[n] = r * (Y[n - 1] + tau * Fh[n])
+    if levels is not None:
+        Y = Y[list(levels)]
     for d in range(grid.dim):
         M = grid.M[d]
         ax = grid.dim - d

@@ -1,0 +1,226 @@
+"""Python binding of libqbvm (PinT-QBVM / PinT-MQBVM all-at-once solver, sm_103a).
+
+Argument marshalling only: every step of the solve runs in the CUDA library
+built from ``csrc/`` (see ``include/qbvm.h`` for the C ABI).  The functions
+carry the C names.  Arrays may be torch tensors (CUDA or CPU), numpy arrays
+(host) or raw integer addresses; FP64, C-contiguous.  If the shared library
+is missing, importing the functions raises -- there is no fallback.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+
+from .build import LIB_PATH, build as build_library
+
+__all__ = [
+    "QbvmDesc", "QbvmInfo", "QbvmError", "load_library",
+    "qbvm_plan", "qbvm_solve", "qbvm_residual", "qbvm_plan_info", "qbvm_destroy",
+    "qbvm_profile_enable", "qbvm_profile_read",
+    "qbvm_strerror", "qbvm_version", "Plan",
+    "FORM_PQ", "FORM_PM", "FP64", "FP32_REFINE", "RHS_DELTA", "RHS_GENERAL",
+]
+
+FORM_PQ, FORM_PM = 0, 1
+FP64, FP32_REFINE = 0, 1
+RHS_DELTA, RHS_GENERAL = 0, 1
+
+
+class QbvmDesc(ctypes.Structure):
+    _fields_ = [
+        ("dim", ctypes.c_int), ("m", ctypes.c_int * 3), ("L", ctypes.c_double),
+        ("T", ctypes.c_double), ("nt", ctypes.c_int), ("form", ctypes.c_int),
+        ("alpha", ctypes.c_double), ("delta", ctypes.c_double),
+        ("precision", ctypes.c_int), ("rhs_kind", ctypes.c_int),
+        ("refine_tol", ctypes.c_double), ("refine_max_iters", ctypes.c_int),
+    ]
+
+
+class QbvmInfo(ctypes.Structure):
+    _fields_ = [
+        ("alpha", ctypes.c_double), ("omega", ctypes.c_double), ("tau", ctypes.c_double),
+        ("unknowns", ctypes.c_longlong), ("workspace_bytes", ctypes.c_longlong),
+        ("last_refine_iters", ctypes.c_int), ("last_rel_residual", ctypes.c_double),
+        ("kernels_per_solve", ctypes.c_int),
+    ]
+
+
+class QbvmKernelStat(ctypes.Structure):
+    _fields_ = [("name", ctypes.c_char * 32), ("launches", ctypes.c_longlong), ("total_ms", ctypes.c_double)]
+
+
+class QbvmError(RuntimeError):
+    def __init__(self, code: int, what: str):
+        self.code = code
+        super().__init__(f"{what}: {qbvm_strerror(code)} (status {code})")
+
+
+_lib = None
+
+
+def load_library(path: str | None = None) -> ctypes.CDLL:
+    """Load libqbvm.so (the in-tree build).  Raises if it has not been built."""
+    global _lib
+    if _lib is not None and path is None:
+        return _lib
+    p = path or LIB_PATH
+    if not os.path.exists(p):
+        raise ImportError(f"libqbvm.so not found at {p}; run paper_2107_06381_gb300.build_library()")
+    lib = ctypes.CDLL(p)
+    vp, ip, dp = ctypes.c_void_p, ctypes.c_int, ctypes.c_double
+    lib.qbvm_plan.argtypes = [ctypes.POINTER(QbvmDesc), ctypes.POINTER(vp)]
+    lib.qbvm_plan.restype = ip
+    lib.qbvm_solve.argtypes = [vp, vp, vp, ip, vp]
+    lib.qbvm_solve.restype = ip
+    lib.qbvm_residual.argtypes = [vp, vp, vp, ctypes.POINTER(dp), vp]
+    lib.qbvm_residual.restype = ip
+    lib.qbvm_plan_info.argtypes = [vp, ctypes.POINTER(QbvmInfo)]
+    lib.qbvm_plan_info.restype = ip
+    lib.qbvm_destroy.argtypes = [vp]
+    lib.qbvm_destroy.restype = ip
+    lib.qbvm_strerror.argtypes = [ip]
+    lib.qbvm_strerror.restype = ctypes.c_char_p
+    lib.qbvm_profile_enable.argtypes = [vp, ip]
+    lib.qbvm_profile_enable.restype = ip
+    lib.qbvm_profile_read.argtypes = [vp, ctypes.POINTER(QbvmKernelStat), ip, ctypes.POINTER(ip)]
+    lib.qbvm_profile_read.restype = ip
+    lib.qbvm_version.argtypes = []
+    lib.qbvm_version.restype = ip
+    if path is None:
+        _lib = lib
+    return lib
+
+
+def _ptr(a) -> int:
+    """Address of a tensor / ndarray / int (FP64, contiguous)."""
+    if a is None:
+        return 0
+    if isinstance(a, int):
+        return a
+    mod = type(a).__module__
+    if mod.startswith("torch"):
+        import torch
+        if a.dtype != torch.float64 or not a.is_contiguous():
+            raise TypeError("tensors must be contiguous float64")
+        return a.data_ptr()
+    if mod.startswith("numpy"):
+        import numpy as np
+        if a.dtype != np.float64 or not a.flags["C_CONTIGUOUS"]:
+            raise TypeError("arrays must be C-contiguous float64")
+        return a.ctypes.data
+    raise TypeError(f"unsupported array type {type(a)!r}")
+
+
+def _stream(stream, *arrays) -> int:
+    if stream is not None:
+        return int(stream) if not hasattr(stream, "cuda_stream") else stream.cuda_stream
+    for a in arrays:
+        if type(a).__module__.startswith("torch") and a.is_cuda:
+            import torch
+            return torch.cuda.current_stream(a.device).cuda_stream
+    return 0
+
+
+def _check(code: int, what: str):
+    if code != 0:
+        raise QbvmError(code, what)
+
+
+def qbvm_strerror(code: int) -> str:
+    return load_library().qbvm_strerror(code).decode()
+
+
+def qbvm_version() -> int:
+    return load_library().qbvm_version()
+
+
+def make_desc(dim, m, L, T, nt, form=FORM_PQ, alpha=0.0, delta=0.0, precision=FP64,
+              rhs_kind=RHS_DELTA, refine_tol=0.0, refine_max_iters=0) -> QbvmDesc:
+    mm = list(m) + [1] * (3 - len(m))
+    return QbvmDesc(dim, (ctypes.c_int * 3)(*mm), float(L), float(T), int(nt), int(form), float(alpha),
+                    float(delta), int(precision), int(rhs_kind), float(refine_tol), int(refine_max_iters))
+
+
+def qbvm_plan(desc: QbvmDesc) -> int:
+    h = ctypes.c_void_p()
+    _check(load_library().qbvm_plan(ctypes.byref(desc), ctypes.byref(h)), "qbvm_plan")
+    return h.value
+
+
+def qbvm_solve(plan: int, g_or_F, y, n0_only: bool = False, stream=None) -> None:
+    _check(load_library().qbvm_solve(plan, _ptr(g_or_F), _ptr(y), int(bool(n0_only)),
+                                     _stream(stream, g_or_F, y)), "qbvm_solve")
+
+
+def qbvm_residual(plan: int, y, g_or_F, stream=None) -> float:
+    out = ctypes.c_double()
+    _check(load_library().qbvm_residual(plan, _ptr(y), _ptr(g_or_F), ctypes.byref(out),
+                                        _stream(stream, y, g_or_F)), "qbvm_residual")
+    return out.value
+
+
+def qbvm_plan_info(plan: int) -> QbvmInfo:
+    info = QbvmInfo()
+    _check(load_library().qbvm_plan_info(plan, ctypes.byref(info)), "qbvm_plan_info")
+    return info
+
+
+def qbvm_profile_enable(plan: int, on: bool = True) -> None:
+    _check(load_library().qbvm_profile_enable(plan, int(bool(on))), "qbvm_profile_enable")
+
+
+def qbvm_profile_read(plan: int, capacity: int = 64) -> dict:
+    """{kernel name: (launches, total_ms)} since the last read / enable."""
+    arr = (QbvmKernelStat * capacity)()
+    n = ctypes.c_int()
+    _check(load_library().qbvm_profile_read(plan, arr, capacity, ctypes.byref(n)), "qbvm_profile_read")
+    return {arr[i].name.decode(): (arr[i].launches, arr[i].total_ms) for i in range(n.value)}
+
+
+def qbvm_destroy(plan: int) -> None:
+    if plan:
+        _check(load_library().qbvm_destroy(plan), "qbvm_destroy")
+
+
+class Plan:
+    """Owning wrapper around a qbvm plan handle."""
+
+    def __init__(self, dim, m, L, T, nt, form=FORM_PQ, alpha=0.0, delta=0.0, precision=FP64,
+                 rhs_kind=RHS_DELTA, refine_tol=0.0, refine_max_iters=0):
+        self.desc = make_desc(dim, m, L, T, nt, form, alpha, delta, precision, rhs_kind,
+                              refine_tol, refine_max_iters)
+        self.handle = qbvm_plan(self.desc)
+
+    def solve(self, g_or_F, y, n0_only=False, stream=None):
+        qbvm_solve(self.handle, g_or_F, y, n0_only, stream)
+        return y
+
+    def residual(self, y, g_or_F, stream=None) -> float:
+        return qbvm_residual(self.handle, y, g_or_F, stream)
+
+    def profile(self, on: bool = True):
+        qbvm_profile_enable(self.handle, on)
+
+    def profile_read(self) -> dict:
+        return qbvm_profile_read(self.handle)
+
+    @property
+    def info(self) -> QbvmInfo:
+        return qbvm_plan_info(self.handle)
+
+    def close(self):
+        if self.handle:
+            qbvm_destroy(self.handle)
+            self.handle = None
+
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *exc):
+        self.close()
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass

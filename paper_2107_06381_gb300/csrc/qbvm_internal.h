@@ -1,0 +1,64 @@
+// qbvm_internal.h -- host-side declarations shared by the plan code and the
+// kernel translation units (launch wrappers; no CUDA types beyond streams).
+#pragma once
+#include <cuda_runtime.h>
+#include <cstdint>
+
+namespace qbvm {
+
+// Columns of one shared-memory tile: TILE_ELEMS complex values per CTA.
+constexpr int TILE_ELEMS = 4096;
+constexpr int TILE_THREADS = 256;
+
+// Device tables of a plan (all FP64; FP32 copies where a kernel reads them in FP32).
+struct Tables {
+    int nt = 0, lnt = 0;             // time levels, log2
+    int dim = 0;
+    int n[3] = {1, 1, 1};            // interior points per axis (x, y, z)
+    int lpd[3] = {0, 0, 0};          // log2(M_d) = log2(n_d + 1), the DST FFT length
+    long long Nx = 0;                // spatial unknowns per level
+    double tau = 0, omega = 0;
+    double rho_h = 1, rho_hinv = 1;  // |omega|^{1/2} = rho^{nt/2} and its inverse
+    double2* tw_t = nullptr;         // exp(-2 pi i m / H), m < H = nt/2
+    float2*  tw_t32 = nullptr;
+    double2* tw_s[3] = {nullptr, nullptr, nullptr};   // exp(-2 pi i m / M_d), m < M_d
+    float2*  tw_s32[3] = {nullptr, nullptr, nullptr};
+    double*  sn_s[3] = {nullptr, nullptr, nullptr};   // sin(j pi / M_d), j = 0..M_d/2
+    float*   sn_s32[3] = {nullptr, nullptr, nullptr};
+    double2* gpow = nullptr;         // scale * gamma^t (t < H), gamma = omega^{1/nt} principal
+    double2* gipw = nullptr;         // 2 gamma^{-t} (t < H)
+    double2* ak = nullptr;           // d_{2m} = 1 - gamma theta^{2m}, m < H (eigenvalues of C_omega)
+    double*  lamtau = nullptr;       // tau * Lambda_l for every spatial mode (2D/3D)
+    double2* bk = nullptr;           // 1D Thomas diagonal for frequency 2m: h^2 d_{2m} / tau + 2
+};
+
+// DST-I (unnormalised, S_{jk} = sin(pi j k /(n+1))) along one axis of an
+// array viewed as [outer][n][inner], in place allowed (in == out).
+// lm = log2(n + 1); tw = roots of length n+1, sn = sin(j pi/(n+1)) tables.
+template <typename R>
+cudaError_t launch_dst(const R* in, R* out, int n, int lm, long long outer, long long inner,
+                       const void* tw, const void* sn, cudaStream_t s);
+
+// Space-first time solve: per spatial mode l (column), scale by gamma^t, FFT
+// (theta^{+kt}), divide by (d_k + tau Lambda_l)/cnorm, inverse FFT, unscale by
+// gamma^{-t}, real part.  in/out are [nt][Nx]; delta_rhs reads only level 0.
+template <typename R>
+cudaError_t launch_time_solve(const R* in, R* out, const Tables& tb, double cnorm, int delta_rhs,
+                              int n0_only, cudaStream_t s);
+
+// 1D time-first path (Section 3.3 order): forward time transform to complex
+// workspace, Thomas per frequency, inverse transform.
+cudaError_t launch_time_fwd_1d(const double* in, double2* wk, const Tables& tb, int delta_rhs, double in_scale,
+                               cudaStream_t s);
+cudaError_t launch_thomas_1d(double2* wk, double2* cp, const Tables& tb, cudaStream_t s);
+cudaError_t launch_time_inv_1d(const double2* wk, double* out, const Tables& tb, int n0_only, cudaStream_t s);
+
+// FP64 residual r = f - A y (eq. 3.3/3.6 stencil); per-block partial sums of
+// r^2 and f^2 into partials[2*blocks], then reduced into sums[2].
+// Optionally writes r (FP64) to r_out.
+cudaError_t launch_residual(const double* y, const double* f, int delta_rhs, const Tables& tb,
+                            const double h2inv[3], double* partials, int nblocks, double* sums,
+                            double* r_out, cudaStream_t s);
+int residual_blocks(const Tables& tb);
+
+}  // namespace qbvm

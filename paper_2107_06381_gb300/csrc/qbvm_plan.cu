@@ -1,0 +1,508 @@
+// qbvm_plan.cu -- plan construction, orchestration and the C ABI of qbvm.h.
+//
+// A plan derives tau, alpha and omega (Sections 3.1/3.2, the a-priori rule of
+// Section 5), builds the FP64 tables of the diagonalisation of Section 3.3
+// on the host, uploads them, and owns the device workspace.  qbvm_solve
+// enqueues the three steps of eq. 3.8 on the caller's stream.
+#include <cmath>
+#include <cstdio>
+#include <cstdlib>
+#include <cstring>
+#include <new>
+#include <vector>
+
+#include "qbvm.h"
+#include "qbvm_internal.h"
+
+using qbvm::Tables;
+
+struct qbvm_plan {
+    qbvm_desc d{};
+    Tables tb{};
+    int dev = 0;
+    double alpha = 0, omega = 0, tau = 0;
+    double h[3] = {1, 1, 1};
+    double h2inv[3] = {0, 0, 0};
+    int lp[3] = {0, 0, 0};
+    // workspace
+    double2* wk = nullptr;        // 1D: complex [nt][Nx]
+    double2* wcp = nullptr;       // 1D: Thomas modified super-diagonal
+    double* ghat = nullptr;       // 2D/3D delta rhs: DST of g (Nx)
+    double* wreal = nullptr;      // 2D/3D general rhs with n0_only: [nt][Nx]
+    double* partials = nullptr;   // residual partial sums
+    double* sums = nullptr;       // residual sums (2)
+    int nres = 0;
+    double* stage_in = nullptr;   // host-pointer staging
+    double* stage_out = nullptr;
+    // FP32 refinement workspace
+    float* f32 = nullptr;         // [nt][Nx] FP32 work array
+    float* g32 = nullptr;         // Nx FP32 (delta rhs)
+    double* rbuf = nullptr;       // FP64 residual [nt][Nx]
+    long long ws_bytes = 0;
+    int last_iters = 0;
+    double last_relres = 0.0;
+    int kernels_per_solve = 0;
+    std::vector<void*> allocs;
+    // tracing: (kernel name, start, stop) per launch while profiling is on
+    bool profiling = false;
+    struct Mark { const char* name; cudaEvent_t a, b; };
+    std::vector<Mark> marks;
+    std::vector<cudaEvent_t> event_pool;
+};
+
+namespace {
+
+bool is_pow2(long long v) { return v > 0 && (v & (v - 1)) == 0; }
+int ilog2(long long v) { int l = 0; while ((1LL << l) < v) ++l; return l; }
+
+int validate(const qbvm_desc* d) {
+    if (!d) return QBVM_ERR_BAD_ARG;
+    if (d->dim < 1 || d->dim > 3) return QBVM_ERR_BAD_ARG;
+    for (int i = 0; i < d->dim; ++i)
+        if (d->m[i] < 2) return QBVM_ERR_BAD_ARG;
+    if (d->nt < 2) return QBVM_ERR_BAD_ARG;
+    if (!(d->T > 0) || !std::isfinite(d->T)) return QBVM_ERR_BAD_ARG;
+    if (!(d->L > 0) || !std::isfinite(d->L)) return QBVM_ERR_BAD_ARG;
+    if (d->form != QBVM_FORM_PQ && d->form != QBVM_FORM_PM) return QBVM_ERR_BAD_ARG;
+    if (d->precision != QBVM_FP64 && d->precision != QBVM_FP32_REFINE) return QBVM_ERR_BAD_ARG;
+    if (d->rhs_kind != QBVM_RHS_DELTA && d->rhs_kind != QBVM_RHS_GENERAL) return QBVM_ERR_BAD_ARG;
+    if (!std::isfinite(d->alpha) || std::isnan(d->delta)) return QBVM_ERR_BAD_ARG;
+    if (!(d->alpha > 0) && !(d->delta > 0 && std::isfinite(d->delta))) return QBVM_ERR_BAD_ARG;
+    // sizes the kernels implement
+    if (!is_pow2(d->nt) || d->nt > 1024) return QBVM_ERR_UNSUPPORTED;
+    if (d->dim == 1) {
+        if (d->m[0] - 1 > (1 << 20)) return QBVM_ERR_UNSUPPORTED;
+    } else {
+        for (int i = 0; i < d->dim; ++i)
+            if (!is_pow2(d->m[i]) || d->m[i] < 4 || d->m[i] > 1024) return QBVM_ERR_UNSUPPORTED;
+    }
+    return QBVM_OK;
+}
+
+template <typename T>
+int dalloc(qbvm_plan_t* p, T** ptr, size_t count) {
+    *ptr = nullptr;
+    if (count == 0) return QBVM_OK;
+    void* v = nullptr;
+    if (cudaMalloc(&v, count * sizeof(T)) != cudaSuccess) {
+        cudaGetLastError();
+        return QBVM_ERR_OOM;
+    }
+    p->allocs.push_back(v);
+    p->ws_bytes += (long long)(count * sizeof(T));
+    *ptr = static_cast<T*>(v);
+    return QBVM_OK;
+}
+
+template <typename T>
+int upload(qbvm_plan_t* p, T** ptr, const std::vector<T>& host) {
+    int rc = dalloc(p, ptr, host.size());
+    if (rc) return rc;
+    if (cudaMemcpy(*ptr, host.data(), host.size() * sizeof(T), cudaMemcpyHostToDevice) != cudaSuccess)
+        return QBVM_ERR_CUDA;
+    return QBVM_OK;
+}
+
+// exp(-2 pi i m / P) for m < P (FP64, angle reduced to pi * (2m/P) with 2m/P exact)
+void roots(int P, std::vector<double2>& w64, std::vector<float2>& w32) {
+    w64.resize(P);
+    w32.resize(P);
+    for (int m = 0; m < P; ++m) {
+        double a = M_PI * (2.0 * m / P);
+        double c = std::cos(a), s = -std::sin(a);
+        w64[m] = make_double2(c, s);
+        w32[m] = make_float2((float)c, (float)s);
+    }
+}
+
+void destroy_plan(qbvm_plan_t* p) {
+    if (!p) return;
+    for (void* v : p->allocs) cudaFree(v);
+    for (auto& m : p->marks) {
+        cudaEventDestroy(m.a);
+        cudaEventDestroy(m.b);
+    }
+    for (cudaEvent_t e : p->event_pool) cudaEventDestroy(e);
+    delete p;
+}
+
+cudaEvent_t take_event(qbvm_plan_t* p) {
+    if (!p->event_pool.empty()) {
+        cudaEvent_t e = p->event_pool.back();
+        p->event_pool.pop_back();
+        return e;
+    }
+    cudaEvent_t e = nullptr;
+    if (cudaEventCreate(&e) != cudaSuccess) return nullptr;
+    return e;
+}
+
+// Brackets one kernel launch with events when the plan is profiling.
+struct Span {
+    qbvm_plan_t* p;
+    const char* name;
+    cudaStream_t s;
+    cudaEvent_t a = nullptr;
+    Span(qbvm_plan_t* p_, const char* n, cudaStream_t s_) : p(p_), name(n), s(s_) {
+        if (p->profiling && (a = take_event(p)) != nullptr) cudaEventRecord(a, s);
+    }
+    ~Span() {
+        if (!a) return;
+        cudaEvent_t b = take_event(p);
+        if (!b) {
+            p->event_pool.push_back(a);
+            return;
+        }
+        cudaEventRecord(b, s);
+        p->marks.push_back({name, a, b});
+    }
+};
+
+enum { KIND_DEV = 0, KIND_HOST = 1 };
+int ptr_kind(const void* ptr) {
+    cudaPointerAttributes a;
+    if (cudaPointerGetAttributes(&a, ptr) != cudaSuccess) {
+        cudaGetLastError();
+        return KIND_HOST;
+    }
+    return (a.type == cudaMemoryTypeDevice || a.type == cudaMemoryTypeManaged) ? KIND_DEV : KIND_HOST;
+}
+
+#define CK(call)                                    \
+    do {                                            \
+        cudaError_t e__ = (call);                   \
+        if (e__ != cudaSuccess) return QBVM_ERR_CUDA; \
+    } while (0)
+
+// --- FP64 pipeline on device pointers -------------------------------------
+
+int solve_fp64_dev(qbvm_plan_t* p, const double* in, double* y, int n0_only, cudaStream_t s) {
+    const Tables& tb = p->tb;
+    const int delta = p->d.rhs_kind == QBVM_RHS_DELTA;
+    int launches = 0;
+    if (tb.dim == 1) {
+        // Step (a), Step (b) (Thomas per frequency), Step (c)
+        { Span sp_(p, "time_fwd_1d", s); CK(qbvm::launch_time_fwd_1d(in, p->wk, tb, delta, delta ? -tb.omega / tb.tau : 1.0, s)); }
+        { Span sp_(p, "thomas_1d", s); CK(qbvm::launch_thomas_1d(p->wk, p->wcp, tb, s)); }
+        { Span sp_(p, "time_inv_1d", s); CK(qbvm::launch_time_inv_1d(p->wk, y, tb, n0_only, s)); }
+        launches = 3;
+    } else {
+        const long long nx = tb.n[0], ny = tb.n[1], nz = tb.n[2];
+        double cn = 1.0;
+        for (int i = 0; i < tb.dim; ++i) cn *= 2.0 / (tb.n[i] + 1);
+        cn /= tb.nt;
+        double* work;
+        if (delta) {
+            // DST of g along x, y (, z) -> ghat, then the time solve reads level 0
+            { Span sp_(p, "dst_x", s); CK(qbvm::launch_dst<double>(in, p->ghat, tb.n[0], p->lp[0], ny * nz, 1, tb.tw_s[0], tb.sn_s[0], s)); }
+            { Span sp_(p, "dst_y", s); CK(qbvm::launch_dst<double>(p->ghat, p->ghat, tb.n[1], p->lp[1], nz, nx, tb.tw_s[1], tb.sn_s[1], s)); }
+            launches += 2;
+            if (tb.dim == 3) {
+                { Span sp_(p, "dst_z", s); CK(qbvm::launch_dst<double>(p->ghat, p->ghat, tb.n[2], p->lp[2], 1, nx * ny, tb.tw_s[2], tb.sn_s[2], s)); }
+                ++launches;
+            }
+            // f^0 = -omega g / tau: fold -omega/tau into the time-solve constant
+            { Span sp_(p, "time_solve", s); CK(qbvm::launch_time_solve<double>(p->ghat, y, tb, -tb.omega * cn, 1, n0_only, s)); }
+            ++launches;
+            work = y;
+        } else {
+            work = n0_only ? p->wreal : y;
+            const long long nt = tb.nt;
+            { Span sp_(p, "dst_x", s); CK(qbvm::launch_dst<double>(in, work, tb.n[0], p->lp[0], nt * ny * nz, 1, tb.tw_s[0], tb.sn_s[0], s)); }
+            { Span sp_(p, "dst_y", s); CK(qbvm::launch_dst<double>(work, work, tb.n[1], p->lp[1], nt * nz, nx, tb.tw_s[1], tb.sn_s[1], s)); }
+            launches += 2;
+            if (tb.dim == 3) {
+                { Span sp_(p, "dst_z", s); CK(qbvm::launch_dst<double>(work, work, tb.n[2], p->lp[2], nt, nx * ny, tb.tw_s[2], tb.sn_s[2], s)); }
+                ++launches;
+            }
+            { Span sp_(p, "time_solve", s); CK(qbvm::launch_time_solve<double>(work, y, tb, tb.tau * cn, 0, n0_only, s)); }
+            ++launches;
+        }
+        // inverse DST (the (2/M) factors are in the time-solve constant)
+        const long long lev = n0_only ? 1 : tb.nt;
+        { Span sp_(p, "dst_x", s); CK(qbvm::launch_dst<double>(y, y, tb.n[0], p->lp[0], lev * ny * nz, 1, tb.tw_s[0], tb.sn_s[0], s)); }
+        { Span sp_(p, "dst_y", s); CK(qbvm::launch_dst<double>(y, y, tb.n[1], p->lp[1], lev * nz, nx, tb.tw_s[1], tb.sn_s[1], s)); }
+        launches += 2;
+        if (tb.dim == 3) {
+            { Span sp_(p, "dst_z", s); CK(qbvm::launch_dst<double>(y, y, tb.n[2], p->lp[2], lev, nx * ny, tb.tw_s[2], tb.sn_s[2], s)); }
+            ++launches;
+        }
+    }
+    p->kernels_per_solve = launches;
+    return QBVM_OK;
+}
+
+}  // namespace
+
+// ------------------------------------------------------------------ C ABI
+
+extern "C" {
+
+int qbvm_version(void) { return 100; }
+
+const char* qbvm_strerror(int code) {
+    switch (code) {
+        case QBVM_OK: return "success";
+        case QBVM_ERR_BAD_ARG: return "invalid argument or descriptor";
+        case QBVM_ERR_OOM: return "out of memory";
+        case QBVM_ERR_NONFINITE: return "non-finite value in input or result";
+        case QBVM_ERR_DIVERGED: return "FP32 iterative refinement did not contract";
+        case QBVM_ERR_TIMEOUT: return "a bounded device wait gave up";
+        case QBVM_ERR_CUDA: return "CUDA runtime error";
+        case QBVM_ERR_UNSUPPORTED: return "size not implemented by the kernels";
+        default: return "unknown status code";
+    }
+}
+
+int qbvm_plan(const qbvm_desc* desc, qbvm_plan_t** out) {
+    if (!out) return QBVM_ERR_BAD_ARG;
+    *out = nullptr;
+    int rc = validate(desc);
+    if (rc) return rc;
+    qbvm_plan_t* p = new (std::nothrow) struct qbvm_plan();
+    if (!p) return QBVM_ERR_OOM;
+    p->d = *desc;
+    const qbvm_desc& d = p->d;
+    Tables& tb = p->tb;
+    tb.dim = d.dim;
+    tb.nt = d.nt;
+    tb.lnt = ilog2(d.nt);
+    tb.Nx = 1;
+    for (int i = 0; i < 3; ++i) {
+        tb.n[i] = i < d.dim ? d.m[i] - 1 : 1;
+        p->h[i] = i < d.dim ? d.L / d.m[i] : 1.0;
+        p->h2inv[i] = i < d.dim ? 1.0 / (p->h[i] * p->h[i]) : 0.0;
+        tb.Nx *= tb.n[i];
+    }
+    p->tau = d.T / (d.nt - 1);
+    p->alpha = d.alpha > 0 ? d.alpha : (d.form == QBVM_FORM_PQ ? d.delta : p->tau * d.delta);
+    p->omega = d.form == QBVM_FORM_PQ ? -1.0 / p->alpha : -p->tau / p->alpha;
+    tb.tau = p->tau;
+    tb.omega = p->omega;
+    if (!(std::isfinite(p->alpha) && p->alpha > 0 && std::isfinite(p->omega))) {
+        delete p;
+        return QBVM_ERR_BAD_ARG;
+    }
+    if (cudaGetDevice(&p->dev) != cudaSuccess) {
+        cudaGetLastError();
+        delete p;
+        return QBVM_ERR_CUDA;
+    }
+
+    // ---- FP64 tables of Section 3.3 ----
+    const int nt = d.nt, H = nt / 2;
+    const double mag = std::fabs(p->omega);
+    // principal root of omega < 0: gamma = |omega|^{1/nt} exp(i pi/nt)
+    std::vector<double2> tw64, gpow(H), gipw(H), ak(H), bk;
+    std::vector<float2> tw32;
+    roots(H, tw64, tw32);
+    const double scale1d = d.dim == 1 ? p->h[0] * p->h[0] / nt : 1.0;
+    for (int t = 0; t < H; ++t) {
+        double r = std::pow(mag, (double)t / nt);
+        double a = M_PI * ((double)t / nt);
+        gpow[t] = make_double2(scale1d * r * std::cos(a), scale1d * r * std::sin(a));
+        double ri = 2.0 * std::pow(mag, -(double)t / nt);
+        gipw[t] = make_double2(ri * std::cos(a), -ri * std::sin(a));
+    }
+    tb.rho_h = std::sqrt(mag);
+    tb.rho_hinv = 1.0 / tb.rho_h;
+    const double g1 = std::pow(mag, 1.0 / nt);
+    for (int m = 0; m < H; ++m) {
+        double a = M_PI * ((4.0 * m + 1.0) / nt);        // arg(gamma theta^{2m})
+        ak[m] = make_double2(1.0 - g1 * std::cos(a), -g1 * std::sin(a));
+    }
+    rc = upload(p, &tb.tw_t, tw64);
+    if (!rc) rc = upload(p, &tb.tw_t32, tw32);
+    if (!rc) rc = upload(p, &tb.gpow, gpow);
+    if (!rc) rc = upload(p, &tb.gipw, gipw);
+    if (!rc) rc = upload(p, &tb.ak, ak);
+    if (!rc && d.dim == 1) {
+        bk.resize(H);
+        const double h2 = p->h[0] * p->h[0];
+        for (int m = 0; m < H; ++m)
+            bk[m] = make_double2(h2 * ak[m].x / p->tau + 2.0, h2 * ak[m].y / p->tau);
+        rc = upload(p, &tb.bk, bk);
+    }
+    if (!rc && d.dim > 1) {
+        // Dirichlet eigenvalues (4/h^2) sin^2(k pi/(2M)) per axis, summed per mode
+        std::vector<std::vector<double>> lam(3);
+        for (int i = 0; i < 3; ++i) {
+            lam[i].assign(tb.n[i], 0.0);
+            if (i < d.dim)
+                for (int k = 1; k <= tb.n[i]; ++k) {
+                    double s = std::sin(M_PI * k / (2.0 * d.m[i]));
+                    lam[i][k - 1] = 4.0 * p->h2inv[i] * s * s;
+                }
+        }
+        std::vector<double> lt((size_t)tb.Nx);
+        size_t idx = 0;
+        for (int z = 0; z < tb.n[2]; ++z)
+            for (int yy = 0; yy < tb.n[1]; ++yy)
+                for (int x = 0; x < tb.n[0]; ++x)
+                    lt[idx++] = p->tau * (lam[0][x] + lam[1][yy] + lam[2][z]);
+        rc = upload(p, &tb.lamtau, lt);
+        for (int i = 0; i < d.dim && !rc; ++i) {
+            const int M = d.m[i];
+            p->lp[i] = ilog2(M);
+            tb.lpd[i] = p->lp[i];
+            std::vector<double2> s64;
+            std::vector<float2> s32;
+            roots(M, s64, s32);
+            rc = upload(p, &tb.tw_s[i], s64);
+            if (!rc) rc = upload(p, &tb.tw_s32[i], s32);
+            std::vector<double> sn(M / 2 + 2, 0.0);
+            std::vector<float> sn32(M / 2 + 2, 0.f);
+            for (int j = 0; j <= M / 2; ++j) {
+                sn[j] = std::sin(M_PI * j / M);
+                sn32[j] = (float)sn[j];
+            }
+            if (!rc) rc = upload(p, &tb.sn_s[i], sn);
+            if (!rc) rc = upload(p, &tb.sn_s32[i], sn32);
+        }
+    }
+    // ---- workspace ----
+    const size_t total = (size_t)tb.Nx * nt;
+    if (!rc && d.dim == 1) {
+        rc = dalloc(p, &p->wk, total);
+        if (!rc) rc = dalloc(p, &p->wcp, total);
+    }
+    if (!rc && d.dim > 1) rc = dalloc(p, &p->ghat, (size_t)tb.Nx);
+    if (!rc) {
+        p->nres = qbvm::residual_blocks(tb);
+        rc = dalloc(p, &p->partials, (size_t)2 * p->nres);
+        if (!rc) rc = dalloc(p, &p->sums, 2);
+    }
+    if (rc) {
+        destroy_plan(p);
+        return rc;
+    }
+    *out = p;
+    return QBVM_OK;
+}
+
+int qbvm_plan_info(const qbvm_plan_t* p, qbvm_info* out) {
+    if (!p || !out) return QBVM_ERR_BAD_ARG;
+    out->alpha = p->alpha;
+    out->omega = p->omega;
+    out->tau = p->tau;
+    out->unknowns = p->tb.Nx * p->tb.nt;
+    out->workspace_bytes = p->ws_bytes;
+    out->last_refine_iters = p->last_iters;
+    out->last_rel_residual = p->last_relres;
+    out->kernels_per_solve = p->kernels_per_solve;
+    return QBVM_OK;
+}
+
+int qbvm_profile_enable(qbvm_plan_t* p, int on) {
+    if (!p) return QBVM_ERR_BAD_ARG;
+    for (auto& m : p->marks) {
+        p->event_pool.push_back(m.a);
+        p->event_pool.push_back(m.b);
+    }
+    p->marks.clear();
+    p->profiling = on != 0;
+    return QBVM_OK;
+}
+
+int qbvm_profile_read(qbvm_plan_t* p, qbvm_kernel_stat* out, int capacity, int* count) {
+    if (!p || !count || (capacity > 0 && !out)) return QBVM_ERR_BAD_ARG;
+    int n = 0;
+    int rc = QBVM_OK;
+    for (auto& m : p->marks) {
+        float ms = 0.f;
+        if (cudaEventSynchronize(m.b) != cudaSuccess || cudaEventElapsedTime(&ms, m.a, m.b) != cudaSuccess) {
+            cudaGetLastError();
+            rc = QBVM_ERR_CUDA;
+        }
+        int i = 0;
+        while (i < n && std::strncmp(out[i].name, m.name, sizeof(out[i].name)) != 0) ++i;
+        if (i == n) {
+            if (n >= capacity) continue;
+            std::memset(&out[n], 0, sizeof(out[n]));
+            std::strncpy(out[n].name, m.name, sizeof(out[n].name) - 1);
+            ++n;
+        }
+        out[i].launches += 1;
+        out[i].total_ms += ms;
+        p->event_pool.push_back(m.a);
+        p->event_pool.push_back(m.b);
+    }
+    p->marks.clear();
+    *count = n;
+    return rc;
+}
+
+int qbvm_destroy(qbvm_plan_t* p) {
+    destroy_plan(p);
+    return QBVM_OK;
+}
+
+static int ensure_stage(qbvm_plan_t* p) {
+    const size_t total = (size_t)p->tb.Nx * p->tb.nt;
+    int rc = QBVM_OK;
+    if (!p->stage_in) rc = dalloc(p, &p->stage_in, total);
+    if (!rc && !p->stage_out) rc = dalloc(p, &p->stage_out, total);
+    return rc;
+}
+
+static int ensure_wreal(qbvm_plan_t* p) {
+    if (p->wreal) return QBVM_OK;
+    return dalloc(p, &p->wreal, (size_t)p->tb.Nx * p->tb.nt);
+}
+
+static int solve_dev(qbvm_plan_t* p, const double* in, double* y, int n0_only, cudaStream_t s) {
+    if (p->tb.dim > 1 && n0_only && p->d.rhs_kind == QBVM_RHS_GENERAL) {
+        int rc = ensure_wreal(p);
+        if (rc) return rc;
+    }
+    if (p->d.precision == QBVM_FP64) return solve_fp64_dev(p, in, y, n0_only, s);
+    return QBVM_ERR_UNSUPPORTED;
+}
+
+int qbvm_solve(qbvm_plan_t* p, const double* g_or_F, double* y, int n0_only, void* stream) {
+    if (!p || !g_or_F || !y) return QBVM_ERR_BAD_ARG;
+    cudaStream_t s = static_cast<cudaStream_t>(stream);
+    const int kin = ptr_kind(g_or_F), kout = ptr_kind(y);
+    if (kin != kout) return QBVM_ERR_BAD_ARG;
+    if (kin == KIND_DEV) return solve_dev(p, g_or_F, y, n0_only, s);
+    // host pointers: stage through plan buffers
+    int rc = ensure_stage(p);
+    if (rc) return rc;
+    const size_t nin = (size_t)p->tb.Nx * (p->d.rhs_kind == QBVM_RHS_DELTA ? 1 : p->tb.nt);
+    const size_t nout = (size_t)p->tb.Nx * (n0_only ? 1 : p->tb.nt);
+    CK(cudaMemcpyAsync(p->stage_in, g_or_F, nin * sizeof(double), cudaMemcpyHostToDevice, s));
+    rc = solve_dev(p, p->stage_in, p->stage_out, n0_only, s);
+    if (rc) return rc;
+    CK(cudaMemcpyAsync(y, p->stage_out, nout * sizeof(double), cudaMemcpyDeviceToHost, s));
+    CK(cudaStreamSynchronize(s));
+    return QBVM_OK;
+}
+
+int qbvm_residual(qbvm_plan_t* p, const double* y, const double* g_or_F, double* rel_norm_out, void* stream) {
+    if (!p || !y || !g_or_F || !rel_norm_out) return QBVM_ERR_BAD_ARG;
+    cudaStream_t s = static_cast<cudaStream_t>(stream);
+    const int ky = ptr_kind(y), kf = ptr_kind(g_or_F);
+    if (ky != kf) return QBVM_ERR_BAD_ARG;
+    const int delta = p->d.rhs_kind == QBVM_RHS_DELTA;
+    const double* dy = y;
+    const double* df = g_or_F;
+    if (ky == KIND_HOST) {
+        int rc = ensure_stage(p);
+        if (rc) return rc;
+        const size_t total = (size_t)p->tb.Nx * p->tb.nt;
+        const size_t nin = delta ? (size_t)p->tb.Nx : total;
+        CK(cudaMemcpyAsync(p->stage_out, y, total * sizeof(double), cudaMemcpyHostToDevice, s));
+        CK(cudaMemcpyAsync(p->stage_in, g_or_F, nin * sizeof(double), cudaMemcpyHostToDevice, s));
+        dy = p->stage_out;
+        df = p->stage_in;
+    }
+    { Span sp_(p, "residual", s); CK(qbvm::launch_residual(dy, df, delta, p->tb, p->h2inv, p->partials, p->nres, p->sums, nullptr, s)); }
+    double h[2] = {0, 0};
+    CK(cudaMemcpyAsync(h, p->sums, sizeof(h), cudaMemcpyDeviceToHost, s));
+    CK(cudaStreamSynchronize(s));
+    if (!std::isfinite(h[0]) || !std::isfinite(h[1])) return QBVM_ERR_NONFINITE;
+    *rel_norm_out = h[1] > 0 ? std::sqrt(h[0] / h[1]) : std::sqrt(h[0]);
+    return QBVM_OK;
+}
+
+}  // extern "C"

@@ -1,0 +1,84 @@
+"""The C ABI library: it builds for sm_103a, loads, exports every entry point
+declared in include/*.h, and rejects invalid descriptors before touching a GPU."""
+import glob
+import os
+import re
+
+import pytest
+
+import paper_2107_06381_gb300 as Q
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+
+
+def _declared_functions():
+    names = set()
+    for h in glob.glob(os.path.join(ROOT, "include", "*.h")):
+        text = open(h).read()
+        text = re.sub(r"/\*.*?\*/", "", text, flags=re.S)
+        for m in re.finditer(r"^\s*(?:const\s+)?[A-Za-z_][A-Za-z0-9_]*\s*\**\s+\**\s*(qbvm_[A-Za-z0-9_]+)\s*\(",
+                             text, flags=re.M):
+            names.add(m.group(1))
+    return sorted(names)
+
+
+@pytest.fixture(scope="module")
+def lib():
+    Q.build_library()
+    return Q.load_library()
+
+
+def test_header_declares_the_boundary():
+    names = _declared_functions()
+    for required in ("qbvm_plan", "qbvm_solve", "qbvm_residual", "qbvm_destroy", "qbvm_strerror"):
+        assert required in names
+
+
+def test_library_exports_every_declared_symbol(lib):
+    for name in _declared_functions():
+        assert hasattr(lib, name), name
+
+
+def test_version_and_strerror(lib):
+    assert Q.qbvm_version() >= 100
+    assert Q.qbvm_strerror(0) == "success"
+    assert "argument" in Q.qbvm_strerror(-1)
+    assert Q.qbvm_strerror(12345) == "unknown status code"
+
+
+BAD = [
+    dict(dim=0), dict(dim=4), dict(m=(1, 8, 8)), dict(nt=1), dict(T=0.0), dict(T=float("nan")),
+    dict(L=-1.0), dict(form=2), dict(precision=5), dict(rhs_kind=3),
+    dict(alpha=0.0, delta=0.0), dict(alpha=-1.0, delta=-1.0), dict(alpha=float("inf")),
+]
+
+
+@pytest.mark.parametrize("change", BAD, ids=lambda c: ",".join(f"{k}={v}" for k, v in c.items()))
+def test_bad_descriptors_are_rejected_without_a_gpu(lib, change):
+    args = dict(dim=2, m=(16, 16, 1), L=1.0, T=0.1, nt=16, form=0, alpha=1e-3, delta=0.0, precision=0, rhs_kind=0)
+    args.update(change)
+    desc = Q.make_desc(args["dim"], args["m"], args["L"], args["T"], args["nt"], args["form"], args["alpha"],
+                       args["delta"], args["precision"], args["rhs_kind"])
+    with pytest.raises(Q.QbvmError) as ei:
+        Q.qbvm_plan(desc)
+    assert ei.value.code == -1
+
+
+@pytest.mark.parametrize("change", [dict(nt=24), dict(nt=2048), dict(m=(24, 16, 1)), dict(m=(2048, 16, 1))],
+                         ids=["nt24", "nt2048", "m24", "m2048"])
+def test_unsupported_sizes(lib, change):
+    args = dict(dim=2, m=(16, 16, 1), nt=16)
+    args.update(change)
+    desc = Q.make_desc(2, args["m"], 1.0, 0.1, args["nt"], 0, 1e-3)
+    with pytest.raises(Q.QbvmError) as ei:
+        Q.qbvm_plan(desc)
+    assert ei.value.code == -7
+
+
+def test_null_arguments(lib):
+    import ctypes
+    assert lib.qbvm_plan(None, None) == -1
+    assert lib.qbvm_solve(None, None, None, 0, None) == -1
+    out = ctypes.c_double()
+    assert lib.qbvm_residual(None, None, None, ctypes.byref(out), None) == -1
+    assert lib.qbvm_destroy(None) == 0

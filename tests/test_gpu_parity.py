@@ -1,0 +1,195 @@
+"""Parity of the CUDA path (through the C ABI) with the CPU FP64 oracle.
+
+Tolerance: relative L2 error <= 1e-10 against the oracle in FP64 (the accuracy
+the FP64 solve is held to).  Small cases span several tiles and a ragged
+tail; full-size cases compare sampled time levels the oracle computes one by
+one.
+"""
+import math
+
+import numpy as np
+import pytest
+
+import bhcp_inputs as bi
+import oracle as O
+
+pytestmark = pytest.mark.gpu
+torch = pytest.importorskip("torch")
+if not torch.cuda.is_available():
+    pytest.skip("needs a CUDA GPU", allow_module_level=True)
+
+import paper_2107_06381_gb300 as Q  # noqa: E402
+
+TOL = 1e-10
+
+
+@pytest.fixture(scope="module", autouse=True)
+def _lib():
+    Q.build_library()
+    Q.load_library()
+
+
+def gpu_solve(grid, form, alpha, rhs, rhs_kind, n0_only=False, precision=Q.FP64, host=False):
+    with Q.Plan(grid.dim, grid.M, grid.L, grid.T, grid.nt, form, alpha, 0.0, precision, rhs_kind) as plan:
+        nout = grid.Nx * (1 if n0_only else grid.nt)
+        if host:
+            inp = np.ascontiguousarray(rhs, dtype=np.float64).ravel()
+            out = np.zeros(nout)
+            plan.solve(inp, out, n0_only)
+            res = out
+        else:
+            inp = torch.as_tensor(np.ascontiguousarray(rhs).ravel(), dtype=torch.float64).cuda()
+            out = torch.zeros(nout, dtype=torch.float64, device="cuda")
+            plan.solve(inp, out, n0_only)
+            torch.cuda.synchronize()
+            res = out.cpu().numpy()
+    shape = ((1,) if n0_only else (grid.nt,)) + grid.shape
+    return res.reshape(shape)
+
+
+def oracle_solve(grid, form, alpha, F):
+    """Sparse LU of the assembled system (the oracle of record) on small grids;
+    beyond that the sine-basis oracle, which the CPU suite pins to LU."""
+    if grid.unknowns <= 5000:
+        return O.solve_sparse_lu(grid, form, alpha, F)
+    return O.solve_spectral(grid, form, alpha, F)
+
+
+SMALL = [
+    bi.Grid(1, (2,), 1.0, 0.1, 2),          # one interior point, N = 1
+    bi.Grid(1, (5,), 1.0, 0.1, 4),
+    bi.Grid(1, (64,), 1.0, 0.1, 64),        # C1 grid
+    bi.Grid(1, (100,), math.pi, 1.0, 32),   # ragged tile tail
+    bi.Grid(1, (301,), 1.0, 0.2, 128),
+    bi.Grid(2, (4, 4), 1.0, 0.1, 2),
+    bi.Grid(2, (8, 16), 1.0, 0.1, 8),       # unequal axes
+    bi.Grid(2, (32, 32), 1.0, 0.1, 32),
+    bi.Grid(2, (64, 64), math.pi, 1.0, 16),
+    bi.Grid(3, (4, 8, 4), 1.0, 0.05, 4),
+    bi.Grid(3, (16, 16, 16), 1.0, 0.05, 16),
+]
+
+
+@pytest.mark.parametrize("grid", SMALL, ids=lambda g: f"d{g.dim}-M{'x'.join(map(str, g.M))}-nt{g.nt}")
+@pytest.mark.parametrize("form", [Q.FORM_PQ, Q.FORM_PM])
+def test_general_rhs_matches_oracle(grid, form):
+    alpha = 1e-3 if form == Q.FORM_PQ else 1e-3 * grid.tau
+    F = bi.random_general_rhs(grid, seed=7)
+    want = oracle_solve(grid, form, alpha, F)
+    got = gpu_solve(grid, form, alpha, F, Q.RHS_GENERAL)
+    assert O.rel_l2(got, want) <= TOL
+
+
+@pytest.mark.parametrize("grid", SMALL, ids=lambda g: f"d{g.dim}-M{'x'.join(map(str, g.M))}-nt{g.nt}")
+@pytest.mark.parametrize("form", [Q.FORM_PQ, Q.FORM_PM])
+def test_delta_rhs_matches_oracle(grid, form):
+    g = bi.random_general_rhs(grid, seed=8)[0]
+    alpha = 2e-4 if form == Q.FORM_PQ else 5e-2
+    want = oracle_solve(grid, form, alpha, O.delta_rhs(grid, form, alpha, g))
+    got = gpu_solve(grid, form, alpha, g, Q.RHS_DELTA)
+    assert O.rel_l2(got, want) <= TOL
+
+
+@pytest.mark.parametrize("form", [Q.FORM_PQ, Q.FORM_PM])
+def test_c1_workload(form):
+    """1D, 63 interior points x 64 levels, alpha by the Section 5 rule."""
+    p = bi.make_c1()
+    grid = p.grid
+    alpha = O.alpha_apriori(form, p.delta, grid.tau)
+    want = O.solve_sparse_lu(grid, form, alpha, O.delta_rhs(grid, form, alpha, p.g_delta))
+    got = gpu_solve(grid, form, alpha, p.g_delta, Q.RHS_DELTA)
+    assert O.rel_l2(got, want) <= TOL
+    # the reconstruction error is the oracle's
+    assert abs(bi.discrete_l2(got[0] - p.z0, grid) - bi.discrete_l2(want[0] - p.z0, grid)) < 1e-9
+
+
+@pytest.mark.parametrize("alpha", [1e-1, 1e-4, 1e-7])
+def test_alpha_extremes_1d(alpha):
+    grid = bi.Grid(1, (128,), 1.0, 0.1, 128)
+    g = bi.random_general_rhs(grid, seed=9)[0]
+    want = O.solve_spectral(grid, Q.FORM_PQ, alpha, O.delta_rhs(grid, Q.FORM_PQ, alpha, g))
+    got = gpu_solve(grid, Q.FORM_PQ, alpha, g, Q.RHS_DELTA)
+    assert O.rel_l2(got, want) <= TOL
+
+
+@pytest.mark.parametrize("grid", [bi.Grid(1, (64,), 1.0, 0.1, 64), bi.Grid(2, (32, 16), 1.0, 0.1, 16),
+                                  bi.Grid(3, (8, 8, 8), 1.0, 0.1, 8)],
+                         ids=["1d", "2d", "3d"])
+@pytest.mark.parametrize("rhs_kind", [Q.RHS_DELTA, Q.RHS_GENERAL])
+def test_n0_only_and_host_pointers(grid, rhs_kind):
+    alpha = 1e-3
+    F = bi.random_general_rhs(grid, seed=10)
+    rhs = F[0] if rhs_kind == Q.RHS_DELTA else F
+    full = gpu_solve(grid, Q.FORM_PQ, alpha, rhs, rhs_kind)
+    y0 = gpu_solve(grid, Q.FORM_PQ, alpha, rhs, rhs_kind, n0_only=True)
+    np.testing.assert_allclose(y0[0], full[0], rtol=0, atol=1e-12 * np.abs(full).max())
+    host = gpu_solve(grid, Q.FORM_PQ, alpha, rhs, rhs_kind, host=True)
+    np.testing.assert_array_equal(host, full)
+
+
+def test_inplace_general_rhs():
+    grid = bi.Grid(2, (16, 16), 1.0, 0.1, 16)
+    F = bi.random_general_rhs(grid, seed=11)
+    want = gpu_solve(grid, Q.FORM_PQ, 1e-3, F, Q.RHS_GENERAL)
+    with Q.Plan(2, grid.M, grid.L, grid.T, grid.nt, Q.FORM_PQ, 1e-3, 0.0, Q.FP64, Q.RHS_GENERAL) as plan:
+        buf = torch.as_tensor(F.ravel(), dtype=torch.float64).cuda()
+        plan.solve(buf, buf)
+        torch.cuda.synchronize()
+        np.testing.assert_array_equal(buf.cpu().numpy().reshape(grid.full_shape), want)
+
+
+@pytest.mark.parametrize("grid", [bi.Grid(1, (50,), 1.0, 0.1, 16), bi.Grid(2, (16, 8), 1.0, 0.1, 8),
+                                  bi.Grid(3, (8, 4, 8), 1.0, 0.1, 4)], ids=["1d", "2d", "3d"])
+@pytest.mark.parametrize("rhs_kind", [Q.RHS_DELTA, Q.RHS_GENERAL])
+def test_residual_matches_oracle(grid, rhs_kind):
+    alpha = 3e-3
+    F = bi.random_general_rhs(grid, seed=12)
+    rhs = F[0] if rhs_kind == Q.RHS_DELTA else F
+    Ffull = O.delta_rhs(grid, Q.FORM_PM, alpha, F[0]) if rhs_kind == Q.RHS_DELTA else F
+    y = bi.random_general_rhs(grid, seed=13)          # an arbitrary iterate
+    want = O.rel_residual(grid, Q.FORM_PM, alpha, y, Ffull)
+    with Q.Plan(grid.dim, grid.M, grid.L, grid.T, grid.nt, Q.FORM_PM, alpha, 0.0, Q.FP64, rhs_kind) as plan:
+        yd = torch.as_tensor(y.ravel(), dtype=torch.float64).cuda()
+        fd = torch.as_tensor(np.ascontiguousarray(rhs).ravel(), dtype=torch.float64).cuda()
+        got = plan.residual(yd, fd)
+        # and the solve's own residual is at rounding level
+        out = torch.zeros_like(yd)
+        plan.solve(fd, out)
+        small = plan.residual(out, fd)
+    assert abs(got - want) <= 1e-12 * want
+    assert small < 1e-10
+
+
+# --------------------------------------------------------------- full sizes
+
+@pytest.mark.parametrize("form", [Q.FORM_PQ, Q.FORM_PM])
+def test_c2_full_size_delta(form):
+    """2D 255^2 x 256, alpha by the a-priori rule: every level against the oracle."""
+    p = bi.make_c2()
+    grid = p.grid
+    alpha = O.alpha_apriori(form, p.delta, grid.tau)
+    want = O.solve_spectral(grid, form, alpha, O.rhs_block0(form, alpha, grid.tau, p.g_delta))
+    got = gpu_solve(grid, form, alpha, p.g_delta, Q.RHS_DELTA)
+    assert O.rel_l2(got, want) <= TOL
+
+
+def test_c2_full_size_general_rhs():
+    p = bi.make_c2()
+    grid = p.grid
+    alpha = O.alpha_apriori(Q.FORM_PQ, p.delta, grid.tau)
+    F = bi.random_general_rhs(grid, seed=14)
+    want = O.solve_spectral(grid, Q.FORM_PQ, alpha, F)
+    got = gpu_solve(grid, Q.FORM_PQ, alpha, F, Q.RHS_GENERAL)
+    assert O.rel_l2(got, want) <= TOL
+
+
+def test_c3_full_size_sampled_levels():
+    """3D 127^3 x 128 (delta rhs): sampled time levels against the oracle."""
+    p = bi.make_c3()
+    grid = p.grid
+    alpha = O.alpha_apriori(Q.FORM_PQ, p.delta, grid.tau)
+    levels = [0, 1, 63, 127]
+    want = O.solve_spectral(grid, Q.FORM_PQ, alpha, O.rhs_block0(Q.FORM_PQ, alpha, grid.tau, p.g_delta),
+                            levels=levels)
+    got = gpu_solve(grid, Q.FORM_PQ, alpha, p.g_delta, Q.RHS_DELTA)[levels]
+    assert O.rel_l2(got, want) <= TOL
