@@ -160,6 +160,35 @@ typedef struct qbvm_kernel_stat {
 int qbvm_profile_enable(qbvm_plan_t* plan, int on);
 int qbvm_profile_read(qbvm_plan_t* plan, qbvm_kernel_stat* out, int capacity, int* count);
 
+/* qbvm_residual_noalloc -- the value qbvm_residual returns, ||f - A y||_2 /
+ * ||f||_2 in FP64, for callers that cannot allocate device memory: no plan is
+ * needed and the call makes no cudaMalloc/cudaFree or other allocating call.
+ * Such callers include code whose device memory is entirely reserved by
+ * another allocator or memory pool (a framework's caching allocator holding
+ * the HBM), and monitoring or real-time loops that must not change the
+ * device-memory footprint or pay for cudaMalloc/cudaFree, which may
+ * synchronise the device.  The paper has no counterpart to this entry point.
+ *
+ * `desc` is validated as in qbvm_plan (BAD_ARG / UNSUPPORTED alike); y and
+ * g_or_F must be DEVICE pointers laid out as for qbvm_residual (host pointers
+ * would need staging memory: BAD_ARG).  The result is written to
+ * *rel_norm_out after `stream` has been synchronised.
+ *
+ * Scratch: a static device array of 8194 doubles (64 KiB) that every GPU
+ * loading this library holds until the process exits: partial sums for at
+ * most 4096 residual blocks plus two totals.  The residual kernel strides over
+ * the unknowns, so the scratch need does not grow with the problem; a launch
+ * that would need more than 4096 blocks is rejected with UNSUPPORTED.  All
+ * calls on a device share the array and each call overwrites what it reads,
+ * so nothing carries over between calls -- but calls that overlap on the GPU
+ * (other streams, other host threads) race on it and must be serialised by
+ * the caller.  The first call on each device looks up the array's device
+ * address (cudaGetSymbolAddress, with that device current) and caches it;
+ * make that first call before any stream capture.
+ * Errors: BAD_ARG, UNSUPPORTED, NONFINITE, CUDA. */
+int qbvm_residual_noalloc(const qbvm_desc* desc, const double* y, const double* g_or_F,
+                          double* rel_norm_out, void* stream);
+
 /* qbvm_destroy -- free the plan and everything it owns (NULL is accepted). */
 int qbvm_destroy(qbvm_plan_t* plan);
 

@@ -16,7 +16,7 @@ from .build import LIB_PATH, build as build_library
 __all__ = [
     "QbvmDesc", "QbvmInfo", "QbvmError", "load_library",
     "qbvm_plan", "qbvm_solve", "qbvm_residual", "qbvm_plan_info", "qbvm_destroy",
-    "qbvm_profile_enable", "qbvm_profile_read",
+    "qbvm_profile_enable", "qbvm_profile_read", "qbvm_residual_noalloc",
     "qbvm_strerror", "qbvm_version", "Plan",
     "FORM_PQ", "FORM_PM", "FP64", "FP32_REFINE", "RHS_DELTA", "RHS_GENERAL",
 ]
@@ -84,6 +84,8 @@ def load_library(path: str | None = None) -> ctypes.CDLL:
     lib.qbvm_profile_enable.restype = ip
     lib.qbvm_profile_read.argtypes = [vp, ctypes.POINTER(QbvmKernelStat), ip, ctypes.POINTER(ip)]
     lib.qbvm_profile_read.restype = ip
+    lib.qbvm_residual_noalloc.argtypes = [ctypes.POINTER(QbvmDesc), vp, vp, ctypes.POINTER(dp), vp]
+    lib.qbvm_residual_noalloc.restype = ip
     lib.qbvm_version.argtypes = []
     lib.qbvm_version.restype = ip
     if path is None:
@@ -156,6 +158,14 @@ def qbvm_residual(plan: int, y, g_or_F, stream=None) -> float:
     out = ctypes.c_double()
     _check(load_library().qbvm_residual(plan, _ptr(y), _ptr(g_or_F), ctypes.byref(out),
                                         _stream(stream, y, g_or_F)), "qbvm_residual")
+    return out.value
+
+
+def qbvm_residual_noalloc(desc: QbvmDesc, y, g_or_F, stream=None) -> float:
+    """Plan-free residual that allocates no device memory (device arrays only)."""
+    out = ctypes.c_double()
+    _check(load_library().qbvm_residual_noalloc(ctypes.byref(desc), _ptr(y), _ptr(g_or_F), ctypes.byref(out),
+                                                _stream(stream, y, g_or_F)), "qbvm_residual_noalloc")
     return out.value
 
 

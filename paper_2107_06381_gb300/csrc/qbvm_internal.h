@@ -62,3 +62,9 @@ cudaError_t launch_residual(const double* y, const double* f, int delta_rhs, con
 int residual_blocks(const Tables& tb);
 
 }  // namespace qbvm
+
+struct qbvm_desc;
+namespace qbvm {
+// The descriptor checks of qbvm_plan (status code; needs no GPU).
+int validate_desc(const qbvm_desc* d);
+}  // namespace qbvm

@@ -234,6 +234,8 @@ int solve_fp64_dev(qbvm_plan_t* p, const double* in, double* y, int n0_only, cud
 
 }  // namespace
 
+int qbvm::validate_desc(const qbvm_desc* d) { return validate(d); }
+
 // ------------------------------------------------------------------ C ABI
 
 extern "C" {
