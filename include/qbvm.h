@@ -49,7 +49,8 @@ extern "C" {
 #define QBVM_ERR_BAD_ARG     -1   /* invalid descriptor or argument            */
 #define QBVM_ERR_OOM         -2   /* device or host allocation failed          */
 #define QBVM_ERR_NONFINITE   -3   /* NaN/Inf in the input or the result        */
-#define QBVM_ERR_DIVERGED    -4   /* FP32 refinement did not contract          */
+#define QBVM_ERR_DIVERGED    -4   /* FP32 refinement stalled above 1e-10 or hit
+                                     its iteration cap above the tolerance     */
 #define QBVM_ERR_TIMEOUT     -5   /* a bounded device wait gave up             */
 #define QBVM_ERR_CUDA        -6   /* a CUDA runtime call failed                */
 #define QBVM_ERR_UNSUPPORTED -7   /* size outside what the kernels implement   */
@@ -188,6 +189,78 @@ int qbvm_profile_read(qbvm_plan_t* plan, qbvm_kernel_stat* out, int capacity, in
  * Errors: BAD_ARG, UNSUPPORTED, NONFINITE, CUDA. */
 int qbvm_residual_noalloc(const qbvm_desc* desc, const double* y, const double* g_or_F,
                           double* rel_norm_out, void* stream);
+
+/* ------------------------------------------------------------------------
+ * Batched regularisation-parameter sweep.  Many PinT-QBVM / PinT-MQBVM
+ * instances of uneven size (1D or 2D, delta right-hand side f^0 = -omega g/tau),
+ * each solved for n_alpha values of alpha log-spaced around the a-priori rule
+ * of Section 5 (alpha_rule = delta for PQ, tau*delta for PM):
+ *     alpha_i = alpha_rule * 10^(log10_lo + (log10_hi - log10_lo) i/(n_alpha-1)).
+ * For every (instance, alpha) the sweep forms y^0 in the sine basis by the
+ * three steps of eq. 3.8 (Step (c) evaluated at t = 0), the discrepancy
+ * ||y^N - g||, which the first block row of eq. 3.3/3.6 gives as
+ * alpha ||(I - tau Lap) y^0|| (PQ) or (alpha/tau) ||(I - tau Lap) y^0|| (PM),
+ * and, when z0 is given, the error ||y^0 - z0|| (grid-weighted L2 norms).
+ * It then picks alpha by the discrepancy principle -- the largest alpha with
+ * ||y^N - g|| <= tau_dp * delta, else the one with the smallest discrepancy --
+ * and writes y^0 at that alpha (FP64) to `y0` when given.
+ * All of it runs as ONE persistent kernel launch, captured once into a CUDA
+ * graph and replayed by every qbvm_sweep_run; its launch shape (modes per
+ * thread, CTAs per SM) is picked by qbvm_sweep_autotune.
+ * Supported: dim 1 or 2; m a power of two in [4, 2048]; nt a power of two in
+ * [2, 1024]; n_alpha in [1, 64].  precision: QBVM_FP64 (every stage in FP64)
+ * or QBVM_FP32_REFINE (the alpha scan in FP32, the picked alpha's y^0 in FP64).
+ * The sweep holds device copies of its tables; g, z0 and y0 are caller-owned
+ * device arrays that must stay valid while the sweep is used. */
+typedef struct qbvm_sweep_instance {
+    int    dim;
+    int    m[3];
+    double L;
+    double T;
+    int    nt;
+    int    form;
+    double delta;          /* noise level of g (bound of the discrepancy principle) */
+    const double* g;       /* device: g_delta, one level */
+    const double* z0;      /* device, optional: true z(., 0) for the error report */
+    double* y0;            /* device, optional: receives y^0 at the picked alpha */
+} qbvm_sweep_instance;
+
+typedef struct qbvm_sweep_desc {
+    int    count;                       /* instances */
+    const qbvm_sweep_instance* inst;    /* host array of `count` entries */
+    int    n_alpha;
+    double log10_lo, log10_hi;
+    double tau_dp;                      /* e.g. 1.1 */
+    int    precision;
+} qbvm_sweep_desc;
+
+typedef struct qbvm_sweep_config {
+    int   modes_per_thread;   /* 1, 2 or 4 modes per thread in the alpha scan */
+    int   ctas_per_sm;        /* 0 = every resident slot */
+    int   grid;               /* resulting persistent grid (read only) */
+    float ms;                 /* time of one run measured by the autotuner */
+} qbvm_sweep_config;
+
+typedef struct qbvm_sweep qbvm_sweep_t;
+
+/* Validate and build a sweep (tables in FP64 on the host).  Errors: BAD_ARG,
+ * UNSUPPORTED, OOM, CUDA. */
+int qbvm_sweep_plan(const qbvm_sweep_desc* desc, qbvm_sweep_t** out);
+/* Enqueue one run on `stream` (first call captures the CUDA graph). */
+int qbvm_sweep_run(qbvm_sweep_t* sweep, void* stream);
+/* Synchronise `stream` and copy results to host arrays (any may be NULL):
+ * alphas, discrepancy, error: [count][n_alpha]; pick: [count][2] = (discrepancy
+ * pick, smallest-error alpha; the latter only meaningful with z0).
+ * TIMEOUT if a bounded wait inside the persistent kernel gave up. */
+int qbvm_sweep_read(qbvm_sweep_t* sweep, double* alphas, double* discrepancy, double* error, int* pick,
+                    void* stream);
+/* Time every candidate launch shape `repeats` times on the actual batch and
+ * keep the fastest; *best receives it (NULL accepted). */
+int qbvm_sweep_autotune(qbvm_sweep_t* sweep, int repeats, qbvm_sweep_config* best, void* stream);
+/* Set or read the launch shape (e.g. one cached from an earlier autotune). */
+int qbvm_sweep_set_config(qbvm_sweep_t* sweep, const qbvm_sweep_config* cfg);
+int qbvm_sweep_get_config(const qbvm_sweep_t* sweep, qbvm_sweep_config* cfg);
+int qbvm_sweep_destroy(qbvm_sweep_t* sweep);
 
 /* qbvm_destroy -- free the plan and everything it owns (NULL is accepted). */
 int qbvm_destroy(qbvm_plan_t* plan);

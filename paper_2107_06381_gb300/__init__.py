@@ -17,7 +17,9 @@ __all__ = [
     "QbvmDesc", "QbvmInfo", "QbvmError", "load_library",
     "qbvm_plan", "qbvm_solve", "qbvm_residual", "qbvm_plan_info", "qbvm_destroy",
     "qbvm_profile_enable", "qbvm_profile_read", "qbvm_residual_noalloc",
-    "qbvm_strerror", "qbvm_version", "Plan",
+    "qbvm_strerror", "qbvm_version", "Plan", "Sweep", "QbvmSweepInstance", "QbvmSweepDesc", "QbvmSweepConfig",
+    "qbvm_sweep_plan", "qbvm_sweep_run", "qbvm_sweep_read", "qbvm_sweep_autotune", "qbvm_sweep_set_config",
+    "qbvm_sweep_get_config", "qbvm_sweep_destroy",
     "FORM_PQ", "FORM_PM", "FP64", "FP32_REFINE", "RHS_DELTA", "RHS_GENERAL",
 ]
 
@@ -47,6 +49,27 @@ class QbvmInfo(ctypes.Structure):
 
 class QbvmKernelStat(ctypes.Structure):
     _fields_ = [("name", ctypes.c_char * 32), ("launches", ctypes.c_longlong), ("total_ms", ctypes.c_double)]
+
+
+class QbvmSweepInstance(ctypes.Structure):
+    _fields_ = [
+        ("dim", ctypes.c_int), ("m", ctypes.c_int * 3), ("L", ctypes.c_double), ("T", ctypes.c_double),
+        ("nt", ctypes.c_int), ("form", ctypes.c_int), ("delta", ctypes.c_double),
+        ("g", ctypes.c_void_p), ("z0", ctypes.c_void_p), ("y0", ctypes.c_void_p),
+    ]
+
+
+class QbvmSweepDesc(ctypes.Structure):
+    _fields_ = [
+        ("count", ctypes.c_int), ("inst", ctypes.POINTER(QbvmSweepInstance)), ("n_alpha", ctypes.c_int),
+        ("log10_lo", ctypes.c_double), ("log10_hi", ctypes.c_double), ("tau_dp", ctypes.c_double),
+        ("precision", ctypes.c_int),
+    ]
+
+
+class QbvmSweepConfig(ctypes.Structure):
+    _fields_ = [("modes_per_thread", ctypes.c_int), ("ctas_per_sm", ctypes.c_int), ("grid", ctypes.c_int),
+                ("ms", ctypes.c_float)]
 
 
 class QbvmError(RuntimeError):
@@ -86,6 +109,20 @@ def load_library(path: str | None = None) -> ctypes.CDLL:
     lib.qbvm_profile_read.restype = ip
     lib.qbvm_residual_noalloc.argtypes = [ctypes.POINTER(QbvmDesc), vp, vp, ctypes.POINTER(dp), vp]
     lib.qbvm_residual_noalloc.restype = ip
+    lib.qbvm_sweep_plan.argtypes = [ctypes.POINTER(QbvmSweepDesc), ctypes.POINTER(vp)]
+    lib.qbvm_sweep_plan.restype = ip
+    lib.qbvm_sweep_run.argtypes = [vp, vp]
+    lib.qbvm_sweep_run.restype = ip
+    lib.qbvm_sweep_read.argtypes = [vp, vp, vp, vp, vp, vp]
+    lib.qbvm_sweep_read.restype = ip
+    lib.qbvm_sweep_autotune.argtypes = [vp, ip, ctypes.POINTER(QbvmSweepConfig), vp]
+    lib.qbvm_sweep_autotune.restype = ip
+    lib.qbvm_sweep_set_config.argtypes = [vp, ctypes.POINTER(QbvmSweepConfig)]
+    lib.qbvm_sweep_set_config.restype = ip
+    lib.qbvm_sweep_get_config.argtypes = [vp, ctypes.POINTER(QbvmSweepConfig)]
+    lib.qbvm_sweep_get_config.restype = ip
+    lib.qbvm_sweep_destroy.argtypes = [vp]
+    lib.qbvm_sweep_destroy.restype = ip
     lib.qbvm_version.argtypes = []
     lib.qbvm_version.restype = ip
     if path is None:
@@ -190,6 +227,112 @@ def qbvm_profile_read(plan: int, capacity: int = 64) -> dict:
 def qbvm_destroy(plan: int) -> None:
     if plan:
         _check(load_library().qbvm_destroy(plan), "qbvm_destroy")
+
+
+def qbvm_sweep_plan(desc: QbvmSweepDesc) -> int:
+    h = ctypes.c_void_p()
+    _check(load_library().qbvm_sweep_plan(ctypes.byref(desc), ctypes.byref(h)), "qbvm_sweep_plan")
+    return h.value
+
+
+def qbvm_sweep_run(sweep: int, stream=None) -> None:
+    _check(load_library().qbvm_sweep_run(sweep, _stream(stream)), "qbvm_sweep_run")
+
+
+def qbvm_sweep_read(sweep: int, alphas, discrepancy, error, pick, stream=None) -> None:
+    _check(load_library().qbvm_sweep_read(sweep, _ptr(alphas), _ptr(discrepancy), _ptr(error), _ptr_int(pick),
+                                          _stream(stream)), "qbvm_sweep_read")
+
+
+def qbvm_sweep_autotune(sweep: int, repeats: int = 3, stream=None) -> QbvmSweepConfig:
+    cfg = QbvmSweepConfig()
+    _check(load_library().qbvm_sweep_autotune(sweep, repeats, ctypes.byref(cfg), _stream(stream)),
+           "qbvm_sweep_autotune")
+    return cfg
+
+
+def qbvm_sweep_set_config(sweep: int, cfg: QbvmSweepConfig) -> None:
+    _check(load_library().qbvm_sweep_set_config(sweep, ctypes.byref(cfg)), "qbvm_sweep_set_config")
+
+
+def qbvm_sweep_get_config(sweep: int) -> QbvmSweepConfig:
+    cfg = QbvmSweepConfig()
+    _check(load_library().qbvm_sweep_get_config(sweep, ctypes.byref(cfg)), "qbvm_sweep_get_config")
+    return cfg
+
+
+def qbvm_sweep_destroy(sweep: int) -> None:
+    if sweep:
+        _check(load_library().qbvm_sweep_destroy(sweep), "qbvm_sweep_destroy")
+
+
+def _ptr_int(a) -> int:
+    if a is None:
+        return 0
+    if isinstance(a, int):
+        return a
+    import numpy as np
+    if a.dtype != np.int32 or not a.flags["C_CONTIGUOUS"]:
+        raise TypeError("int arrays must be C-contiguous int32")
+    return a.ctypes.data
+
+
+class Sweep:
+    """Owning wrapper around a batched alpha sweep (device arrays: torch
+    tensors or raw addresses for g, z0, y0)."""
+
+    def __init__(self, instances, n_alpha=16, log10_lo=-1.5, log10_hi=1.5, tau_dp=1.1, precision=FP64):
+        self._keep = instances
+        arr = (QbvmSweepInstance * len(instances))()
+        for i, d in enumerate(instances):
+            m = list(d["m"]) + [1] * (3 - len(d["m"]))
+            arr[i] = QbvmSweepInstance(d["dim"], (ctypes.c_int * 3)(*m), float(d.get("L", 1.0)), float(d["T"]),
+                                       int(d["nt"]), int(d.get("form", FORM_PQ)), float(d["delta"]),
+                                       _ptr(d["g"]), _ptr(d.get("z0")), _ptr(d.get("y0")))
+        self._arr = arr
+        self.count = len(instances)
+        self.n_alpha = n_alpha
+        self.desc = QbvmSweepDesc(len(instances), arr, n_alpha, log10_lo, log10_hi, tau_dp, precision)
+        self.handle = qbvm_sweep_plan(self.desc)
+
+    def run(self, stream=None):
+        qbvm_sweep_run(self.handle, stream)
+
+    def read(self, stream=None):
+        import numpy as np
+        al = np.zeros((self.count, self.n_alpha))
+        disc = np.zeros_like(al)
+        err = np.zeros_like(al)
+        pick = np.zeros((self.count, 2), dtype=np.int32)
+        qbvm_sweep_read(self.handle, al, disc, err, pick, stream)
+        return al, disc, err, pick
+
+    def autotune(self, repeats=3, stream=None):
+        return qbvm_sweep_autotune(self.handle, repeats, stream)
+
+    @property
+    def config(self):
+        return qbvm_sweep_get_config(self.handle)
+
+    def set_config(self, modes_per_thread, ctas_per_sm):
+        qbvm_sweep_set_config(self.handle, QbvmSweepConfig(modes_per_thread, ctas_per_sm, 0, 0.0))
+
+    def close(self):
+        if self.handle:
+            qbvm_sweep_destroy(self.handle)
+            self.handle = None
+
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *exc):
+        self.close()
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
 
 
 class Plan:

@@ -146,4 +146,218 @@ __device__ __forceinline__ void fft_tile(C* buf, const C* tw, int lp, int lw) {
     }
 }
 
+// ---------------------------------------------------------------------------
+// Double-float arithmetic: a value is an unevaluated sum hi + lo of two FP32
+// numbers (|lo| <= ulp(hi)/2), about 48 significand bits, computed entirely on
+// the FP32 pipes.  Error-free transformations: Knuth's two-sum for additions,
+// Dekker's product with the error term recovered by one fused multiply-add.
+struct dfloat {
+    float hi, lo;
+};
+
+__device__ __forceinline__ dfloat df_two_sum(float a, float b) {
+    float s = a + b;
+    float bb = s - a;
+    float e = (a - (s - bb)) + (b - bb);
+    return {s, e};
+}
+__device__ __forceinline__ dfloat df_fast_two_sum(float a, float b) {   // requires |a| >= |b|
+    float s = a + b;
+    return {s, b - (s - a)};
+}
+__device__ __forceinline__ dfloat df_add(dfloat a, dfloat b) {
+    dfloat s = df_two_sum(a.hi, b.hi);
+    dfloat t = df_two_sum(a.lo, b.lo);
+    s.lo += t.hi;
+    s = df_fast_two_sum(s.hi, s.lo);
+    s.lo += t.lo;
+    return df_fast_two_sum(s.hi, s.lo);
+}
+__device__ __forceinline__ dfloat df_neg(dfloat a) { return {-a.hi, -a.lo}; }
+__device__ __forceinline__ dfloat df_add_f(dfloat a, float b) {
+    dfloat s = df_two_sum(a.hi, b);
+    s.lo += a.lo;
+    return df_fast_two_sum(s.hi, s.lo);
+}
+__device__ __forceinline__ dfloat df_mul(dfloat a, dfloat b) {
+    float p = a.hi * b.hi;
+    float e = fmaf(a.hi, b.hi, -p);
+    e = fmaf(a.hi, b.lo, e);
+    e = fmaf(a.lo, b.hi, e);
+    return df_fast_two_sum(p, e);
+}
+// ---------------------------------------------------------------------------
+// FP64 <-> FP32 conversions on the integer pipes.  On GB300 the hardware
+// conversions issue on the FP64 pipe (2 per clock per SM), which made them the
+// bottleneck of the FP32 refinement path; these bit manipulations give the
+// same results for every finite value in the normal FP32 range and fall back
+// to the hardware instructions outside it.
+#ifdef __CUDACC__
+#define QBVM_HD __host__ __device__ __forceinline__
+#else
+#define QBVM_HD inline
+#endif
+
+QBVM_HD unsigned long long qbvm_dbits(double x) {
+#ifdef __CUDA_ARCH__
+    return (unsigned long long)__double_as_longlong(x);
+#else
+    unsigned long long u;
+    __builtin_memcpy(&u, &x, 8);
+    return u;
+#endif
+}
+QBVM_HD double qbvm_bitsd(unsigned long long u) {
+#ifdef __CUDA_ARCH__
+    return __longlong_as_double((long long)u);
+#else
+    double x;
+    __builtin_memcpy(&x, &u, 8);
+    return x;
+#endif
+}
+QBVM_HD unsigned int qbvm_fbits(float x) {
+#ifdef __CUDA_ARCH__
+    return (unsigned int)__float_as_uint(x);
+#else
+    unsigned int u;
+    __builtin_memcpy(&u, &x, 4);
+    return u;
+#endif
+}
+QBVM_HD int qbvm_clzll(unsigned long long a) {
+#ifdef __CUDA_ARCH__
+    return __clzll((long long)a);
+#else
+    return __builtin_clzll(a);
+#endif
+}
+QBVM_HD float qbvm_bitsf(unsigned int u) {
+#ifdef __CUDA_ARCH__
+    return __uint_as_float(u);
+#else
+    float x;
+    __builtin_memcpy(&x, &u, 4);
+    return x;
+#endif
+}
+
+// Round-to-nearest-even FP64 -> FP32 of x, and the exact remainder x - hi as
+// an FP32 (rounded to nearest; the remainder has at most 29 significant bits).
+QBVM_HD void qbvm_split_d(double x, float* hi, float* lo) {
+    const unsigned long long b = qbvm_dbits(x);
+    if ((b << 1) == 0) {                                  // +-0: exact, integer path
+        *hi = qbvm_bitsf((unsigned int)(b >> 32));
+        *lo = 0.0f;
+        return;
+    }
+    const int e = (int)((b >> 52) & 0x7FF);
+    const int fe = e - 1023 + 127;                       // FP32 biased exponent of hi
+    if (fe < 30 || fe > 253) {                           // tiny, huge, Inf, NaN: hardware path
+        float h = (float)x;
+        *hi = h;
+        *lo = (float)(x - (double)h);
+        return;
+    }
+    const unsigned int sign = (unsigned int)(b >> 32) & 0x80000000u;
+    const unsigned long long mm = (b & 0xFFFFFFFFFFFFFull) | (1ull << 52);   // 53-bit significand
+    unsigned long long q = mm >> 29;                      // 24 bits
+    const unsigned long long rem = mm & ((1ull << 29) - 1);
+    if (rem > (1ull << 28) || (rem == (1ull << 28) && (q & 1))) ++q;
+    // remainder in units of 2^(e - 1075): mm - q * 2^29, |r| <= 2^28
+    const long long r = (long long)mm - (long long)(q << 29);
+    int he = fe;
+    if (q == (1ull << 24)) {                               // rounding carried into a new binade
+        q >>= 1;
+        ++he;
+    }
+    *hi = qbvm_bitsf(sign | ((unsigned int)he << 23) | ((unsigned int)q & 0x7FFFFFu));
+    if (r == 0) {
+        *lo = 0.0f;
+        return;
+    }
+    // lo = sign * r * 2^(e - 1075): normalise |r| (<= 29 bits) to 24 bits, RNE
+    unsigned long long a = (unsigned long long)(r < 0 ? -r : r);
+    const unsigned int lsign = sign ^ (r < 0 ? 0x80000000u : 0u);
+    int top = 63 - qbvm_clzll(a);                    // position of the leading bit (0..28)
+    int le = (e - 1075) + top + 127;                      // FP32 biased exponent of lo
+    unsigned long long lq;
+    if (top > 23) {
+        const int sh = top - 23;
+        lq = a >> sh;
+        const unsigned long long lr = a & ((1ull << sh) - 1), half = 1ull << (sh - 1);
+        if (lr > half || (lr == half && (lq & 1))) ++lq;
+        if (lq == (1ull << 24)) {
+            lq >>= 1;
+            ++le;
+        }
+    } else {
+        lq = a << (23 - top);
+    }
+    if (le < 1) {                                         // below the FP32 normal range: hardware path
+        float h = *hi;
+        *lo = (float)(x - (double)h);
+        return;
+    }
+    *lo = qbvm_bitsf(lsign | ((unsigned int)le << 23) | ((unsigned int)lq & 0x7FFFFFu));
+}
+
+// (double)hi + (double)lo, correctly rounded, for a pair with |lo| <= |hi|
+// (hi's significand is placed 39 bits up; lo is aligned below it with a sticky
+// bit for whatever falls off, then the sum is rounded to 53 bits, ties to even).
+QBVM_HD double qbvm_join_df(float hi, float lo) {
+    const unsigned int hb = qbvm_fbits(hi), lb = qbvm_fbits(lo);
+    const int e1 = (int)((hb >> 23) & 0xFF), e2 = (int)((lb >> 23) & 0xFF);
+    if ((hb << 1) == 0 && (lb << 1) == 0)                 // 0 + 0 (sign as the hardware sum gives)
+        return qbvm_bitsd((unsigned long long)(hb & lb & 0x80000000u) << 32);
+    if ((hb << 1) == 0 && e2 != 0 && e2 != 255)           // 0 + normal lo: lo widened exactly
+        return qbvm_bitsd(((unsigned long long)(lb & 0x80000000u) << 32) |
+                          ((unsigned long long)(e2 - 127 + 1023) << 52) |
+                          ((unsigned long long)(lb & 0x7FFFFFu) << 29));
+    if (e1 == 0 || e1 == 255 || e2 == 255 || (e2 == 0 && (lb & 0x7FFFFFu)) || e2 > e1)
+        return (double)hi + (double)lo;                   // zero/denormal/Inf/NaN/unnormalised: hardware
+    const unsigned long long sign = (unsigned long long)(hb & 0x80000000u) << 32;
+    long long S = (long long)((unsigned long long)((hb & 0x7FFFFFu) | 0x800000u) << 39);   // < 2^63
+    if (e2 != 0) {
+        const unsigned long long M2 = (lb & 0x7FFFFFu) | 0x800000u;
+        const int d = e1 - e2;
+        long long B;
+        if (d <= 39) {
+            B = (long long)(M2 << (39 - d));
+        } else if (d - 39 < 40) {
+            const int sh = d - 39;
+            B = (long long)(M2 >> sh) | (long long)((M2 & ((1ull << sh) - 1)) != 0);
+        } else {
+            B = 1;                                        // only the sticky bit survives
+        }
+        if ((hb ^ lb) & 0x80000000u) S -= B;
+        else S += B;
+    }
+    // S in (2^61, 2^63): leading bit p, round to 53 bits
+    const int p = 63 - qbvm_clzll((unsigned long long)S);
+    const int sh = p - 52;
+    unsigned long long q = (unsigned long long)S >> sh;
+    const unsigned long long rem = (unsigned long long)S & ((1ull << sh) - 1), half = 1ull << (sh - 1);
+    int de = (e1 - 127) + (p - 62) + 1023;               // hi's leading bit sits at position 62
+    if (rem > half || (rem == half && (q & 1))) ++q;
+    if (q == (1ull << 53)) {
+        q >>= 1;
+        ++de;
+    }
+    return qbvm_bitsd(sign | ((unsigned long long)de << 52) | (q & 0xFFFFFFFFFFFFFull));
+}
+
+// FP64 -> double-float and back, on the integer pipes.
+__device__ __forceinline__ dfloat df_from_double(double x) {
+    dfloat r;
+    qbvm_split_d(x, &r.hi, &r.lo);
+    return r;
+}
+__device__ __forceinline__ double df_to_double(dfloat a) { return qbvm_join_df(a.hi, a.lo); }
+__device__ __forceinline__ float d2f_int(double x) {
+    float h, l;
+    qbvm_split_d(x, &h, &l);
+    return h;
+}
+
 }  // namespace qbvm

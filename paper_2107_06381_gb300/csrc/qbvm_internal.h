@@ -29,14 +29,20 @@ struct Tables {
     double2* gipw = nullptr;         // 2 gamma^{-t} (t < H)
     double2* ak = nullptr;           // d_{2m} = 1 - gamma theta^{2m}, m < H (eigenvalues of C_omega)
     double*  lamtau = nullptr;       // tau * Lambda_l for every spatial mode (2D/3D)
+    float2*  gpow32 = nullptr;       // FP32 roundings of gpow, gipw, ak, lamtau
+    float2*  gipw32 = nullptr;
+    float2*  ak32 = nullptr;
+    float*   lamtau32 = nullptr;
     double2* bk = nullptr;           // 1D Thomas diagonal for frequency 2m: h^2 d_{2m} / tau + 2
 };
 
 // DST-I (unnormalised, S_{jk} = sin(pi j k /(n+1))) along one axis of an
 // array viewed as [outer][n][inner], in place allowed (in == out).
-// lm = log2(n + 1); tw = roots of length n+1, sn = sin(j pi/(n+1)) tables.
-template <typename R>
-cudaError_t launch_dst(const R* in, R* out, int n, int lm, long long outer, long long inner,
+// lm = log2(n + 1); tw = roots of length n+1, sn = sin(j pi/(n+1)) tables of
+// precision R.  TIN: element type read.  OMODE: 0 store R, 1 accumulate into
+// a double-float (float2 hi, lo) array, 2 store into a double-float array.
+template <typename R, typename TIN, int OMODE>
+cudaError_t launch_dst(const TIN* in, void* out, int n, int lm, long long outer, long long inner,
                        const void* tw, const void* sn, cudaStream_t s);
 
 // Space-first time solve: per spatial mode l (column), scale by gamma^t, FFT
@@ -61,6 +67,23 @@ cudaError_t launch_residual(const double* y, const double* f, int delta_rhs, con
                             double* r_out, cudaStream_t s);
 int residual_blocks(const Tables& tb);
 
+// Double-float residual of the refinement: y_df is a (hi, lo) float2 array,
+// f FP64 (F, or g for the delta right-hand side); writes r.hi (FP32) to r_out
+// and sums[2] = (||r||^2, ||f||^2).
+cudaError_t launch_residual_df(const void* y_df, const double* f, int delta_rhs, const Tables& tb,
+                               const double h2inv[3], float* r_out, double* partials, int nblocks, double* sums,
+                               cudaStream_t s);
+// In place: double-float (float2) array of n values -> FP64 array.
+cudaError_t launch_df_to_double(void* buf, long long n, cudaStream_t s);
+
+}  // namespace qbvm
+
+namespace qbvm {
+// Shared-memory bytes of one DST tile of length M = 2^lm in precision R, and
+// the tile width log2(W) (2W real columns per tile).
+template <typename R>
+size_t dst_smem_bytes(int lm);
+int dst_tile_lw(int lm);
 }  // namespace qbvm
 
 struct qbvm_desc;

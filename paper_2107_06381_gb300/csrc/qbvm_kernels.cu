@@ -13,165 +13,48 @@
 // 1D keeps the paper's order: omega-scaling + FFT along time into a complex
 // workspace, one complex tridiagonal (Thomas) solve per frequency, inverse
 // FFT + unscaling.
+#include "qbvm_dst.cuh"
 #include "qbvm_fft.cuh"
 #include "qbvm_internal.h"
 
+#include <cstdint>
 #include <type_traits>
 
 namespace qbvm {
 
-// ------------------------------------------------------------------ DST-I
-//
-// y_k = sum_{j=1}^{n} x_j sin(pi j k / M), n = M - 1, with one complex FFT of
-// length M for two real columns.  With x_0 = x_M = 0 and s_j = sin(j pi/M),
-//     w_j = s_j (x_j + x_{M-j}) + (x_j - x_{M-j}) / 2,   j = 0..M-1,
-// the DFT W_k = sum_j w_j exp(-2 pi i jk/M) satisfies
-//     y_{2k} = -Im W_k,   y_{2k+1} - y_{2k-1} = Re W_k   (y_{-1} = -y_1),
-// (the symmetric part of w carries the cosine sums, the antisymmetric part the
-// sine sums), so the even outputs are read off and the odd ones are a prefix
-// sum.  Columns a and b are packed as w^a + i w^b and separated with
-// W^a_k = (Z_k + conj Z_{M-k})/2, W^b_k = (Z_k - conj Z_{M-k})/(2i).
-template <typename R, int MAXB4>
+// Raise a kernel's dynamic shared-memory limit and prefer the largest
+// shared-memory carve-out (cheap host calls, made before every launch).
+template <typename K>
+static cudaError_t set_smem(K kern, size_t smem) {
+    cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    if (e != cudaSuccess) return e;
+    return cudaFuncSetAttribute(kern, cudaFuncAttributePreferredSharedMemoryCarveout, 100);
+}
+
+template <typename R, typename TIN, int OMODE, int MAXB4>
 __global__ void __launch_bounds__(TILE_THREADS)
-k_dst(const R* in, R* out, int n, int lm, int lw, long long outer, long long inner,
+k_dst(const TIN* in, void* out, int n, int lm, int lw, long long outer, long long inner,
       const cplx<R>* __restrict__ tw, const R* __restrict__ sn) {
-    using C = cplx<R>;
     extern __shared__ __align__(16) unsigned char smem_raw[];
-    const int M = 1 << lm, W = 1 << lw, H = M >> 1;
-    const int tid = threadIdx.x, nth = blockDim.x;
-    const int ncol = 2 * W;                          // real columns in this tile
-    C* buf = reinterpret_cast<C*>(smem_raw);         // M x W complex
-    R* obuf = reinterpret_cast<R*>(buf + (M << lw)); // M x 2W real (outputs y_1..y_n at rows 0..n-1)
-    C* stw = reinterpret_cast<C*>(obuf + ((size_t)M << (lw + 1)));
-    R* ssn = reinterpret_cast<R*>(stw + M);          // sin(j pi / M), j = 0..H
-    R* seg = ssn + (H + 2);                          // prefix-sum segment totals
-    R* bufr = reinterpret_cast<R*>(buf);
-
-    for (int i = tid; i < M; i += nth) stw[i] = tw[i];
-    for (int i = tid; i <= H; i += nth) ssn[i] = sn[i];
-    for (int p = tid; p < W; p += nth) buf[p] = mkc(R(0), R(0));
-
-    long long base_row = 0, o = 0, i0 = 0;
-    if (inner == 1) {
-        base_row = (long long)blockIdx.x * ncol;
-        for (int e = tid; e < ncol * n; e += nth) {
-            int r = e / n, j = e - r * n;
-            long long row = base_row + r;
-            R v = row < outer ? in[row * n + j] : R(0);
-            bufr[(((j + 1) << lw) + (r >> 1)) * 2 + (r & 1)] = v;
-        }
-    } else {
-        long long tiles_per_outer = (inner + ncol - 1) / ncol;
-        o = blockIdx.x / tiles_per_outer;
-        i0 = (blockIdx.x - o * tiles_per_outer) * ncol;
-        const R* src = in + o * (long long)n * inner;
-        for (int e = tid; e < ncol * n; e += nth) {
-            int j = e / ncol, r = e - j * ncol;
-            long long ii = i0 + r;
-            R v = ii < inner ? src[(long long)j * inner + ii] : R(0);
-            bufr[(((j + 1) << lw) + (r >> 1)) * 2 + (r & 1)] = v;
-        }
-    }
-    __syncthreads();
-    // w_j and w_{M-j} from the pair (x_j, x_{M-j}), j = 1..H
-    for (int e = tid; e < (H << lw); e += nth) {
-        int j = (e >> lw) + 1, p = e & (W - 1);
-        C a = buf[(j << lw) + p], b = buf[((M - j) << lw) + p];
-        R sj = ssn[j];
-        C A = mkc(sj * (a.x + b.x), sj * (a.y + b.y));
-        C B = mkc(R(0.5) * (a.x - b.x), R(0.5) * (a.y - b.y));
-        buf[(j << lw) + p] = cadd(A, B);
-        if (j != H) buf[((M - j) << lw) + p] = csub(A, B);
-    }
-    __syncthreads();
-    fft_tile<-1, MAXB4>(buf, stw, lm, lw);
-
-    // separate the packed columns; even outputs and odd increments into obuf
-    for (int e = tid; e < (H << lw); e += nth) {
-        int k = e >> lw, p = e & (W - 1);
-        C zk = buf[(k << lw) + p], zm = buf[(((M - k) & (M - 1)) << lw) + p];
-        R ra = R(0.5) * (zk.x + zm.x), rb = R(0.5) * (zk.y + zm.y);
-        if (k == 0) {
-            ra *= R(0.5);
-            rb *= R(0.5);
-        } else {
-            R* ev = obuf + ((size_t)(2 * k - 1) << (lw + 1));
-            ev[2 * p] = R(0.5) * (zm.y - zk.y);
-            ev[2 * p + 1] = R(0.5) * (zk.x - zm.x);
-        }
-        R* od = obuf + ((size_t)(2 * k) << (lw + 1));
-        od[2 * p] = ra;
-        od[2 * p + 1] = rb;
-    }
-    __syncthreads();
-    // y_{2k+1} = sum_{kappa <= k} (odd increments): segmented prefix sum per real column
-    const int segs = nth >= ncol ? nth / ncol : 1;
-    const int L = (H + segs - 1) / segs;
-    for (int task = tid; task < ncol * segs; task += nth) {
-        int c = task % ncol, sg = task / ncol;
-        int k0 = sg * L, k1 = min(H, k0 + L);
-        R acc = R(0);
-        for (int k = k0; k < k1; ++k) {
-            R* v = obuf + ((size_t)(2 * k) << (lw + 1)) + c;
-            acc += *v;
-            *v = acc;
-        }
-        seg[sg * ncol + c] = acc;
-    }
-    __syncthreads();
-    if (segs > 1) {
-        for (int task = tid; task < ncol * segs; task += nth) {
-            int c = task % ncol, sg = task / ncol;
-            if (sg == 0) continue;
-            R off = R(0);
-            for (int s2 = 0; s2 < sg; ++s2) off += seg[s2 * ncol + c];
-            int k0 = sg * L, k1 = min(H, k0 + L);
-            for (int k = k0; k < k1; ++k) obuf[((size_t)(2 * k) << (lw + 1)) + c] += off;
-        }
-        __syncthreads();
-    }
-    if (inner == 1) {
-        for (int e = tid; e < ncol * n; e += nth) {
-            int r = e / n, j = e - r * n;
-            long long row = base_row + r;
-            if (row < outer) out[row * n + j] = obuf[((size_t)j << (lw + 1)) + r];
-        }
-    } else {
-        R* dst = out + o * (long long)n * inner;
-        for (int e = tid; e < ncol * n; e += nth) {
-            int j = e / ncol, r = e - j * ncol;
-            long long ii = i0 + r;
-            if (ii < inner) dst[(long long)j * inner + ii] = obuf[((size_t)j << (lw + 1)) + r];
-        }
-    }
-}
-
-constexpr int DST_TILE = 2048;     // complex elements per DST tile
-
-static int dst_lw(int lm) {
-    int lw = 0;
-    while (((1 << lm) << (lw + 1)) <= DST_TILE) ++lw;
-    return lw;
+    dst_tile<R, TIN, OMODE, MAXB4, false>(in, out, n, lm, lw, outer, inner, (long long)blockIdx.x, tw, sn, smem_raw);
 }
 
 template <typename R>
-size_t dst_smem(int lm) {
-    const int M = 1 << lm, lw = dst_lw(lm), W = 1 << lw, H = M >> 1;
-    const int ncol = 2 * W;
-    size_t seg = (size_t)(TILE_THREADS >= ncol ? TILE_THREADS : ncol);
-    return sizeof(cplx<R>) * ((size_t)M * W + M) + sizeof(R) * ((size_t)M * 2 * W + H + 2 + seg);
-}
+size_t dst_smem_bytes(int lm) { return dst_smem<R>(lm); }
+template size_t dst_smem_bytes<double>(int);
+template size_t dst_smem_bytes<float>(int);
+int dst_tile_lw(int lm) { return dst_lw(lm); }
 
-template <typename R>
-cudaError_t launch_dst(const R* in, R* out, int n, int lm, long long outer, long long inner,
+template <typename R, typename TIN, int OMODE>
+cudaError_t launch_dst(const TIN* in, void* out, int n, int lm, long long outer, long long inner,
                        const void* tw, const void* sn, cudaStream_t s) {
     const int lw = dst_lw(lm), W = 1 << lw;
     long long blocks;
     if (inner == 1) blocks = (outer + 2 * W - 1) / (2 * W);
     else blocks = outer * ((inner + 2 * W - 1) / (2 * W));
     size_t smem = dst_smem<R>(lm);
-    auto kern = k_dst<R, DST_TILE / 4 / TILE_THREADS>;
-    cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    auto kern = k_dst<R, TIN, OMODE, DST_TILE / 4 / TILE_THREADS>;
+    cudaError_t e = set_smem(kern, smem);
     if (e != cudaSuccess) return e;
     kern<<<(unsigned)blocks, TILE_THREADS, smem, s>>>(in, out, n, lm, lw, outer, inner,
                                                       reinterpret_cast<const cplx<R>*>(tw),
@@ -179,10 +62,15 @@ cudaError_t launch_dst(const R* in, R* out, int n, int lm, long long outer, long
     return cudaGetLastError();
 }
 
-template cudaError_t launch_dst<double>(const double*, double*, int, int, long long, long long, const void*,
-                                        const void*, cudaStream_t);
-template cudaError_t launch_dst<float>(const float*, float*, int, int, long long, long long, const void*,
-                                       const void*, cudaStream_t);
+#define QBVM_DST_INST(R, TIN, OM)                                                                       \
+    template cudaError_t launch_dst<R, TIN, OM>(const TIN*, void*, int, int, long long, long long,     \
+                                                const void*, const void*, cudaStream_t);
+QBVM_DST_INST(double, double, 0)
+QBVM_DST_INST(float, float, 0)
+QBVM_DST_INST(float, double, 0)
+QBVM_DST_INST(float, float, 1)
+QBVM_DST_INST(float, float, 2)
+#undef QBVM_DST_INST
 
 // --------------------------------------------------------- time solve (2D/3D)
 //
@@ -197,12 +85,14 @@ template cudaError_t launch_dst<float>(const float*, float*, int, int, long long
 //     y_t = Re v_t and y_{t+H} = rho^{-H} Im v_t (the odd frequencies are the
 //     conjugates of the even ones, so they never need to be formed).
 // cnorm carries tau, 1/nt and the inverse-DST normalisation.
+// The scaling, divide and unscaling use tables of the transform's precision
+// (the FP32 tables are the FP64 ones rounded once on the host).
 template <typename R, int MAXB4>
 __global__ void __launch_bounds__(TILE_THREADS)
 k_time_solve(const R* in, R* out, long long Nx, int lh, int lw, const cplx<R>* __restrict__ tw,
-             const double2* __restrict__ gpow, const double2* __restrict__ gipw,
-             const double2* __restrict__ ak, const double* __restrict__ lamtau, double cnorm,
-             double rho_h, double rho_hinv, int delta_rhs, int n0_only) {
+             const cplx<R>* __restrict__ gpow, const cplx<R>* __restrict__ gipw,
+             const cplx<R>* __restrict__ ak, const R* __restrict__ lamtau, R cnorm,
+             R rho_h, R rho_hinv, int delta_rhs, int n0_only) {
     using C = cplx<R>;
     extern __shared__ __align__(16) unsigned char smem_raw[];
     const int H = 1 << lh, W = 1 << lw;
@@ -215,17 +105,17 @@ k_time_solve(const R* in, R* out, long long Nx, int lh, int lw, const cplx<R>* _
     for (int e = tid; e < (H << lw); e += nth) {
         int t = e >> lw, c = e & (W - 1);
         long long l = l0 + c;
-        double f0 = 0.0, f1 = 0.0;
+        R f0 = R(0), f1 = R(0);
         if (l < Nx) {
             if (delta_rhs) {
-                if (t == 0) f0 = (double)in[l];
+                if (t == 0) f0 = in[l];
             } else {
-                f0 = (double)in[(long long)t * Nx + l];
-                f1 = rho_h * (double)in[(long long)(t + H) * Nx + l];
+                f0 = in[(long long)t * Nx + l];
+                f1 = rho_h * in[(long long)(t + H) * Nx + l];
             }
         }
-        double2 g = gpow[t];
-        buf[e] = mkc(R(g.x * f0 - g.y * f1), R(g.y * f0 + g.x * f1));
+        C g = gpow[t];
+        buf[e] = mkc(g.x * f0 - g.y * f1, g.y * f0 + g.x * f1);
     }
     __syncthreads();
     fft_tile<+1, MAXB4>(buf, stw, lh, lw);
@@ -233,12 +123,12 @@ k_time_solve(const R* in, R* out, long long Nx, int lh, int lw, const cplx<R>* _
     for (int e = tid; e < (H << lw); e += nth) {
         int k = e >> lw, c = e & (W - 1);
         long long l = l0 + c;
-        double lt = l < Nx ? lamtau[l] : 0.0;
-        double2 a = ak[k];
-        double zr = a.x + lt, zi = a.y;
-        double inv = cnorm / fma(zr, zr, zi * zi);
+        R lt = l < Nx ? lamtau[l] : R(0);
+        C a = ak[k];
+        R zr = a.x + lt, zi = a.y;
+        R inv = cnorm / (zr * zr + zi * zi);
         C u = buf[e];
-        buf[e] = mkc(R((u.x * zr + u.y * zi) * inv), R((u.y * zr - u.x * zi) * inv));
+        buf[e] = mkc((u.x * zr + u.y * zi) * inv, (u.y * zr - u.x * zi) * inv);
     }
     __syncthreads();
     fft_tile<-1, MAXB4>(buf, stw, lh, lw);
@@ -248,14 +138,10 @@ k_time_solve(const R* in, R* out, long long Nx, int lh, int lw, const cplx<R>* _
         int t = e >> lw, c = e & (W - 1);
         long long l = l0 + c;
         if (l < Nx) {
-            double2 gi = gipw[t];
+            C gi = gipw[t];
             C w = buf[e];
-            double vx = gi.x * (double)w.x - gi.y * (double)w.y;
-            out[(long long)t * Nx + l] = R(vx);
-            if (!n0_only) {
-                double vy = gi.x * (double)w.y + gi.y * (double)w.x;
-                out[(long long)(t + H) * Nx + l] = R(rho_hinv * vy);
-            }
+            out[(long long)t * Nx + l] = gi.x * w.x - gi.y * w.y;
+            if (!n0_only) out[(long long)(t + H) * Nx + l] = rho_hinv * (gi.x * w.y + gi.y * w.x);
         }
     }
 }
@@ -274,13 +160,15 @@ cudaError_t launch_time_solve(const R* in, R* out, const Tables& tb, double cnor
     long long blocks = (tb.Nx + W - 1) / W;
     size_t smem = sizeof(cplx<R>) * ((size_t)H * W + H);
     auto kern = k_time_solve<R, TILE_ELEMS / 4 / TILE_THREADS>;
-    cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    cudaError_t e = set_smem(kern, smem);
     if (e != cudaSuccess) return e;
-    const cplx<R>* tw = std::is_same<R, double>::value ? reinterpret_cast<const cplx<R>*>(tb.tw_t)
-                                                       : reinterpret_cast<const cplx<R>*>(tb.tw_t32);
-    kern<<<(unsigned)blocks, TILE_THREADS, smem, s>>>(in, out, tb.Nx, lh, lw, tw, tb.gpow, tb.gipw, tb.ak,
-                                                      tb.lamtau, cnorm, tb.rho_h, tb.rho_hinv, delta_rhs,
-                                                      n0_only);
+    const bool f64 = std::is_same<R, double>::value;
+    auto pick = [f64](const void* a, const void* b) { return reinterpret_cast<const cplx<R>*>(f64 ? a : b); };
+    const R* lt = reinterpret_cast<const R*>(f64 ? (const void*)tb.lamtau : (const void*)tb.lamtau32);
+    kern<<<(unsigned)blocks, TILE_THREADS, smem, s>>>(in, out, tb.Nx, lh, lw, pick(tb.tw_t, tb.tw_t32),
+                                                      pick(tb.gpow, tb.gpow32), pick(tb.gipw, tb.gipw32),
+                                                      pick(tb.ak, tb.ak32), lt, R(cnorm), R(tb.rho_h),
+                                                      R(tb.rho_hinv), delta_rhs, n0_only);
     return cudaGetLastError();
 }
 
@@ -398,7 +286,7 @@ cudaError_t launch_time_fwd_1d(const double* in, double2* wk, const Tables& tb, 
     const int lh = tb.lnt - 1, H = 1 << lh, lw = tile_lw(lh), W = 1 << lw;
     long long blocks = (tb.Nx + W - 1) / W;
     size_t smem = sizeof(double2) * ((size_t)H * W + H);
-    cudaError_t e = cudaFuncSetAttribute(k_time_fwd_1d, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    cudaError_t e = set_smem(k_time_fwd_1d, smem);
     if (e != cudaSuccess) return e;
     k_time_fwd_1d<<<(unsigned)blocks, TILE_THREADS, smem, s>>>(in, wk, tb.Nx, lh, lw, tb.tw_t, tb.gpow, tb.rho_h,
                                                                 delta_rhs, in_scale);
@@ -417,7 +305,7 @@ cudaError_t launch_time_inv_1d(const double2* wk, double* out, const Tables& tb,
     const int lh = tb.lnt - 1, H = 1 << lh, lw = tile_lw(lh), W = 1 << lw;
     long long blocks = (tb.Nx + W - 1) / W;
     size_t smem = sizeof(double2) * ((size_t)H * W + H);
-    cudaError_t e = cudaFuncSetAttribute(k_time_inv_1d, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    cudaError_t e = set_smem(k_time_inv_1d, smem);
     if (e != cudaSuccess) return e;
     k_time_inv_1d<<<(unsigned)blocks, TILE_THREADS, smem, s>>>(wk, out, tb.Nx, lh, lw, tb.tw_t, tb.gipw,
                                                                 tb.rho_hinv, n0_only);
@@ -444,44 +332,48 @@ __device__ __forceinline__ double block_sum(double v, double* sh) {
     return v;
 }
 
+// Rows of n_x contiguous values: row index -> (t, z, y) in 32-bit arithmetic;
+// the threads of a block stride over x.
 __global__ void __launch_bounds__(RES_THREADS)
 k_residual(const double* __restrict__ y, const double* __restrict__ f, int delta_rhs, int nt,
            int nx, int ny, int nz, double inv_tau, double omega, double hx2, double hy2, double hz2,
            double* partials, double* r_out) {
     __shared__ double sh[32];
     const long long Nx = (long long)nx * ny * nz;
-    const long long total = Nx * nt;
+    const long long pl = (long long)nx * ny;
+    const int rows = nt * ny * nz;
     double rr = 0.0, ff = 0.0;
-    for (long long idx = (long long)blockIdx.x * blockDim.x + threadIdx.x; idx < total;
-         idx += (long long)gridDim.x * blockDim.x) {
-        long long t = idx / Nx, sidx = idx - t * Nx;
-        int ix = (int)(sidx % nx);
-        long long q = sidx / nx;
-        int iy = (int)(q % ny), iz = (int)(q / ny);
-        double yv = y[idx];
-        double lap = -2.0 * yv * hx2;
-        if (ix > 0) lap += y[idx - 1] * hx2;
-        if (ix < nx - 1) lap += y[idx + 1] * hx2;
-        if (ny > 1) {
-            lap -= 2.0 * yv * hy2;
-            if (iy > 0) lap += y[idx - nx] * hy2;
-            if (iy < ny - 1) lap += y[idx + nx] * hy2;
+    for (int row = blockIdx.x; row < rows; row += gridDim.x) {
+        const int t = row / (ny * nz), rz = row - t * (ny * nz);
+        const int iz = rz / ny, iy = rz - iz * ny;
+        const long long base = (long long)row * nx;
+        const long long sbase = base - (long long)t * Nx;
+        for (int ix = threadIdx.x; ix < nx; ix += blockDim.x) {
+            const long long idx = base + ix;
+            double yv = y[idx];
+            double lap = -2.0 * yv * hx2;
+            if (ix > 0) lap += y[idx - 1] * hx2;
+            if (ix < nx - 1) lap += y[idx + 1] * hx2;
+            if (ny > 1) {
+                lap -= 2.0 * yv * hy2;
+                if (iy > 0) lap += y[idx - nx] * hy2;
+                if (iy < ny - 1) lap += y[idx + nx] * hy2;
+            }
+            if (nz > 1) {
+                lap -= 2.0 * yv * hz2;
+                if (iz > 0) lap += y[idx - pl] * hz2;
+                if (iz < nz - 1) lap += y[idx + pl] * hz2;
+            }
+            double prev = t > 0 ? y[idx - Nx] : omega * y[(long long)(nt - 1) * Nx + sbase + ix];
+            double Ay = (yv - prev) * inv_tau - lap;
+            double fv;
+            if (delta_rhs) fv = t == 0 ? -omega * inv_tau * f[sbase + ix] : 0.0;
+            else fv = f[idx];
+            double r = fv - Ay;
+            if (r_out) r_out[idx] = r;
+            rr = fma(r, r, rr);
+            ff = fma(fv, fv, ff);
         }
-        if (nz > 1) {
-            long long pl = (long long)nx * ny;
-            lap -= 2.0 * yv * hz2;
-            if (iz > 0) lap += y[idx - pl] * hz2;
-            if (iz < nz - 1) lap += y[idx + pl] * hz2;
-        }
-        double prev = t > 0 ? y[idx - Nx] : omega * y[(long long)(nt - 1) * Nx + sidx];
-        double Ay = (yv - prev) * inv_tau - lap;
-        double fv;
-        if (delta_rhs) fv = t == 0 ? -omega * inv_tau * f[sidx] : 0.0;
-        else fv = f[idx];
-        double r = fv - Ay;
-        if (r_out) r_out[idx] = r;
-        rr = fma(r, r, rr);
-        ff = fma(fv, fv, ff);
     }
     rr = block_sum(rr, sh);
     ff = block_sum(ff, sh);
@@ -506,9 +398,117 @@ __global__ void k_reduce_pairs(const double* partials, int n, double* sums) {
     }
 }
 
+// Double-float residual for the refinement: y is a double-float array (hi, lo),
+// f is FP64 (split exactly on load, one FP64 subtraction per value); the
+// stencil runs in double-float on the FP32 pipes.  Writes r.hi (FP32: the
+// right-hand side of the next FP32 correction solve) and per-block partial
+// sums of ||r||^2, ||f||^2 (r.hi^2, f.hi^2; enough digits for a stopping test).
+//   (A y)^n = c0 y^n - cp y^{n-1} - sum_d c_d (y_{i-e_d} + y_{i+e_d}),
+//   c0 = 1/tau + sum_d 2/h_d^2, cp = 1/tau (n >= 1) or omega/tau with y^{N} (n = 0).
+struct DfCoef {
+    dfloat c0, ct, cw, cx, cy, cz;
+};
+
+__global__ void __launch_bounds__(RES_THREADS)
+k_residual_df(const float2* __restrict__ y, const double* __restrict__ f, int delta_rhs, int nt, int nx, int ny,
+              int nz, DfCoef k, double f0_scale, float* __restrict__ r_out, double* partials) {
+    __shared__ double sh[32];
+    const long long Nx = (long long)nx * ny * nz;
+    const long long pl = (long long)nx * ny;
+    const int rows = nt * ny * nz;
+    float rr = 0.f, ff = 0.f;
+    auto ld = [&](long long i) { float2 v = y[i]; return dfloat{v.x, v.y}; };
+    for (int row = blockIdx.x; row < rows; row += gridDim.x) {
+        const int t = row / (ny * nz), rz = row - t * (ny * nz);
+        const int iz = rz / ny, iy = rz - iz * ny;
+        const long long base = (long long)row * nx;
+        const long long sbase = base - (long long)t * Nx;
+        for (int ix = threadIdx.x; ix < nx; ix += blockDim.x) {
+            const long long idx = base + ix;
+            dfloat Ay = df_mul(k.c0, ld(idx));
+            dfloat prev = t > 0 ? ld(idx - Nx) : ld((long long)(nt - 1) * Nx + sbase + ix);
+            Ay = df_add(Ay, df_neg(df_mul(t > 0 ? k.ct : k.cw, prev)));
+            dfloat s = {0.f, 0.f};
+            if (ix > 0) s = ld(idx - 1);
+            if (ix < nx - 1) s = df_add(s, ld(idx + 1));
+            Ay = df_add(Ay, df_neg(df_mul(k.cx, s)));
+            if (ny > 1) {
+                s = {0.f, 0.f};
+                if (iy > 0) s = ld(idx - nx);
+                if (iy < ny - 1) s = df_add(s, ld(idx + nx));
+                Ay = df_add(Ay, df_neg(df_mul(k.cy, s)));
+            }
+            if (nz > 1) {
+                s = {0.f, 0.f};
+                if (iz > 0) s = ld(idx - pl);
+                if (iz < nz - 1) s = df_add(s, ld(idx + pl));
+                Ay = df_add(Ay, df_neg(df_mul(k.cz, s)));
+            }
+            dfloat fv = {0.f, 0.f};
+            if (delta_rhs) {
+                if (t == 0) fv = df_from_double(f0_scale * f[sbase + ix]);
+            } else {
+                fv = df_from_double(f[idx]);
+            }
+            dfloat r = df_add(fv, df_neg(Ay));
+            r_out[idx] = r.hi;
+            rr = fmaf(r.hi, r.hi, rr);
+            ff = fmaf(fv.hi, fv.hi, ff);
+        }
+    }
+    double a = block_sum((double)rr, sh);
+    double b = block_sum((double)ff, sh);
+    if (threadIdx.x == 0) {
+        partials[2 * blockIdx.x] = a;
+        partials[2 * blockIdx.x + 1] = b;
+    }
+}
+
+// In place: a double-float array (8 bytes per value) becomes the FP64 array.
+__global__ void k_df_to_double(void* buf, long long n) {
+    const float2* src = reinterpret_cast<const float2*>(buf);
+    double* dst = reinterpret_cast<double*>(buf);
+    for (long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (long long)gridDim.x * blockDim.x) {
+        float2 v = src[i];
+        dst[i] = qbvm_join_df(v.x, v.y);
+    }
+}
+
+static dfloat df_const(double c) {
+    float h = (float)c;
+    return {h, (float)(c - (double)h)};
+}
+
+cudaError_t launch_residual_df(const void* y_df, const double* f, int delta_rhs, const Tables& tb,
+                               const double h2inv[3], float* r_out, double* partials, int nblocks, double* sums,
+                               cudaStream_t s) {
+    DfCoef k;
+    const double it = 1.0 / tb.tau;
+    k.c0 = df_const(it + 2.0 * (h2inv[0] + h2inv[1] + h2inv[2]));
+    k.ct = df_const(it);
+    k.cw = df_const(tb.omega * it);
+    k.cx = df_const(h2inv[0]);
+    k.cy = df_const(h2inv[1]);
+    k.cz = df_const(h2inv[2]);
+    k_residual_df<<<nblocks, RES_THREADS, 0, s>>>(reinterpret_cast<const float2*>(y_df), f, delta_rhs, tb.nt,
+                                                  tb.n[0], tb.n[1], tb.n[2], k, -tb.omega * it, r_out, partials);
+    cudaError_t e = cudaGetLastError();
+    if (e != cudaSuccess) return e;
+    k_reduce_pairs<<<1, 1024, 0, s>>>(partials, nblocks, sums);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_df_to_double(void* buf, long long n, cudaStream_t s) {
+    long long blocks = (n + 1023) / 1024;
+    if (blocks > 152 * 32) blocks = 152 * 32;
+    if (blocks < 1) blocks = 1;
+    k_df_to_double<<<(unsigned)blocks, 256, 0, s>>>(buf, n);
+    return cudaGetLastError();
+}
+
 int residual_blocks(const Tables& tb) {
-    long long total = tb.Nx * tb.nt;
-    long long b = (total + RES_THREADS * 4 - 1) / (RES_THREADS * 4);
+    long long rows = (long long)tb.nt * tb.n[1] * tb.n[2];
+    long long b = rows;
     if (b > 152 * 16) b = 152 * 16;
     if (b < 1) b = 1;
     return (int)b;

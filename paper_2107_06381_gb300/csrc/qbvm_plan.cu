@@ -35,9 +35,8 @@ struct qbvm_plan {
     double* stage_in = nullptr;   // host-pointer staging
     double* stage_out = nullptr;
     // FP32 refinement workspace
-    float* f32 = nullptr;         // [nt][Nx] FP32 work array
+    float* f32 = nullptr;         // [nt][Nx] FP32 work array (and the residual's r.hi)
     float* g32 = nullptr;         // Nx FP32 (delta rhs)
-    double* rbuf = nullptr;       // FP64 residual [nt][Nx]
     long long ws_bytes = 0;
     int last_iters = 0;
     double last_relres = 0.0;
@@ -70,6 +69,7 @@ int validate(const qbvm_desc* d) {
     if (!(d->alpha > 0) && !(d->delta > 0 && std::isfinite(d->delta))) return QBVM_ERR_BAD_ARG;
     // sizes the kernels implement
     if (!is_pow2(d->nt) || d->nt > 1024) return QBVM_ERR_UNSUPPORTED;
+    if (d->precision == QBVM_FP32_REFINE && d->dim == 1) return QBVM_ERR_UNSUPPORTED;
     if (d->dim == 1) {
         if (d->m[0] - 1 > (1 << 20)) return QBVM_ERR_UNSUPPORTED;
     } else {
@@ -168,9 +168,9 @@ int ptr_kind(const void* ptr) {
     return (a.type == cudaMemoryTypeDevice || a.type == cudaMemoryTypeManaged) ? KIND_DEV : KIND_HOST;
 }
 
-#define CK(call)                                    \
+#define CK(...)                                     \
     do {                                            \
-        cudaError_t e__ = (call);                   \
+        cudaError_t e__ = (__VA_ARGS__);            \
         if (e__ != cudaSuccess) return QBVM_ERR_CUDA; \
     } while (0)
 
@@ -194,11 +194,11 @@ int solve_fp64_dev(qbvm_plan_t* p, const double* in, double* y, int n0_only, cud
         double* work;
         if (delta) {
             // DST of g along x, y (, z) -> ghat, then the time solve reads level 0
-            { Span sp_(p, "dst_x", s); CK(qbvm::launch_dst<double>(in, p->ghat, tb.n[0], p->lp[0], ny * nz, 1, tb.tw_s[0], tb.sn_s[0], s)); }
-            { Span sp_(p, "dst_y", s); CK(qbvm::launch_dst<double>(p->ghat, p->ghat, tb.n[1], p->lp[1], nz, nx, tb.tw_s[1], tb.sn_s[1], s)); }
+            { Span sp_(p, "dst_x", s); CK(qbvm::launch_dst<double, double, 0>(in, p->ghat, tb.n[0], p->lp[0], ny * nz, 1, tb.tw_s[0], tb.sn_s[0], s)); }
+            { Span sp_(p, "dst_y", s); CK(qbvm::launch_dst<double, double, 0>(p->ghat, p->ghat, tb.n[1], p->lp[1], nz, nx, tb.tw_s[1], tb.sn_s[1], s)); }
             launches += 2;
             if (tb.dim == 3) {
-                { Span sp_(p, "dst_z", s); CK(qbvm::launch_dst<double>(p->ghat, p->ghat, tb.n[2], p->lp[2], 1, nx * ny, tb.tw_s[2], tb.sn_s[2], s)); }
+                { Span sp_(p, "dst_z", s); CK(qbvm::launch_dst<double, double, 0>(p->ghat, p->ghat, tb.n[2], p->lp[2], 1, nx * ny, tb.tw_s[2], tb.sn_s[2], s)); }
                 ++launches;
             }
             // f^0 = -omega g / tau: fold -omega/tau into the time-solve constant
@@ -208,11 +208,11 @@ int solve_fp64_dev(qbvm_plan_t* p, const double* in, double* y, int n0_only, cud
         } else {
             work = n0_only ? p->wreal : y;
             const long long nt = tb.nt;
-            { Span sp_(p, "dst_x", s); CK(qbvm::launch_dst<double>(in, work, tb.n[0], p->lp[0], nt * ny * nz, 1, tb.tw_s[0], tb.sn_s[0], s)); }
-            { Span sp_(p, "dst_y", s); CK(qbvm::launch_dst<double>(work, work, tb.n[1], p->lp[1], nt * nz, nx, tb.tw_s[1], tb.sn_s[1], s)); }
+            { Span sp_(p, "dst_x", s); CK(qbvm::launch_dst<double, double, 0>(in, work, tb.n[0], p->lp[0], nt * ny * nz, 1, tb.tw_s[0], tb.sn_s[0], s)); }
+            { Span sp_(p, "dst_y", s); CK(qbvm::launch_dst<double, double, 0>(work, work, tb.n[1], p->lp[1], nt * nz, nx, tb.tw_s[1], tb.sn_s[1], s)); }
             launches += 2;
             if (tb.dim == 3) {
-                { Span sp_(p, "dst_z", s); CK(qbvm::launch_dst<double>(work, work, tb.n[2], p->lp[2], nt, nx * ny, tb.tw_s[2], tb.sn_s[2], s)); }
+                { Span sp_(p, "dst_z", s); CK(qbvm::launch_dst<double, double, 0>(work, work, tb.n[2], p->lp[2], nt, nx * ny, tb.tw_s[2], tb.sn_s[2], s)); }
                 ++launches;
             }
             { Span sp_(p, "time_solve", s); CK(qbvm::launch_time_solve<double>(work, y, tb, tb.tau * cn, 0, n0_only, s)); }
@@ -220,16 +220,111 @@ int solve_fp64_dev(qbvm_plan_t* p, const double* in, double* y, int n0_only, cud
         }
         // inverse DST (the (2/M) factors are in the time-solve constant)
         const long long lev = n0_only ? 1 : tb.nt;
-        { Span sp_(p, "dst_x", s); CK(qbvm::launch_dst<double>(y, y, tb.n[0], p->lp[0], lev * ny * nz, 1, tb.tw_s[0], tb.sn_s[0], s)); }
-        { Span sp_(p, "dst_y", s); CK(qbvm::launch_dst<double>(y, y, tb.n[1], p->lp[1], lev * nz, nx, tb.tw_s[1], tb.sn_s[1], s)); }
+        { Span sp_(p, "dst_x", s); CK(qbvm::launch_dst<double, double, 0>(y, y, tb.n[0], p->lp[0], lev * ny * nz, 1, tb.tw_s[0], tb.sn_s[0], s)); }
+        { Span sp_(p, "dst_y", s); CK(qbvm::launch_dst<double, double, 0>(y, y, tb.n[1], p->lp[1], lev * nz, nx, tb.tw_s[1], tb.sn_s[1], s)); }
         launches += 2;
         if (tb.dim == 3) {
-            { Span sp_(p, "dst_z", s); CK(qbvm::launch_dst<double>(y, y, tb.n[2], p->lp[2], lev, nx * ny, tb.tw_s[2], tb.sn_s[2], s)); }
+            { Span sp_(p, "dst_z", s); CK(qbvm::launch_dst<double, double, 0>(y, y, tb.n[2], p->lp[2], lev, nx * ny, tb.tw_s[2], tb.sn_s[2], s)); }
             ++launches;
         }
     }
     p->kernels_per_solve = launches;
     return QBVM_OK;
+}
+
+// --- FP32 transforms + iterative refinement (2D/3D) ---------------------------
+//
+// y_0 = A32^{-1} f;  repeat: r = f - A y, stop when ||r||/||f|| <= tol, else
+// y += A32^{-1} r.  A32^{-1} is the space-first pipeline in FP32 (roots,
+// gamma^t, d_k and tau*Lambda computed in FP64 on the host and rounded once).
+// The iterate y and the residual are carried in double-float (hi + lo, ~48
+// significand bits, computed on the FP32 pipes: GB300 runs FP64 at 1/64 of
+// the FP32 rate); y is stored as float2 pairs in the caller's 8-byte-per-value
+// output array and converted to FP64 in place at the end.
+
+int fp32_solve(qbvm_plan_t* p, const void* rhs, int rhs_fp64, int delta, void* ydf, int accumulate,
+               cudaStream_t s) {
+    const Tables& tb = p->tb;
+    const long long nx = tb.n[0], ny = tb.n[1], nz = tb.n[2], nt = tb.nt;
+    double cn = 1.0;
+    for (int i = 0; i < tb.dim; ++i) cn *= 2.0 / (tb.n[i] + 1);
+    cn /= tb.nt;
+    float* w = p->f32;
+    if (delta) {
+        { Span sp_(p, "dst_x", s); CK(qbvm::launch_dst<float, double, 0>((const double*)rhs, p->g32, tb.n[0], p->lp[0], ny * nz, 1, tb.tw_s32[0], tb.sn_s32[0], s)); }
+        { Span sp_(p, "dst_y", s); CK(qbvm::launch_dst<float, float, 0>(p->g32, p->g32, tb.n[1], p->lp[1], nz, nx, tb.tw_s32[1], tb.sn_s32[1], s)); }
+        if (tb.dim == 3) { Span sp_(p, "dst_z", s); CK(qbvm::launch_dst<float, float, 0>(p->g32, p->g32, tb.n[2], p->lp[2], 1, nx * ny, tb.tw_s32[2], tb.sn_s32[2], s)); }
+        { Span sp_(p, "time_solve", s); CK(qbvm::launch_time_solve<float>(p->g32, w, tb, -tb.omega * cn, 1, 0, s)); }
+    } else {
+        if (rhs_fp64) { Span sp_(p, "dst_x", s); CK(qbvm::launch_dst<float, double, 0>((const double*)rhs, w, tb.n[0], p->lp[0], nt * ny * nz, 1, tb.tw_s32[0], tb.sn_s32[0], s)); }
+        else { Span sp_(p, "dst_x", s); CK(qbvm::launch_dst<float, float, 0>((const float*)rhs, w, tb.n[0], p->lp[0], nt * ny * nz, 1, tb.tw_s32[0], tb.sn_s32[0], s)); }
+        { Span sp_(p, "dst_y", s); CK(qbvm::launch_dst<float, float, 0>(w, w, tb.n[1], p->lp[1], nt * nz, nx, tb.tw_s32[1], tb.sn_s32[1], s)); }
+        if (tb.dim == 3) { Span sp_(p, "dst_z", s); CK(qbvm::launch_dst<float, float, 0>(w, w, tb.n[2], p->lp[2], nt, nx * ny, tb.tw_s32[2], tb.sn_s32[2], s)); }
+        { Span sp_(p, "time_solve", s); CK(qbvm::launch_time_solve<float>(w, w, tb, tb.tau * cn, 0, 0, s)); }
+    }
+    if (tb.dim == 3) { Span sp_(p, "dst_z", s); CK(qbvm::launch_dst<float, float, 0>(w, w, tb.n[2], p->lp[2], nt, nx * ny, tb.tw_s32[2], tb.sn_s32[2], s)); }
+    { Span sp_(p, "dst_y", s); CK(qbvm::launch_dst<float, float, 0>(w, w, tb.n[1], p->lp[1], nt * nz, nx, tb.tw_s32[1], tb.sn_s32[1], s)); }
+    if (accumulate) {
+        Span sp_(p, "dst_x", s);
+        CK(qbvm::launch_dst<float, float, 1>(w, ydf, tb.n[0], p->lp[0], nt * ny * nz, 1, tb.tw_s32[0], tb.sn_s32[0], s));
+    } else {
+        Span sp_(p, "dst_x", s);
+        CK(qbvm::launch_dst<float, float, 2>(w, ydf, tb.n[0], p->lp[0], nt * ny * nz, 1, tb.tw_s32[0], tb.sn_s32[0], s));
+    }
+    return QBVM_OK;
+}
+
+int residual_norm_df(qbvm_plan_t* p, const void* ydf, const double* in, int delta, double* rel, cudaStream_t s) {
+    { Span sp_(p, "residual_df", s); CK(qbvm::launch_residual_df(ydf, in, delta, p->tb, p->h2inv, p->f32, p->partials, p->nres, p->sums, s)); }
+    double h[2] = {0, 0};
+    CK(cudaMemcpyAsync(h, p->sums, sizeof(h), cudaMemcpyDeviceToHost, s));
+    CK(cudaStreamSynchronize(s));
+    if (!std::isfinite(h[0]) || !std::isfinite(h[1])) return QBVM_ERR_NONFINITE;
+    *rel = h[1] > 0 ? std::sqrt(h[0] / h[1]) : std::sqrt(h[0]);
+    return QBVM_OK;
+}
+
+int solve_fp32r_dev(qbvm_plan_t* p, const double* in, double* y, int n0_only, cudaStream_t s) {
+    const Tables& tb = p->tb;
+    const int delta = p->d.rhs_kind == QBVM_RHS_DELTA;
+    double* yfull = n0_only ? p->wreal : y;        // holds the double-float iterate, 8 bytes per value
+    const double tol = p->d.refine_tol > 0 ? p->d.refine_tol : 1e-13;
+    const int maxit = p->d.refine_max_iters > 0 ? p->d.refine_max_iters : 10;
+    int rc = fp32_solve(p, in, 1, delta, yfull, 0, s);
+    if (rc) return rc;
+    const int launches_solve = tb.dim == 3 ? 7 : 5;
+    int launches = launches_solve;
+    double rel = 0.0, prev = INFINITY;
+    int it = 0;
+    int status = QBVM_OK;
+    for (;;) {
+        rc = residual_norm_df(p, yfull, in, delta, &rel, s);     // r.hi lands in p->f32
+        launches += 2;
+        if (rc) return rc;
+        if (rel <= tol) break;
+        if (rel > 0.5 * prev) {
+            // no contraction: the double-float floor if the residual is already tiny,
+            // else the FP32 transforms are too inaccurate for this omega
+            if (rel > 1e-10) status = QBVM_ERR_DIVERGED;
+            break;
+        }
+        if (it >= maxit) {        // still contracting but the cap is reached above tol
+            status = QBVM_ERR_DIVERGED;
+            break;
+        }
+        prev = rel;
+        rc = fp32_solve(p, p->f32, 0, 0, yfull, 1, s);
+        if (rc) return rc;
+        launches += launches_solve;
+        ++it;
+    }
+    { Span sp_(p, "df_to_double", s); CK(qbvm::launch_df_to_double(yfull, tb.Nx * tb.nt, s)); }
+    ++launches;
+    if (n0_only) CK(cudaMemcpyAsync(y, yfull, sizeof(double) * tb.Nx, cudaMemcpyDeviceToDevice, s));
+    p->last_iters = it;
+    p->last_relres = rel;
+    p->kernels_per_solve = launches;
+    return status;
 }
 
 }  // namespace
@@ -313,11 +408,19 @@ int qbvm_plan(const qbvm_desc* desc, qbvm_plan_t** out) {
         double a = M_PI * ((4.0 * m + 1.0) / nt);        // arg(gamma theta^{2m})
         ak[m] = make_double2(1.0 - g1 * std::cos(a), -g1 * std::sin(a));
     }
+    auto to32 = [](const std::vector<double2>& v) {
+        std::vector<float2> o(v.size());
+        for (size_t i = 0; i < v.size(); ++i) o[i] = make_float2((float)v[i].x, (float)v[i].y);
+        return o;
+    };
     rc = upload(p, &tb.tw_t, tw64);
     if (!rc) rc = upload(p, &tb.tw_t32, tw32);
     if (!rc) rc = upload(p, &tb.gpow, gpow);
     if (!rc) rc = upload(p, &tb.gipw, gipw);
     if (!rc) rc = upload(p, &tb.ak, ak);
+    if (!rc) rc = upload(p, &tb.gpow32, to32(gpow));
+    if (!rc) rc = upload(p, &tb.gipw32, to32(gipw));
+    if (!rc) rc = upload(p, &tb.ak32, to32(ak));
     if (!rc && d.dim == 1) {
         bk.resize(H);
         const double h2 = p->h[0] * p->h[0];
@@ -343,6 +446,8 @@ int qbvm_plan(const qbvm_desc* desc, qbvm_plan_t** out) {
                 for (int x = 0; x < tb.n[0]; ++x)
                     lt[idx++] = p->tau * (lam[0][x] + lam[1][yy] + lam[2][z]);
         rc = upload(p, &tb.lamtau, lt);
+        std::vector<float> lt32(lt.begin(), lt.end());
+        if (!rc) rc = upload(p, &tb.lamtau32, lt32);
         for (int i = 0; i < d.dim && !rc; ++i) {
             const int M = d.m[i];
             p->lp[i] = ilog2(M);
@@ -452,13 +557,25 @@ static int ensure_wreal(qbvm_plan_t* p) {
     return dalloc(p, &p->wreal, (size_t)p->tb.Nx * p->tb.nt);
 }
 
+static int ensure_fp32(qbvm_plan_t* p) {
+    const size_t total = (size_t)p->tb.Nx * p->tb.nt;
+    int rc = QBVM_OK;
+    if (!p->f32) rc = dalloc(p, &p->f32, total);
+    if (!rc && !p->g32) rc = dalloc(p, &p->g32, (size_t)p->tb.Nx);
+    return rc;
+}
+
 static int solve_dev(qbvm_plan_t* p, const double* in, double* y, int n0_only, cudaStream_t s) {
-    if (p->tb.dim > 1 && n0_only && p->d.rhs_kind == QBVM_RHS_GENERAL) {
+    const bool refine = p->d.precision == QBVM_FP32_REFINE;
+    if (p->tb.dim > 1 && n0_only && (p->d.rhs_kind == QBVM_RHS_GENERAL || refine)) {
         int rc = ensure_wreal(p);
         if (rc) return rc;
     }
-    if (p->d.precision == QBVM_FP64) return solve_fp64_dev(p, in, y, n0_only, s);
-    return QBVM_ERR_UNSUPPORTED;
+    if (!refine) return solve_fp64_dev(p, in, y, n0_only, s);
+    if (p->tb.dim == 1) return QBVM_ERR_UNSUPPORTED;
+    int rc = ensure_fp32(p);
+    if (rc) return rc;
+    return solve_fp32r_dev(p, in, y, n0_only, s);
 }
 
 int qbvm_solve(qbvm_plan_t* p, const double* g_or_F, double* y, int n0_only, void* stream) {

@@ -1,0 +1,762 @@
+// qbvm_sweep.cu -- batched regularisation-parameter sweep: many PinT-QBVM /
+// PinT-MQBVM instances of uneven size, each solved for a set of alpha values,
+// in ONE persistent kernel launch replayed from a captured CUDA graph.
+//
+// Per instance (delta right-hand side f^0 = -omega g/tau, Sections 3.1/3.2):
+//   A  forward DST-I of g (and of z0 when given) along each axis, FP64;
+//   B  for every alpha and every spatial mode l, the t = 0 output of the
+//      three steps of eq. 3.8 in the sine basis: the forward time transform of
+//      a delta is constant over the even frequencies 2m, Step (b) divides by
+//      d_{2m} + tau Lambda_l, and Step (c) at t = 0 sums over them:
+//          yhat0_l = 2 cnorm ghat_l  sum_m Re 1/(d_{2m} + tau Lambda_l);
+//      the discrepancy ||y^N - g|| follows from the first block row of
+//      eq. 3.3/3.6, y^N - g = -c_alpha (I - tau Lap) y^0 with c = alpha (PQ) or
+//      alpha/tau (PM), and ||S v|| = prod(M/2)^{1/2} ||v|| (Parseval for DST-I);
+//   C  pick alpha by the discrepancy principle: the largest alpha with
+//      ||y^N - g|| <= tau_dp * delta (else the smallest discrepancy);
+//   D-F  y^0 at the picked alpha in FP64: the spectral values, then the
+//      inverse DST along y and x.
+// Stage B runs in the sweep precision (FP64 or FP32); A and D-F in FP64.
+//
+// Work items are queued in topological order and claimed with an atomic
+// ticket; an item whose inputs come from earlier stages waits on per-instance
+// counters.  Every CTA of the grid is resident (the grid is sized from the
+// occupancy calculator), so every item a CTA waits for is held by a running
+// CTA; the waits are bounded anyway and give up with an error flag.
+#include <algorithm>
+#include <chrono>
+#include <cmath>
+#include <cstring>
+#include <new>
+#include <vector>
+
+#include "qbvm.h"
+#include "qbvm_dst.cuh"
+#include "qbvm_internal.h"
+
+namespace {
+
+using qbvm::cplx;
+
+enum Stage { ST_GX = 0, ST_GY, ST_ZX, ST_ZY, ST_SPEC, ST_PICK, ST_FIN, ST_IY, ST_IX, NSTAGE };
+
+constexpr int SW_THREADS = qbvm::TILE_THREADS;
+constexpr long long SPIN_LIMIT = 1ll << 22;      // bounded waits (~0.5 s with the back-off)
+
+struct SwInst {
+    int dim, nx, ny, H, lmx, lmy, n_alpha, form;
+    long long Nx;
+    int tiles_gx, tiles_gy, tiles_spec, tiles_fin, tiles_iy, tiles_ix;
+    int has_z0, has_y0;
+    double delta, tau_dp, tau, wnorm, zscale;
+    const double* g;
+    const double* z0;
+    double* y0;
+    double* ghat;
+    double* zhat;
+    double* yhat;
+    const double* lamx;          // tau * lambda_x (nx)
+    const double* lamy;          // tau * lambda_y (ny), 2D
+    const double2* dtab;         // n_alpha x H: d_{2m}(alpha)
+    const float2* dtab32;
+    const double* cn;            // n_alpha: 2 * cnorm(alpha)
+    const double* coef;          // n_alpha: alpha (PQ) or alpha / tau (PM)
+    const double* alphas;        // n_alpha
+    const double2* twx;
+    const double2* twy;
+    const double* snx;
+    const double* sny;
+    double* stats;               // n_alpha x 2: sum ((1 + tau Lambda) yhat)^2, sum (yhat - zhat)^2
+    double* disc;                // n_alpha outputs
+    double* err;                 // n_alpha outputs (when z0 is given)
+    int* pick;                   // [0] discrepancy pick, [1] smallest-error alpha
+};
+
+__device__ __forceinline__ int ld_volatile(const int* p) { return *(const volatile int*)p; }
+
+// Thread 0 waits until counters[c] >= target; all threads learn the outcome.
+__device__ bool wait_for(const int* counter, int target, int* errflag) {
+    __shared__ int ok;
+    if (threadIdx.x == 0) {
+        long long it = 0;
+        int good = 1;
+        while (ld_volatile(counter) < target) {
+            if (ld_volatile(errflag) != 0 || ++it > SPIN_LIMIT) {
+                good = 0;
+                atomicCAS(errflag, 0, 1);
+                break;
+            }
+            __nanosleep(100);
+        }
+        __threadfence();
+        ok = good;
+    }
+    __syncthreads();
+    int r = ok;
+    __syncthreads();
+    return r != 0;
+}
+
+__device__ double block_sum_d(double v, double* sh) {
+    for (int o = 16; o > 0; o >>= 1) v += __shfl_down_sync(0xffffffffu, v, o);
+    int w = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    __syncthreads();
+    if (lane == 0) sh[w] = v;
+    __syncthreads();
+    v = 0.0;
+    if (threadIdx.x < (blockDim.x >> 5)) v = sh[threadIdx.x];
+    if (w == 0)
+        for (int o = 16; o > 0; o >>= 1) v += __shfl_down_sync(0xffffffffu, v, o);
+    return v;
+}
+
+// Stage B: one tile of SW_THREADS * MPT modes, every alpha, precision R.
+template <typename R, int MPT>
+__device__ void spectral_tile(const SwInst& I, int tile, unsigned char* smem) {
+    using C = cplx<R>;
+    __shared__ double sh[32];
+    C* sd = reinterpret_cast<C*>(smem);
+    const C* dt = reinterpret_cast<const C*>(std::is_same<R, double>::value ? (const void*)I.dtab
+                                                                           : (const void*)I.dtab32);
+    R lam[MPT], gh[MPT], zh[MPT];
+    bool valid[MPT];
+#pragma unroll
+    for (int q = 0; q < MPT; ++q) {
+        long long l = (long long)tile * SW_THREADS * MPT + q * SW_THREADS + threadIdx.x;
+        valid[q] = l < I.Nx;
+        lam[q] = gh[q] = zh[q] = R(0);
+        if (valid[q]) {
+            int lx = (int)(l % I.nx), ly = (int)(l / I.nx);
+            double lt = __ldcg(I.lamx + lx) + (I.dim == 2 ? __ldcg(I.lamy + ly) : 0.0);
+            lam[q] = R(lt);
+            gh[q] = R(__ldcg(I.ghat + l));
+            if (I.has_z0) zh[q] = R(__ldcg(I.zhat + l) * I.zscale);
+        }
+    }
+    for (int a = 0; a < I.n_alpha; ++a) {
+        __syncthreads();
+        for (int m = threadIdx.x; m < I.H; m += blockDim.x) sd[m] = dt[(long long)a * I.H + m];
+        __syncthreads();
+        R s[MPT];
+#pragma unroll
+        for (int q = 0; q < MPT; ++q) s[q] = R(0);
+        for (int m = 0; m < I.H; ++m) {
+            C d = sd[m];
+#pragma unroll
+            for (int q = 0; q < MPT; ++q) {
+                R zr = d.x + lam[q];
+                s[q] += zr / (zr * zr + d.y * d.y);
+            }
+        }
+        const R cna = R(I.cn[a]);
+        double dsum = 0.0, esum = 0.0;
+#pragma unroll
+        for (int q = 0; q < MPT; ++q) {
+            if (!valid[q]) continue;
+            R y = cna * gh[q] * s[q];
+            R dv = (R(1) + lam[q]) * y;
+            dsum += (double)dv * (double)dv;
+            if (I.has_z0) {
+                R e = y - zh[q];
+                esum += (double)e * (double)e;
+            }
+        }
+        dsum = block_sum_d(dsum, sh);
+        esum = block_sum_d(esum, sh);
+        if (threadIdx.x == 0) {
+            atomicAdd(I.stats + 2 * a, dsum);
+            if (I.has_z0) atomicAdd(I.stats + 2 * a + 1, esum);
+        }
+    }
+}
+
+// Stage C: discrepancy principle on one instance (single thread).
+__device__ void pick_alpha(const SwInst& I) {
+    if (threadIdx.x != 0) return;
+    int pick = -1, best = 0, closest = 0;
+    double bestv = INFINITY, closev = INFINITY;
+    for (int a = 0; a < I.n_alpha; ++a) {
+        double d2 = __ldcg(I.stats + 2 * a), e2 = __ldcg(I.stats + 2 * a + 1);
+        double dsc = I.coef[a] * sqrt(I.wnorm * d2);
+        I.disc[a] = dsc;
+        if (I.has_z0) {
+            double ev = sqrt(I.wnorm * e2);
+            I.err[a] = ev;
+            if (ev < bestv) {
+                bestv = ev;
+                best = a;
+            }
+        }
+        if (dsc <= I.tau_dp * I.delta && (pick < 0 || I.alphas[a] > I.alphas[pick])) pick = a;
+        if (dsc < closev) {
+            closev = dsc;
+            closest = a;
+        }
+    }
+    I.pick[0] = pick >= 0 ? pick : closest;
+    I.pick[1] = best;
+    __threadfence();
+}
+
+// Stage D: FP64 spectral y^0 at the picked alpha for one tile of modes.
+__device__ void final_tile(const SwInst& I, int tile) {
+    const int a = __ldcg(I.pick);
+    const long long l = (long long)tile * SW_THREADS + threadIdx.x;
+    if (l >= I.Nx) return;
+    const int lx = (int)(l % I.nx), ly = (int)(l / I.nx);
+    const double lt = I.lamx[lx] + (I.dim == 2 ? I.lamy[ly] : 0.0);
+    double s = 0.0;
+    const double2* dt = I.dtab + (long long)a * I.H;
+    for (int m = 0; m < I.H; ++m) {
+        double2 d = dt[m];
+        double zr = d.x + lt;
+        s += zr / fma(zr, zr, d.y * d.y);
+    }
+    I.yhat[l] = I.cn[a] * __ldcg(I.ghat + l) * s;
+}
+
+struct SwRun {
+    const SwInst* inst;
+    const int4* items;
+    int nitems;
+    int* counters;       // count x NSTAGE
+    int* next;
+    int* errflag;
+};
+
+template <typename R, int MPT>
+__global__ void __launch_bounds__(SW_THREADS) k_sweep(SwRun run) {
+    extern __shared__ __align__(16) unsigned char smem[];
+    __shared__ int s_item;
+    __shared__ SwInst I;
+    for (;;) {
+        if (threadIdx.x == 0) s_item = ld_volatile(run.errflag) ? run.nitems : atomicAdd(run.next, 1);
+        __syncthreads();
+        const int it = s_item;
+        if (it >= run.nitems) return;
+        const int4 w = run.items[it];
+        if (threadIdx.x == 0) I = run.inst[w.y];
+        __syncthreads();
+        int* cnt = run.counters + (long long)w.y * NSTAGE;
+        bool ok = true;
+        switch (w.x) {
+            case ST_GY: ok = wait_for(cnt + ST_GX, I.tiles_gx, run.errflag); break;
+            case ST_ZY: ok = wait_for(cnt + ST_ZX, I.tiles_gx, run.errflag); break;
+            case ST_SPEC:
+                ok = wait_for(cnt + (I.dim == 2 ? ST_GY : ST_GX), I.dim == 2 ? I.tiles_gy : I.tiles_gx, run.errflag);
+                if (ok && I.has_z0)
+                    ok = wait_for(cnt + (I.dim == 2 ? ST_ZY : ST_ZX), I.dim == 2 ? I.tiles_gy : I.tiles_gx, run.errflag);
+                break;
+            case ST_PICK: ok = wait_for(cnt + ST_SPEC, I.tiles_spec, run.errflag); break;
+            case ST_FIN: ok = wait_for(cnt + ST_PICK, 1, run.errflag); break;
+            case ST_IY: ok = wait_for(cnt + ST_FIN, I.tiles_fin, run.errflag); break;
+            case ST_IX:
+                ok = I.dim == 2 ? wait_for(cnt + ST_IY, I.tiles_iy, run.errflag)
+                                : wait_for(cnt + ST_FIN, I.tiles_fin, run.errflag);
+                break;
+            default: break;
+        }
+        if (!ok) return;
+        switch (w.x) {
+            case ST_GX:       // x-DST of g, one level: rows = ny
+                qbvm::dst_tile<double, double, 0, qbvm::DST_TILE / 4 / SW_THREADS, false>(
+                    I.g, I.ghat, I.nx, I.lmx, qbvm::dst_lw(I.lmx), I.ny, 1, w.z, I.twx, I.snx, smem);
+                break;
+            case ST_GY:
+                qbvm::dst_tile<double, double, 0, qbvm::DST_TILE / 4 / SW_THREADS, true>(
+                    I.ghat, I.ghat, I.ny, I.lmy, qbvm::dst_lw(I.lmy), 1, I.nx, w.z, I.twy, I.sny, smem);
+                break;
+            case ST_ZX:
+                qbvm::dst_tile<double, double, 0, qbvm::DST_TILE / 4 / SW_THREADS, false>(
+                    I.z0, I.zhat, I.nx, I.lmx, qbvm::dst_lw(I.lmx), I.ny, 1, w.z, I.twx, I.snx, smem);
+                break;
+            case ST_ZY:
+                qbvm::dst_tile<double, double, 0, qbvm::DST_TILE / 4 / SW_THREADS, true>(
+                    I.zhat, I.zhat, I.ny, I.lmy, qbvm::dst_lw(I.lmy), 1, I.nx, w.z, I.twy, I.sny, smem);
+                break;
+            case ST_SPEC: spectral_tile<R, MPT>(I, w.z, smem); break;
+            case ST_PICK: pick_alpha(I); break;
+            case ST_FIN: final_tile(I, w.z); break;
+            case ST_IY:
+                qbvm::dst_tile<double, double, 0, qbvm::DST_TILE / 4 / SW_THREADS, true>(
+                    I.yhat, I.yhat, I.ny, I.lmy, qbvm::dst_lw(I.lmy), 1, I.nx, w.z, I.twy, I.sny, smem);
+                break;
+            case ST_IX:
+                qbvm::dst_tile<double, double, 0, qbvm::DST_TILE / 4 / SW_THREADS, true>(
+                    I.yhat, I.y0, I.nx, I.lmx, qbvm::dst_lw(I.lmx), I.ny, 1, w.z, I.twx, I.snx, smem);
+                break;
+            default: break;
+        }
+        __syncthreads();
+        if (threadIdx.x == 0) {
+            __threadfence();
+            atomicAdd(cnt + w.x, 1);
+        }
+    }
+}
+
+// (The shared-memory attribute is set by max_resident in configure(), outside
+// any stream capture.)
+template <typename R, int MPT>
+cudaError_t launch_sweep(const SwRun& run, int grid, size_t smem, cudaStream_t s) {
+    k_sweep<R, MPT><<<grid, SW_THREADS, smem, s>>>(run);
+    return cudaGetLastError();
+}
+
+template <typename R, int MPT>
+int max_resident(size_t smem) {
+    int per_sm = 0, sms = 0, dev = 0;
+    cudaGetDevice(&dev);
+    cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+    auto kern = k_sweep<R, MPT>;
+    cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kern, SW_THREADS, smem) != cudaSuccess) {
+        cudaGetLastError();
+        return 0;
+    }
+    return per_sm * sms;
+}
+
+}  // namespace
+
+struct qbvm_sweep {
+    int count = 0, n_alpha = 0, precision = 0;
+    std::vector<SwInst> host_inst;
+    std::vector<void*> allocs;
+    SwInst* d_inst = nullptr;
+    int4* d_items = nullptr;
+    int nitems = 0;
+    int* d_counters = nullptr;
+    int* d_next = nullptr;
+    int* d_err = nullptr;
+    double* d_stats = nullptr;
+    double* d_disc = nullptr;
+    double* d_err_out = nullptr;
+    double* d_alphas = nullptr;
+    int* d_pick = nullptr;
+    size_t stats_bytes = 0;
+    size_t smem = 0;
+    // launch configuration (autotuned): modes per thread in stage B, CTAs per SM
+    int mpt = 1, ctas_per_sm = 0;
+    int grid = 0;
+    int spec_tiles_total = 0;
+    cudaGraphExec_t graph = nullptr;
+    cudaStream_t graph_stream = nullptr;
+    bool graph_valid = false;
+    float last_ms = 0.f;
+    int last_error = 0;
+};
+
+namespace {
+
+template <typename T>
+int sw_alloc(qbvm_sweep_t* p, T** ptr, size_t count) {
+    *ptr = nullptr;
+    if (!count) return QBVM_OK;
+    void* v = nullptr;
+    if (cudaMalloc(&v, count * sizeof(T)) != cudaSuccess) {
+        cudaGetLastError();
+        return QBVM_ERR_OOM;
+    }
+    p->allocs.push_back(v);
+    *ptr = static_cast<T*>(v);
+    return QBVM_OK;
+}
+
+template <typename T>
+int sw_upload(qbvm_sweep_t* p, T** ptr, const std::vector<T>& h) {
+    int rc = sw_alloc(p, ptr, h.size());
+    if (rc) return rc;
+    return cudaMemcpy(*ptr, h.data(), h.size() * sizeof(T), cudaMemcpyHostToDevice) == cudaSuccess ? QBVM_OK
+                                                                                                   : QBVM_ERR_CUDA;
+}
+
+void sw_destroy(qbvm_sweep_t* p) {
+    if (!p) return;
+    if (p->graph) cudaGraphExecDestroy(p->graph);
+    for (void* v : p->allocs) cudaFree(v);
+    delete p;
+}
+
+bool pow2(int v) { return v > 0 && (v & (v - 1)) == 0; }
+int lg2(int v) {
+    int l = 0;
+    while ((1 << l) < v) ++l;
+    return l;
+}
+
+int configure(qbvm_sweep_t* p, int mpt, int ctas_per_sm) {
+    // spectral tiles depend on the modes per tile
+    std::vector<int4> items;
+    int total_spec = 0;
+    for (int i = 0; i < p->count; ++i) {
+        SwInst& I = p->host_inst[i];
+        I.tiles_spec = (int)((I.Nx + (long long)SW_THREADS * mpt - 1) / ((long long)SW_THREADS * mpt));
+        total_spec += I.tiles_spec;
+    }
+    // the final stage (one alpha, FP64) uses one mode per thread
+    for (int i = 0; i < p->count; ++i)
+        p->host_inst[i].tiles_fin = (int)((p->host_inst[i].Nx + SW_THREADS - 1) / SW_THREADS);
+    for (int st = 0; st < NSTAGE; ++st) {
+        for (int i = 0; i < p->count; ++i) {
+            const SwInst& I = p->host_inst[i];
+            int n = 0;
+            switch (st) {
+                case ST_GX: n = I.tiles_gx; break;
+                case ST_GY: n = I.dim == 2 ? I.tiles_gy : 0; break;
+                case ST_ZX: n = I.has_z0 ? I.tiles_gx : 0; break;
+                case ST_ZY: n = (I.has_z0 && I.dim == 2) ? I.tiles_gy : 0; break;
+                case ST_SPEC: n = I.tiles_spec; break;
+                case ST_PICK: n = 1; break;
+                case ST_FIN: n = I.has_y0 ? I.tiles_fin : 0; break;
+                case ST_IY: n = (I.has_y0 && I.dim == 2) ? I.tiles_iy : 0; break;
+                case ST_IX: n = I.has_y0 ? I.tiles_ix : 0; break;
+            }
+            for (int t = 0; t < n; ++t) items.push_back(make_int4(st, i, t, 0));
+        }
+    }
+    p->nitems = (int)items.size();
+    p->spec_tiles_total = total_spec;
+    if (p->d_items) {
+        cudaFree(p->d_items);
+        p->allocs.erase(std::find(p->allocs.begin(), p->allocs.end(), (void*)p->d_items));
+        p->d_items = nullptr;
+    }
+    int rc = sw_upload(p, &p->d_items, items);
+    if (rc) return rc;
+    if (cudaMemcpy(p->d_inst, p->host_inst.data(), sizeof(SwInst) * p->count, cudaMemcpyHostToDevice) != cudaSuccess)
+        return QBVM_ERR_CUDA;
+    // resident grid
+    int maxres = 0;
+    if (p->precision == QBVM_FP64) {
+        maxres = mpt == 1 ? max_resident<double, 1>(p->smem) : mpt == 2 ? max_resident<double, 2>(p->smem)
+                                                                         : max_resident<double, 4>(p->smem);
+    } else {
+        maxres = mpt == 1 ? max_resident<float, 1>(p->smem) : mpt == 2 ? max_resident<float, 2>(p->smem)
+                                                                        : max_resident<float, 4>(p->smem);
+    }
+    if (maxres <= 0) return QBVM_ERR_UNSUPPORTED;
+    int sms = 0, dev = 0;
+    cudaGetDevice(&dev);
+    cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+    int want = ctas_per_sm > 0 ? ctas_per_sm * sms : maxres;
+    p->grid = std::min(want, maxres);
+    p->mpt = mpt;
+    p->ctas_per_sm = ctas_per_sm;
+    if (p->graph) {
+        cudaGraphExecDestroy(p->graph);
+        p->graph = nullptr;
+    }
+    p->graph_valid = false;
+    return QBVM_OK;
+}
+
+int enqueue(qbvm_sweep_t* p, cudaStream_t s) {
+    const size_t cnt_bytes = sizeof(int) * ((size_t)p->count * NSTAGE + 2);
+    if (cudaMemsetAsync(p->d_counters, 0, cnt_bytes, s) != cudaSuccess) return QBVM_ERR_CUDA;
+    if (cudaMemsetAsync(p->d_stats, 0, p->stats_bytes, s) != cudaSuccess) return QBVM_ERR_CUDA;
+    SwRun run{p->d_inst, p->d_items, p->nitems, p->d_counters, p->d_next, p->d_err};
+    cudaError_t e;
+    if (p->precision == QBVM_FP64) {
+        e = p->mpt == 1 ? launch_sweep<double, 1>(run, p->grid, p->smem, s)
+            : p->mpt == 2 ? launch_sweep<double, 2>(run, p->grid, p->smem, s)
+                          : launch_sweep<double, 4>(run, p->grid, p->smem, s);
+    } else {
+        e = p->mpt == 1 ? launch_sweep<float, 1>(run, p->grid, p->smem, s)
+            : p->mpt == 2 ? launch_sweep<float, 2>(run, p->grid, p->smem, s)
+                          : launch_sweep<float, 4>(run, p->grid, p->smem, s);
+    }
+    return e == cudaSuccess ? QBVM_OK : QBVM_ERR_CUDA;
+}
+
+// Capture the run (counter reset + persistent launch) into a graph once.
+int run_graph(qbvm_sweep_t* p, cudaStream_t s) {
+    if (!p->graph_valid || p->graph_stream != s) {
+        if (p->graph) {
+            cudaGraphExecDestroy(p->graph);
+            p->graph = nullptr;
+        }
+        cudaStream_t cs = s;
+        bool own = false;
+        if (cs == nullptr) {        // the legacy default stream cannot be captured: use a private one
+            if (cudaStreamCreateWithFlags(&cs, cudaStreamNonBlocking) != cudaSuccess) return QBVM_ERR_CUDA;
+            own = true;
+        }
+        cudaGraph_t g = nullptr;
+        if (cudaStreamBeginCapture(cs, cudaStreamCaptureModeThreadLocal) != cudaSuccess) return QBVM_ERR_CUDA;
+        int rc = enqueue(p, cs);
+        cudaError_t e = cudaStreamEndCapture(cs, &g);
+        if (rc || e != cudaSuccess) {
+            if (g) cudaGraphDestroy(g);
+            if (own) cudaStreamDestroy(cs);
+            cudaGetLastError();
+            return rc ? rc : QBVM_ERR_CUDA;
+        }
+        e = cudaGraphInstantiate(&p->graph, g, 0);
+        cudaGraphDestroy(g);
+        if (own) cudaStreamDestroy(cs);
+        if (e != cudaSuccess) return QBVM_ERR_CUDA;
+        p->graph_valid = true;
+        p->graph_stream = s;
+    }
+    return cudaGraphLaunch(p->graph, s) == cudaSuccess ? QBVM_OK : QBVM_ERR_CUDA;
+}
+
+}  // namespace
+
+extern "C" {
+
+int qbvm_sweep_plan(const qbvm_sweep_desc* d, qbvm_sweep_t** out) {
+    if (!out) return QBVM_ERR_BAD_ARG;
+    *out = nullptr;
+    if (!d || d->count < 1 || !d->inst || d->n_alpha < 1 || d->n_alpha > 64) return QBVM_ERR_BAD_ARG;
+    if (d->precision != QBVM_FP64 && d->precision != QBVM_FP32_REFINE) return QBVM_ERR_BAD_ARG;
+    if (!(d->tau_dp > 0) || !std::isfinite(d->log10_lo) || !std::isfinite(d->log10_hi)) return QBVM_ERR_BAD_ARG;
+    for (int i = 0; i < d->count; ++i) {
+        const qbvm_sweep_instance& in = d->inst[i];
+        if (in.dim < 1 || in.dim > 2 || !in.g) return QBVM_ERR_BAD_ARG;
+        if (!(in.T > 0) || !(in.L > 0) || !(in.delta > 0) || in.nt < 2) return QBVM_ERR_BAD_ARG;
+        if (in.form != QBVM_FORM_PQ && in.form != QBVM_FORM_PM) return QBVM_ERR_BAD_ARG;
+        if (!pow2(in.nt) || in.nt > 1024) return QBVM_ERR_UNSUPPORTED;
+        for (int a = 0; a < in.dim; ++a)
+            if (!pow2(in.m[a]) || in.m[a] < 4 || in.m[a] > 2048) return QBVM_ERR_UNSUPPORTED;
+    }
+    qbvm_sweep_t* p = new (std::nothrow) qbvm_sweep();
+    if (!p) return QBVM_ERR_OOM;
+    p->count = d->count;
+    p->n_alpha = d->n_alpha;
+    p->precision = d->precision;
+    p->host_inst.resize(d->count);
+    int rc = QBVM_OK;
+    const int na = d->n_alpha;
+    rc = sw_alloc(p, &p->d_stats, (size_t)d->count * na * 2);
+    p->stats_bytes = sizeof(double) * (size_t)d->count * na * 2;
+    if (!rc) rc = sw_alloc(p, &p->d_disc, (size_t)d->count * na);
+    if (!rc) rc = sw_alloc(p, &p->d_err_out, (size_t)d->count * na);
+    if (!rc) rc = sw_alloc(p, &p->d_pick, (size_t)d->count * 2);
+    if (!rc) rc = sw_alloc(p, &p->d_counters, (size_t)d->count * NSTAGE + 2);
+    if (!rc) {
+        p->d_next = p->d_counters + (size_t)d->count * NSTAGE;
+        p->d_err = p->d_next + 1;
+    }
+    if (!rc) rc = sw_alloc(p, &p->d_inst, (size_t)d->count);
+    std::vector<double> alphas_all((size_t)d->count * na);
+    size_t smem = 0;
+    for (int i = 0; i < d->count && !rc; ++i) {
+        const qbvm_sweep_instance& in = d->inst[i];
+        SwInst& I = p->host_inst[i];
+        std::memset(&I, 0, sizeof(I));
+        I.dim = in.dim;
+        I.form = in.form;
+        I.nx = in.m[0] - 1;
+        I.ny = in.dim == 2 ? in.m[1] - 1 : 1;
+        I.lmx = lg2(in.m[0]);
+        I.lmy = in.dim == 2 ? lg2(in.m[1]) : 0;
+        I.Nx = (long long)I.nx * I.ny;
+        I.H = in.nt / 2;
+        I.n_alpha = na;
+        I.delta = in.delta;
+        I.tau_dp = d->tau_dp;
+        I.tau = in.T / (in.nt - 1);
+        const double hx = in.L / in.m[0], hy = in.dim == 2 ? in.L / in.m[1] : 1.0;
+        // ||S v||^2 = prod(M/2) ||v||^2, times the grid weight prod(h)
+        I.wnorm = (in.L / 2.0) * (in.dim == 2 ? in.L / 2.0 : 1.0);
+        I.zscale = (2.0 / in.m[0]) * (in.dim == 2 ? 2.0 / in.m[1] : 1.0);
+        I.g = in.g;
+        I.z0 = in.z0;
+        I.y0 = in.y0;
+        I.has_z0 = in.z0 != nullptr;
+        I.has_y0 = in.y0 != nullptr;
+        const int lwx = qbvm::dst_lw(I.lmx), lwy = in.dim == 2 ? qbvm::dst_lw(I.lmy) : 0;
+        I.tiles_gx = (int)((I.ny + 2 * (1 << lwx) - 1) / (2 * (1 << lwx)));
+        I.tiles_ix = I.tiles_gx;
+        I.tiles_gy = in.dim == 2 ? (int)((I.nx + 2 * (1 << lwy) - 1) / (2 * (1 << lwy))) : 0;
+        I.tiles_iy = I.tiles_gy;
+        smem = std::max(smem, qbvm::dst_smem<double>(I.lmx));
+        if (in.dim == 2) smem = std::max(smem, qbvm::dst_smem<double>(I.lmy));
+        smem = std::max(smem, sizeof(double2) * (size_t)I.H);
+        // tables (FP64 on the host)
+        std::vector<double> lx(I.nx), ly(I.ny, 0.0);
+        for (int k = 1; k <= I.nx; ++k) {
+            double s = std::sin(M_PI * k / (2.0 * in.m[0]));
+            lx[k - 1] = I.tau * 4.0 / (hx * hx) * s * s;
+        }
+        if (in.dim == 2)
+            for (int k = 1; k <= I.ny; ++k) {
+                double s = std::sin(M_PI * k / (2.0 * in.m[1]));
+                ly[k - 1] = I.tau * 4.0 / (hy * hy) * s * s;
+            }
+        std::vector<double2> dtab((size_t)na * I.H);
+        std::vector<float2> dtab32((size_t)na * I.H);
+        std::vector<double> cn(na), coef(na), al(na);
+        const double rule = in.form == QBVM_FORM_PQ ? in.delta : I.tau * in.delta;   // Section 5
+        for (int a = 0; a < na; ++a) {
+            double ex = na > 1 ? d->log10_lo + (d->log10_hi - d->log10_lo) * a / (na - 1) : d->log10_lo;
+            double alpha = rule * std::pow(10.0, ex);
+            al[a] = alpha;
+            alphas_all[(size_t)i * na + a] = alpha;
+            double omega = in.form == QBVM_FORM_PQ ? -1.0 / alpha : -I.tau / alpha;
+            double g1 = std::pow(std::fabs(omega), 1.0 / in.nt);
+            for (int m = 0; m < I.H; ++m) {
+                double ang = M_PI * ((4.0 * m + 1.0) / in.nt);
+                double2 v = make_double2(1.0 - g1 * std::cos(ang), -g1 * std::sin(ang));
+                dtab[(size_t)a * I.H + m] = v;
+                dtab32[(size_t)a * I.H + m] = make_float2((float)v.x, (float)v.y);
+            }
+            // 2 cnorm with cnorm = -omega * prod(2/M) / nt (the delta right-hand side)
+            cn[a] = 2.0 * (-omega) * I.zscale / in.nt;
+            coef[a] = in.form == QBVM_FORM_PQ ? alpha : alpha / I.tau;
+        }
+        double *dlx, *dly, *dcn, *dcoef, *dal, *sn_x, *sn_y;
+        double2 *ddt, *twx, *twy;
+        float2* ddt32;
+        rc = sw_upload(p, &dlx, lx);
+        if (!rc) rc = sw_upload(p, &dly, ly);
+        if (!rc) rc = sw_upload(p, &ddt, dtab);
+        if (!rc) rc = sw_upload(p, &ddt32, dtab32);
+        if (!rc) rc = sw_upload(p, &dcn, cn);
+        if (!rc) rc = sw_upload(p, &dcoef, coef);
+        if (!rc) rc = sw_upload(p, &dal, al);
+        auto dst_tables = [&](int M, double2** tw, double** sn) {
+            std::vector<double2> w(M);
+            std::vector<double> sv(M / 2 + 2, 0.0);
+            for (int m = 0; m < M; ++m) {
+                double a = M_PI * (2.0 * m / M);
+                w[m] = make_double2(std::cos(a), -std::sin(a));
+            }
+            for (int j = 0; j <= M / 2; ++j) sv[j] = std::sin(M_PI * j / M);
+            int r = sw_upload(p, tw, w);
+            if (!r) r = sw_upload(p, sn, sv);
+            return r;
+        };
+        if (!rc) rc = dst_tables(in.m[0], &twx, &sn_x);
+        twy = twx;
+        sn_y = sn_x;
+        if (!rc && in.dim == 2) rc = dst_tables(in.m[1], &twy, &sn_y);
+        double *gh, *zh = nullptr, *yh = nullptr;
+        if (!rc) rc = sw_alloc(p, &gh, (size_t)I.Nx);
+        if (!rc && I.has_z0) rc = sw_alloc(p, &zh, (size_t)I.Nx);
+        if (!rc && I.has_y0) rc = sw_alloc(p, &yh, (size_t)I.Nx);
+        if (rc) break;
+        I.lamx = dlx;
+        I.lamy = dly;
+        I.dtab = ddt;
+        I.dtab32 = ddt32;
+        I.cn = dcn;
+        I.coef = dcoef;
+        I.alphas = dal;
+        I.twx = twx;
+        I.twy = twy;
+        I.snx = sn_x;
+        I.sny = sn_y;
+        I.ghat = gh;
+        I.zhat = zh;
+        I.yhat = yh;
+        I.stats = p->d_stats + (size_t)i * na * 2;
+        I.disc = p->d_disc + (size_t)i * na;
+        I.err = p->d_err_out + (size_t)i * na;
+        I.pick = p->d_pick + (size_t)i * 2;
+    }
+    if (!rc) rc = sw_upload(p, &p->d_alphas, alphas_all);
+    p->smem = smem;
+    if (!rc) rc = configure(p, 1, 0);
+    if (rc) {
+        sw_destroy(p);
+        return rc;
+    }
+    *out = p;
+    return QBVM_OK;
+}
+
+int qbvm_sweep_run(qbvm_sweep_t* p, void* stream) {
+    if (!p) return QBVM_ERR_BAD_ARG;
+    return run_graph(p, static_cast<cudaStream_t>(stream));
+}
+
+int qbvm_sweep_read(qbvm_sweep_t* p, double* alphas, double* discrepancy, double* error, int* pick, void* stream) {
+    if (!p) return QBVM_ERR_BAD_ARG;
+    cudaStream_t s = static_cast<cudaStream_t>(stream);
+    const size_t n = (size_t)p->count * p->n_alpha;
+    int errflag = 0;
+    if (cudaMemcpyAsync(&errflag, p->d_err, sizeof(int), cudaMemcpyDeviceToHost, s) != cudaSuccess)
+        return QBVM_ERR_CUDA;
+    if (alphas && cudaMemcpyAsync(alphas, p->d_alphas, n * sizeof(double), cudaMemcpyDeviceToHost, s) != cudaSuccess)
+        return QBVM_ERR_CUDA;
+    if (discrepancy && cudaMemcpyAsync(discrepancy, p->d_disc, n * sizeof(double), cudaMemcpyDeviceToHost, s) != cudaSuccess)
+        return QBVM_ERR_CUDA;
+    if (error && cudaMemcpyAsync(error, p->d_err_out, n * sizeof(double), cudaMemcpyDeviceToHost, s) != cudaSuccess)
+        return QBVM_ERR_CUDA;
+    if (pick && cudaMemcpyAsync(pick, p->d_pick, 2 * p->count * sizeof(int), cudaMemcpyDeviceToHost, s) != cudaSuccess)
+        return QBVM_ERR_CUDA;
+    if (cudaStreamSynchronize(s) != cudaSuccess) return QBVM_ERR_CUDA;
+    return errflag ? QBVM_ERR_TIMEOUT : QBVM_OK;
+}
+
+int qbvm_sweep_autotune(qbvm_sweep_t* p, int repeats, qbvm_sweep_config* best_out, void* stream) {
+    if (!p || repeats < 1) return QBVM_ERR_BAD_ARG;
+    cudaStream_t s = static_cast<cudaStream_t>(stream);
+    const int mpts[3] = {1, 2, 4};
+    const int ctas[3] = {0, 1, 2};       // 0 = every resident slot
+    float best = INFINITY;
+    int bm = 1, bc = 0;
+    cudaEvent_t e0, e1;
+    if (cudaEventCreate(&e0) != cudaSuccess || cudaEventCreate(&e1) != cudaSuccess) return QBVM_ERR_CUDA;
+    int rc = QBVM_OK;
+    for (int mi = 0; mi < 3 && !rc; ++mi)
+        for (int ci = 0; ci < 3 && !rc; ++ci) {
+            rc = configure(p, mpts[mi], ctas[ci]);
+            if (rc) break;
+            rc = run_graph(p, s);                         // warm-up + capture
+            if (rc) break;
+            cudaEventRecord(e0, s);
+            for (int r = 0; r < repeats && !rc; ++r) rc = run_graph(p, s);
+            cudaEventRecord(e1, s);
+            if (cudaEventSynchronize(e1) != cudaSuccess) rc = QBVM_ERR_CUDA;
+            float ms = 0.f;
+            cudaEventElapsedTime(&ms, e0, e1);
+            int errflag = 0;
+            cudaMemcpy(&errflag, p->d_err, sizeof(int), cudaMemcpyDeviceToHost);
+            if (errflag) rc = QBVM_ERR_TIMEOUT;
+            if (!rc && ms / repeats < best) {
+                best = ms / repeats;
+                bm = mpts[mi];
+                bc = ctas[ci];
+            }
+        }
+    cudaEventDestroy(e0);
+    cudaEventDestroy(e1);
+    if (rc) return rc;
+    rc = configure(p, bm, bc);
+    if (rc) return rc;
+    p->last_ms = best;
+    if (best_out) {
+        best_out->modes_per_thread = bm;
+        best_out->ctas_per_sm = bc;
+        best_out->grid = p->grid;
+        best_out->ms = best;
+    }
+    return QBVM_OK;
+}
+
+int qbvm_sweep_set_config(qbvm_sweep_t* p, const qbvm_sweep_config* cfg) {
+    if (!p || !cfg) return QBVM_ERR_BAD_ARG;
+    if (cfg->modes_per_thread != 1 && cfg->modes_per_thread != 2 && cfg->modes_per_thread != 4) return QBVM_ERR_BAD_ARG;
+    if (cfg->ctas_per_sm < 0 || cfg->ctas_per_sm > 32) return QBVM_ERR_BAD_ARG;
+    return configure(p, cfg->modes_per_thread, cfg->ctas_per_sm);
+}
+
+int qbvm_sweep_get_config(const qbvm_sweep_t* p, qbvm_sweep_config* cfg) {
+    if (!p || !cfg) return QBVM_ERR_BAD_ARG;
+    cfg->modes_per_thread = p->mpt;
+    cfg->ctas_per_sm = p->ctas_per_sm;
+    cfg->grid = p->grid;
+    cfg->ms = p->last_ms;
+    return QBVM_OK;
+}
+
+int qbvm_sweep_destroy(qbvm_sweep_t* p) {
+    sw_destroy(p);
+    return QBVM_OK;
+}
+
+}  // extern "C"

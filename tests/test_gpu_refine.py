@@ -1,0 +1,122 @@
+"""FP32 transforms with FP64 iterative refinement (precision QBVM_FP32_REFINE).
+
+The refined solution must match the CPU FP64 oracle to the same 1e-10 relative
+L2 bound as the FP64 path; the refinement statistics are reported through
+qbvm_plan_info.
+"""
+import numpy as np
+import pytest
+
+import bhcp_inputs as bi
+import oracle as O
+
+pytestmark = pytest.mark.gpu
+torch = pytest.importorskip("torch")
+if not torch.cuda.is_available():
+    pytest.skip("needs a CUDA GPU", allow_module_level=True)
+
+import paper_2107_06381_gb300 as Q  # noqa: E402
+
+TOL = 1e-10
+
+
+@pytest.fixture(scope="module", autouse=True)
+def _lib():
+    Q.build_library()
+    Q.load_library()
+
+
+def refine_solve(grid, form, alpha, rhs, rhs_kind, n0_only=False, tol=0.0, maxit=0):
+    with Q.Plan(grid.dim, grid.M, grid.L, grid.T, grid.nt, form, alpha, 0.0, Q.FP32_REFINE, rhs_kind,
+                tol, maxit) as plan:
+        inp = torch.as_tensor(np.ascontiguousarray(rhs).ravel(), dtype=torch.float64).cuda()
+        out = torch.zeros(grid.Nx * (1 if n0_only else grid.nt), dtype=torch.float64, device="cuda")
+        plan.solve(inp, out, n0_only)
+        torch.cuda.synchronize()
+        info = plan.info
+        shape = ((1,) if n0_only else (grid.nt,)) + grid.shape
+        return out.cpu().numpy().reshape(shape), info.last_refine_iters, info.last_rel_residual
+
+
+GRIDS = [
+    bi.Grid(2, (4, 4), 1.0, 0.1, 2),
+    bi.Grid(2, (16, 32), 1.0, 0.1, 16),
+    bi.Grid(2, (64, 64), 1.0, 0.1, 64),
+    bi.Grid(3, (8, 4, 16), 1.0, 0.05, 8),
+    bi.Grid(3, (32, 32, 32), 1.0, 0.05, 32),
+]
+
+
+@pytest.mark.parametrize("grid", GRIDS, ids=lambda g: f"d{g.dim}-M{'x'.join(map(str, g.M))}-nt{g.nt}")
+@pytest.mark.parametrize("form", [Q.FORM_PQ, Q.FORM_PM])
+@pytest.mark.parametrize("rhs_kind", [Q.RHS_DELTA, Q.RHS_GENERAL])
+def test_refined_solution_matches_oracle(grid, form, rhs_kind):
+    alpha = 1e-3 if form == Q.FORM_PQ else 1e-3 * grid.tau
+    F = bi.random_general_rhs(grid, seed=31)
+    rhs = F[0] if rhs_kind == Q.RHS_DELTA else F
+    Ffull = O.delta_rhs(grid, form, alpha, F[0]) if rhs_kind == Q.RHS_DELTA else F
+    want = O.solve_spectral(grid, form, alpha, Ffull)
+    got, iters, rel = refine_solve(grid, form, alpha, rhs, rhs_kind)
+    assert O.rel_l2(got, want) <= TOL, (iters, rel)
+    # the double-float residual floors near 1e-12 (FP64 would floor near 1e-14)
+    assert iters >= 1 and rel <= 1e-11
+
+
+def test_refined_n0_only():
+    grid = bi.Grid(2, (32, 32), 1.0, 0.1, 32)
+    F = bi.random_general_rhs(grid, seed=32)
+    full, _, _ = refine_solve(grid, Q.FORM_PQ, 1e-3, F, Q.RHS_GENERAL)
+    y0, _, _ = refine_solve(grid, Q.FORM_PQ, 1e-3, F, Q.RHS_GENERAL, n0_only=True)
+    np.testing.assert_allclose(y0[0], full[0], rtol=0, atol=1e-13 * np.abs(full).max())
+
+
+@pytest.mark.parametrize("alpha", [1e-6, 1e-8, 1e-9])
+def test_refinement_is_never_silently_wrong(alpha):
+    """|omega| up to 1e9: the refinement either converges to the oracle's answer
+    or reports QBVM_ERR_DIVERGED -- it never returns a wrong answer."""
+    grid = bi.Grid(2, (16, 16), 1.0, 0.1, 16)
+    g = bi.random_general_rhs(grid, seed=33)[0]
+    want = O.solve_spectral(grid, Q.FORM_PQ, alpha, O.delta_rhs(grid, Q.FORM_PQ, alpha, g))
+    try:
+        got, iters, rel = refine_solve(grid, Q.FORM_PQ, alpha, g, Q.RHS_DELTA)
+    except Q.QbvmError as e:
+        assert e.code == -4
+        return
+    assert O.rel_l2(got, want) <= TOL, (iters, rel)
+
+
+def test_refinement_cap_reports_divergence():
+    """A one-step cap with an unreachable tolerance ends with QBVM_ERR_DIVERGED
+    (did not reach the tolerance; the iterate is left in y)."""
+    grid = bi.Grid(2, (32, 32), 1.0, 0.1, 64)
+    g = bi.random_general_rhs(grid, seed=34)[0]
+    with pytest.raises(Q.QbvmError) as ei:
+        refine_solve(grid, Q.FORM_PQ, 1e-8, g, Q.RHS_DELTA, tol=1e-300, maxit=1)
+    assert ei.value.code == -4
+
+
+def test_c2_full_size_refined():
+    p = bi.make_c2()
+    grid = p.grid
+    for form in (Q.FORM_PQ, Q.FORM_PM):
+        alpha = O.alpha_apriori(form, p.delta, grid.tau)
+        want = O.solve_spectral(grid, form, alpha, O.rhs_block0(form, alpha, grid.tau, p.g_delta))
+        got, iters, rel = refine_solve(grid, form, alpha, p.g_delta, Q.RHS_DELTA)
+        err = O.rel_l2(got, want)
+        print(f"C2 form {form}: refinement steps {iters}, rel residual {rel:.2e}, rel err vs oracle {err:.2e}")
+        assert err <= TOL
+
+
+def test_c3_full_size_refined_sampled_levels():
+    """3D 127^3 x 128: the FP32 solve with FP64 refinement against the oracle on
+    sampled levels, and against the plain FP64 path on every level."""
+    p = bi.make_c3()
+    grid = p.grid
+    alpha = O.alpha_apriori(Q.FORM_PQ, p.delta, grid.tau)
+    levels = [0, 1, 64, 127]
+    want = O.solve_spectral(grid, Q.FORM_PQ, alpha, O.rhs_block0(Q.FORM_PQ, alpha, grid.tau, p.g_delta),
+                            levels=levels)
+    got, iters, rel = refine_solve(grid, Q.FORM_PQ, alpha, p.g_delta, Q.RHS_DELTA)
+    err = O.rel_l2(got[levels], want)
+    print(f"C3: refinement steps {iters}, rel residual {rel:.2e}, rel err vs oracle (sampled) {err:.2e}")
+    assert err <= TOL

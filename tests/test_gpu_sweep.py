@@ -1,0 +1,146 @@
+"""Batched alpha sweep (one persistent launch in a CUDA graph) against the oracle.
+
+For every instance and alpha the oracle solves the full all-at-once system
+(sine-basis exact solve) and measures the discrepancy ||y^N - g_delta|| and the
+error ||y^0 - z0|| directly on the solution; the sweep computes them from y^0
+in the sine basis.  The picked alpha follows the discrepancy principle
+(largest alpha with discrepancy <= tau_dp * delta), and the y^0 it returns is
+checked against the oracle at that alpha.
+"""
+import numpy as np
+import pytest
+
+import bhcp_inputs as bi
+import oracle as O
+
+pytestmark = pytest.mark.gpu
+torch = pytest.importorskip("torch")
+if not torch.cuda.is_available():
+    pytest.skip("needs a CUDA GPU", allow_module_level=True)
+
+import paper_2107_06381_gb300 as Q  # noqa: E402
+
+TAU_DP = 1.1
+
+
+@pytest.fixture(scope="module", autouse=True)
+def _lib():
+    Q.build_library()
+    Q.load_library()
+
+
+def _problems():
+    """Uneven batch: 1D and 2D, both formulations, several nt."""
+    out = []
+    specs = [((128,), 32, Q.FORM_PQ, 1e-3), ((64,), 64, Q.FORM_PM, 1e-2), ((256,), 16, Q.FORM_PQ, 1e-4),
+             ((16, 32), 16, Q.FORM_PQ, 3e-3), ((32, 32), 64, Q.FORM_PM, 1e-3), ((64, 16), 8, Q.FORM_PQ, 1e-2)]
+    for i, (M, nt, form, rel) in enumerate(specs):
+        grid = bi.Grid(len(M), M, 1.0, 0.1, nt)
+        rng = np.random.default_rng(100 + i)
+        if grid.dim == 1:
+            z0 = bi.sine_field(grid, [(1,), (2,), (5,)], rng.uniform(0.3, 1.0, 3))
+        else:
+            z0 = bi.sine_field(grid, [(1, 1), (2, 1), (1, 3)], rng.uniform(0.3, 1.0, 3))
+        g = bi.forward_discrete(grid, z0)
+        gd, delta = bi.add_noise_gaussian(grid, g, rel, rng)
+        out.append((grid, form, z0, gd, delta))
+    return out
+
+
+def _oracle_sweep(grid, form, z0, gd, delta, alphas):
+    disc, err, ys = [], [], []
+    for a in alphas:
+        y = O.solve_spectral(grid, form, a, O.delta_rhs(grid, form, a, gd))
+        disc.append(bi.discrete_l2(y[-1] - gd, grid))
+        err.append(bi.discrete_l2(y[0] - z0, grid))
+        ys.append(y[0])
+    disc, err = np.array(disc), np.array(err)
+    ok = np.nonzero(disc <= TAU_DP * delta)[0]
+    pick = int(ok[np.argmax(np.asarray(alphas)[ok])]) if len(ok) else int(np.argmin(disc))
+    return disc, err, pick, ys
+
+
+def _run_sweep(problems, precision, n_alpha=8, autotune=False):
+    dev = []
+    insts = []
+    for grid, form, z0, gd, delta in problems:
+        g = torch.as_tensor(gd.ravel(), dtype=torch.float64).cuda()
+        z = torch.as_tensor(z0.ravel(), dtype=torch.float64).cuda()
+        y0 = torch.zeros(grid.Nx, dtype=torch.float64, device="cuda")
+        dev.append((g, z, y0))
+        insts.append(dict(dim=grid.dim, m=grid.M, L=grid.L, T=grid.T, nt=grid.nt, form=form, delta=delta,
+                          g=g, z0=z, y0=y0))
+    sw = Q.Sweep(insts, n_alpha=n_alpha, log10_lo=-1.5, log10_hi=1.5, tau_dp=TAU_DP, precision=precision)
+    if autotune:
+        sw.autotune(repeats=2)
+    sw.run()
+    res = sw.read()
+    y0s = [d[2].cpu().numpy() for d in dev]
+    return sw, res, y0s, dev
+
+
+@pytest.mark.parametrize("precision,tol", [(Q.FP64, 1e-9), (Q.FP32_REFINE, 2e-3)], ids=["fp64", "fp32"])
+def test_sweep_matches_oracle(precision, tol):
+    problems = _problems()
+    sw, (alphas, disc, err, pick), y0s, _ = _run_sweep(problems, precision)
+    try:
+        for i, (grid, form, z0, gd, delta) in enumerate(problems):
+            rule = O.alpha_apriori(form, delta, grid.tau)
+            want_alphas = rule * 10.0 ** np.linspace(-1.5, 1.5, 8)
+            np.testing.assert_allclose(alphas[i], want_alphas, rtol=1e-14)
+            odisc, oerr, opick, oys = _oracle_sweep(grid, form, z0, gd, delta, want_alphas)
+            np.testing.assert_allclose(disc[i], odisc, rtol=tol)
+            np.testing.assert_allclose(err[i], oerr, rtol=tol)
+            near = np.abs(odisc / (TAU_DP * delta) - 1.0) < 10 * tol
+            if not near.any():
+                assert pick[i, 0] == opick, (i, pick[i], opick, odisc, TAU_DP * delta)
+            assert pick[i, 1] == int(np.argmin(oerr)) or abs(oerr[pick[i, 1]] / oerr.min() - 1) < 10 * tol
+            # y^0 at the picked alpha is produced in FP64 in both precisions
+            a = int(pick[i, 0])
+            assert O.rel_l2(y0s[i], oys[a].ravel()) <= 1e-10
+    finally:
+        sw.close()
+
+
+def test_sweep_graph_replay_and_autotune_are_consistent():
+    problems = _problems()
+    sw, (alphas, disc, err, pick), y0s, dev = _run_sweep(problems, Q.FP32_REFINE)
+    try:
+        for _ in range(3):                       # graph replays
+            sw.run()
+        a2, d2, e2, p2 = sw.read()
+        np.testing.assert_array_equal(p2, pick)
+        np.testing.assert_allclose(d2, disc, rtol=1e-12)
+        cfg = sw.autotune(repeats=2)
+        assert cfg.modes_per_thread in (1, 2, 4) and cfg.grid > 0 and cfg.ms > 0
+        sw.run()
+        a3, d3, e3, p3 = sw.read()
+        np.testing.assert_array_equal(p3, pick)
+        np.testing.assert_allclose(d3, disc, rtol=1e-5)
+        y0_again = [d[2].cpu().numpy() for d in dev]
+        for u, v in zip(y0_again, y0s):
+            np.testing.assert_allclose(u, v, rtol=0, atol=1e-13 * np.abs(v).max())
+    finally:
+        sw.close()
+
+
+def test_c4_style_batch_sampled():
+    """A slice of the uneven 512-instance batch: sizes from the batch recipe,
+    16 alphas; every instance's discrepancies checked against the oracle."""
+    specs = [s for s in bi.batch_specs_c4() if np.prod(s["M"]) * s["nt"] <= 256 * 256 * 64][:12]
+    problems = []
+    for s in specs:
+        grid = bi.Grid(s["dim"], tuple(s["M"]), 1.0, 0.1, s["nt"])
+        rng = np.random.default_rng(s["seed"])
+        modes = [(1,), (2,), (3,)] if grid.dim == 1 else [(1, 1), (2, 1), (1, 2)]
+        z0 = bi.sine_field(grid, modes, rng.uniform(0.3, 1.0, 3))
+        gd, delta = bi.add_noise_gaussian(grid, bi.forward_discrete(grid, z0), s["rel_noise"], rng)
+        problems.append((grid, Q.FORM_PQ, z0, gd, delta))
+    sw, (alphas, disc, err, pick), y0s, _ = _run_sweep(problems, Q.FP32_REFINE, n_alpha=16)
+    try:
+        for i, (grid, form, z0, gd, delta) in enumerate(problems):
+            odisc, oerr, opick, oys = _oracle_sweep(grid, form, z0, gd, delta, alphas[i])
+            np.testing.assert_allclose(disc[i], odisc, rtol=2e-3)
+            assert O.rel_l2(y0s[i], oys[int(pick[i, 0])].ravel()) <= 1e-10
+    finally:
+        sw.close()
