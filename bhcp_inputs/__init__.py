@@ -35,7 +35,7 @@ __all__ = [
     "Grid", "Problem", "discrete_l2", "interior_coords", "sine_field",
     "forward_discrete", "add_noise_multiplicative", "add_noise_gaussian",
     "make_c1", "make_c2", "make_c3", "make_paper_ex1", "make_paper_ex2",
-    "make_problem", "random_general_rhs", "batch_specs_c4",
+    "make_problem", "random_general_rhs", "batch_specs_c4", "alpha_training_batch",
 ]
 
 
@@ -315,3 +315,40 @@ def batch_specs_c4(seed: int = 4, count: int = 512):
             M = (int(rng.choice([64, 128, 256])), int(rng.choice([64, 128, 256])))
         out.append({"dim": len(M), "M": M, "nt": nt, "rel_noise": rel, "seed": seed * 100003 + i})
     return out
+
+
+def alpha_training_batch(count: int, seed: int, M: int = 128, nt: int = 128, T: float = 0.1,
+                         rel_range=(1e-4, 1e-2), modes: int = 16, kmax: int = 8):
+    """A batch of 2D instances on the unit square for the learned-alpha data:
+    z0 = `modes` random decaying sine modes (as for the 2D workload), g the
+    exact discrete forward solution at T, additive Gaussian noise with relative
+    level log-uniform in rel_range.
+
+    Returns (grid, z0, g_delta, delta) with z0 and g_delta of shape
+    (count, M-1, M-1) (x fastest) and delta (count,), the grid-weighted noise
+    norms.  Built mode by mode: with S_k the sine vectors of the grid,
+    z0_b = Sy^T C_b Sx and g_b = Sy^T (C_b * r^N) Sx, r = 1/(1 + tau lambda).
+    """
+    grid = Grid(2, (M, M), 1.0, T, nt)
+    rng = np.random.default_rng(seed)
+    n = M - 1
+    x = np.arange(1, M) / M
+    ks = np.arange(1, kmax + 1)
+    S = np.sin(np.pi * np.outer(ks, x))                       # (kmax, n)
+    lam1 = (4.0 * M * M) * np.sin(ks * np.pi / (2 * M)) ** 2
+    lam = lam1[:, None] + lam1[None, :]                       # (ky, kx)
+    decay = (1.0 + grid.tau * lam) ** (-(nt - 1.0))
+    C = np.zeros((count, kmax, kmax))
+    for b in range(count):
+        md, amps = _decaying_sine_modes(rng, 2, modes, kmax)
+        for (kx, ky), a in zip(md, amps):
+            C[b, ky - 1, kx - 1] += a
+    z0 = np.einsum("yn,byx,xm->bnm", S, C, S, optimize=True)
+    g = np.einsum("yn,byx,xm->bnm", S, C * decay, S, optimize=True)
+    rel = 10.0 ** rng.uniform(np.log10(rel_range[0]), np.log10(rel_range[1]), size=count)
+    eta = rng.standard_normal(g.shape)
+    gn = np.sqrt((g * g).sum(axis=(1, 2)))
+    en = np.sqrt((eta * eta).sum(axis=(1, 2)))
+    eta *= (rel * gn / en)[:, None, None]
+    delta = (1.0 / M) * np.sqrt((eta * eta).sum(axis=(1, 2)))
+    return grid, z0, g + eta, delta

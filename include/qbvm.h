@@ -194,8 +194,9 @@ int qbvm_residual_noalloc(const qbvm_desc* desc, const double* y, const double* 
  * Batched regularisation-parameter sweep.  Many PinT-QBVM / PinT-MQBVM
  * instances of uneven size (1D or 2D, delta right-hand side f^0 = -omega g/tau),
  * each solved for n_alpha values of alpha log-spaced around the a-priori rule
- * of Section 5 (alpha_rule = delta for PQ, tau*delta for PM):
- *     alpha_i = alpha_rule * 10^(log10_lo + (log10_hi - log10_lo) i/(n_alpha-1)).
+ * of Section 5 (alpha_rule = delta for PQ, tau*delta for PM) or around a
+ * caller-given alpha_base:
+ *     alpha_i = base * 10^(log10_lo + (log10_hi - log10_lo) i/(n_alpha-1)).
  * For every (instance, alpha) the sweep forms y^0 in the sine basis by the
  * three steps of eq. 3.8 (Step (c) evaluated at t = 0), the discrepancy
  * ||y^N - g||, which the first block row of eq. 3.3/3.6 gives as
@@ -220,6 +221,7 @@ typedef struct qbvm_sweep_instance {
     int    nt;
     int    form;
     double delta;          /* noise level of g (bound of the discrepancy principle) */
+    double alpha_base;     /* > 0: replaces the a-priori alpha_rule as the centre of the scan */
     const double* g;       /* device: g_delta, one level */
     const double* z0;      /* device, optional: true z(., 0) for the error report */
     double* y0;            /* device, optional: receives y^0 at the picked alpha */
@@ -261,6 +263,47 @@ int qbvm_sweep_autotune(qbvm_sweep_t* sweep, int repeats, qbvm_sweep_config* bes
 int qbvm_sweep_set_config(qbvm_sweep_t* sweep, const qbvm_sweep_config* cfg);
 int qbvm_sweep_get_config(const qbvm_sweep_t* sweep, qbvm_sweep_config* cfg);
 int qbvm_sweep_destroy(qbvm_sweep_t* sweep);
+
+/* ------------------------------------------------------------------------
+ * Learned regularisation parameter.  The paper picks alpha a priori
+ * (Section 5); this network predicts t = log10(alpha / alpha_rule) from
+ * spectrum features of g_delta and is trained on solves of the method itself
+ * (labels: the alpha with the smallest reconstruction error in a sweep).
+ *
+ * Features (qbvm_features_*): for a 2D instance on (0,L)^2 with m intervals
+ * per axis, 67 FP32 values: 64 bins of the radial sine spectrum of g_delta
+ * (bin b = floor(64 |k| / (sqrt(2) m)) over modes k = (k_x, k_y), value
+ * log10 of the mean squared sine-series coefficient in the bin), then
+ * log10 delta, T and log2 nt.  g is a device array [B][m-1][m-1] (FP64),
+ * delta a host array of B values, feats a device array [B][67].
+ *
+ * Network (qbvm_mlp_*): x -> relu(W1 x' + b1) -> relu(W2 h1 + b2) -> w3.h2 + b3,
+ * x' = (x - mean)/sd (qbvm_mlp_set_norm), bfloat16 weights in the products,
+ * FP32 accumulation and FP32 master weights; loss (1/2B) sum (y - t)^2;
+ * Adam (beta 0.9/0.999, eps 1e-8).  Flat parameter order: W1 [width][in],
+ * b1 [width], W2 [width][width], b2 [width], w3 [width], b3 [1].
+ * x, t, y are device FP32 arrays; grads (qbvm_mlp_gradients) a host array of
+ * qbvm_mlp_num_params values, loss_out a host double. */
+typedef struct qbvm_mlp qbvm_mlp_t;
+typedef struct qbvm_features qbvm_features_t;
+
+int qbvm_mlp_create(int in_dim, int width, int max_batch, unsigned long long seed, qbvm_mlp_t** out);
+long long qbvm_mlp_num_params(const qbvm_mlp_t* mlp);
+int qbvm_mlp_set_norm(qbvm_mlp_t* mlp, const float* mean, const float* sd);
+int qbvm_mlp_get_params(const qbvm_mlp_t* mlp, float* params, float* adam_m, float* adam_v, long long* step);
+int qbvm_mlp_set_params(qbvm_mlp_t* mlp, const float* params, const float* adam_m, const float* adam_v,
+                        long long step);
+int qbvm_mlp_forward(qbvm_mlp_t* mlp, const float* x, int batch, float* y, void* stream);
+int qbvm_mlp_gradients(qbvm_mlp_t* mlp, const float* x, const float* t, int batch, float* grads,
+                       double* loss_out, void* stream);
+int qbvm_mlp_train_step(qbvm_mlp_t* mlp, const float* x, const float* t, int batch, float lr, void* stream);
+int qbvm_mlp_last_loss(qbvm_mlp_t* mlp, double* loss, void* stream);
+int qbvm_mlp_destroy(qbvm_mlp_t* mlp);
+
+int qbvm_features_plan(int m, double T, int nt, int max_batch, qbvm_features_t** out);
+int qbvm_features_run(qbvm_features_t* feats_plan, const double* g, const double* delta_host, int batch,
+                      float* feats, void* stream);
+int qbvm_features_destroy(qbvm_features_t* feats_plan);
 
 /* qbvm_destroy -- free the plan and everything it owns (NULL is accepted). */
 int qbvm_destroy(qbvm_plan_t* plan);

@@ -19,7 +19,7 @@ __all__ = [
     "qbvm_profile_enable", "qbvm_profile_read", "qbvm_residual_noalloc",
     "qbvm_strerror", "qbvm_version", "Plan", "Sweep", "QbvmSweepInstance", "QbvmSweepDesc", "QbvmSweepConfig",
     "qbvm_sweep_plan", "qbvm_sweep_run", "qbvm_sweep_read", "qbvm_sweep_autotune", "qbvm_sweep_set_config",
-    "qbvm_sweep_get_config", "qbvm_sweep_destroy",
+    "qbvm_sweep_get_config", "qbvm_sweep_destroy", "MLP", "Features",
     "FORM_PQ", "FORM_PM", "FP64", "FP32_REFINE", "RHS_DELTA", "RHS_GENERAL",
 ]
 
@@ -55,6 +55,7 @@ class QbvmSweepInstance(ctypes.Structure):
     _fields_ = [
         ("dim", ctypes.c_int), ("m", ctypes.c_int * 3), ("L", ctypes.c_double), ("T", ctypes.c_double),
         ("nt", ctypes.c_int), ("form", ctypes.c_int), ("delta", ctypes.c_double),
+        ("alpha_base", ctypes.c_double),
         ("g", ctypes.c_void_p), ("z0", ctypes.c_void_p), ("y0", ctypes.c_void_p),
     ]
 
@@ -123,6 +124,33 @@ def load_library(path: str | None = None) -> ctypes.CDLL:
     lib.qbvm_sweep_get_config.restype = ip
     lib.qbvm_sweep_destroy.argtypes = [vp]
     lib.qbvm_sweep_destroy.restype = ip
+    vp_, ll = ctypes.c_void_p, ctypes.c_longlong
+    lib.qbvm_mlp_create.argtypes = [ip, ip, ip, ctypes.c_ulonglong, ctypes.POINTER(vp)]
+    lib.qbvm_mlp_create.restype = ip
+    lib.qbvm_mlp_num_params.argtypes = [vp]
+    lib.qbvm_mlp_num_params.restype = ll
+    lib.qbvm_mlp_set_norm.argtypes = [vp, vp_, vp_]
+    lib.qbvm_mlp_set_norm.restype = ip
+    lib.qbvm_mlp_get_params.argtypes = [vp, vp_, vp_, vp_, ctypes.POINTER(ll)]
+    lib.qbvm_mlp_get_params.restype = ip
+    lib.qbvm_mlp_set_params.argtypes = [vp, vp_, vp_, vp_, ll]
+    lib.qbvm_mlp_set_params.restype = ip
+    lib.qbvm_mlp_forward.argtypes = [vp, vp_, ip, vp_, vp]
+    lib.qbvm_mlp_forward.restype = ip
+    lib.qbvm_mlp_gradients.argtypes = [vp, vp_, vp_, ip, vp_, ctypes.POINTER(dp), vp]
+    lib.qbvm_mlp_gradients.restype = ip
+    lib.qbvm_mlp_train_step.argtypes = [vp, vp_, vp_, ip, ctypes.c_float, vp]
+    lib.qbvm_mlp_train_step.restype = ip
+    lib.qbvm_mlp_last_loss.argtypes = [vp, ctypes.POINTER(dp), vp]
+    lib.qbvm_mlp_last_loss.restype = ip
+    lib.qbvm_mlp_destroy.argtypes = [vp]
+    lib.qbvm_mlp_destroy.restype = ip
+    lib.qbvm_features_plan.argtypes = [ip, dp, ip, ip, ctypes.POINTER(vp)]
+    lib.qbvm_features_plan.restype = ip
+    lib.qbvm_features_run.argtypes = [vp, vp_, vp_, ip, vp_, vp]
+    lib.qbvm_features_run.restype = ip
+    lib.qbvm_features_destroy.argtypes = [vp]
+    lib.qbvm_features_destroy.restype = ip
     lib.qbvm_version.argtypes = []
     lib.qbvm_version.restype = ip
     if path is None:
@@ -288,6 +316,7 @@ class Sweep:
             m = list(d["m"]) + [1] * (3 - len(d["m"]))
             arr[i] = QbvmSweepInstance(d["dim"], (ctypes.c_int * 3)(*m), float(d.get("L", 1.0)), float(d["T"]),
                                        int(d["nt"]), int(d.get("form", FORM_PQ)), float(d["delta"]),
+                                       float(d.get("alpha_base", 0.0)),
                                        _ptr(d["g"]), _ptr(d.get("z0")), _ptr(d.get("y0")))
         self._arr = arr
         self.count = len(instances)
@@ -327,6 +356,137 @@ class Sweep:
 
     def __exit__(self, *exc):
         self.close()
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+
+def _fptr(a) -> int:
+    """Address of a float32 tensor / ndarray."""
+    if a is None:
+        return 0
+    if isinstance(a, int):
+        return a
+    mod = type(a).__module__
+    if mod.startswith("torch"):
+        import torch
+        if a.dtype != torch.float32 or not a.is_contiguous():
+            raise TypeError("tensors must be contiguous float32")
+        return a.data_ptr()
+    import numpy as np
+    if a.dtype != np.float32 or not a.flags["C_CONTIGUOUS"]:
+        raise TypeError("arrays must be C-contiguous float32")
+    return a.ctypes.data
+
+
+class MLP:
+    """The learned-alpha network on the GPU (see include/qbvm.h)."""
+
+    def __init__(self, in_dim=67, width=128, max_batch=4096, seed=0):
+        lib = load_library()
+        h = ctypes.c_void_p()
+        _check(lib.qbvm_mlp_create(in_dim, width, max_batch, seed, ctypes.byref(h)), "qbvm_mlp_create")
+        self.handle = h.value
+        self.in_dim, self.width = in_dim, width
+        self.nparam = lib.qbvm_mlp_num_params(self.handle)
+
+    def set_norm(self, mean, sd):
+        import numpy as np
+        m = np.ascontiguousarray(mean, dtype=np.float32)
+        s = np.ascontiguousarray(sd, dtype=np.float32)
+        _check(load_library().qbvm_mlp_set_norm(self.handle, m.ctypes.data, s.ctypes.data), "qbvm_mlp_set_norm")
+        self._norm = (m, s)
+
+    def get_params(self):
+        import numpy as np
+        p = np.zeros(self.nparam, dtype=np.float32)
+        m = np.zeros_like(p)
+        v = np.zeros_like(p)
+        step = ctypes.c_longlong()
+        _check(load_library().qbvm_mlp_get_params(self.handle, p.ctypes.data, m.ctypes.data, v.ctypes.data,
+                                                  ctypes.byref(step)), "qbvm_mlp_get_params")
+        return p, m, v, step.value
+
+    def set_params(self, p, m=None, v=None, step=0):
+        import numpy as np
+        p = np.ascontiguousarray(p, dtype=np.float32)
+        mm = None if m is None else np.ascontiguousarray(m, dtype=np.float32)
+        vv = None if v is None else np.ascontiguousarray(v, dtype=np.float32)
+        _check(load_library().qbvm_mlp_set_params(self.handle, p.ctypes.data, 0 if mm is None else mm.ctypes.data,
+                                                  0 if vv is None else vv.ctypes.data, int(step)),
+               "qbvm_mlp_set_params")
+
+    def forward(self, x, y, stream=None):
+        _check(load_library().qbvm_mlp_forward(self.handle, _fptr(x), int(x.shape[0]), _fptr(y), _stream(stream, x)),
+               "qbvm_mlp_forward")
+        return y
+
+    def gradients(self, x, t):
+        import numpy as np
+        g = np.zeros(self.nparam, dtype=np.float32)
+        loss = ctypes.c_double()
+        _check(load_library().qbvm_mlp_gradients(self.handle, _fptr(x), _fptr(t), int(x.shape[0]), g.ctypes.data,
+                                                 ctypes.byref(loss), _stream(None, x)), "qbvm_mlp_gradients")
+        return loss.value, g
+
+    def train_step(self, x, t, lr, stream=None):
+        _check(load_library().qbvm_mlp_train_step(self.handle, _fptr(x), _fptr(t), int(x.shape[0]), float(lr),
+                                                  _stream(stream, x)), "qbvm_mlp_train_step")
+
+    def last_loss(self, stream=None):
+        out = ctypes.c_double()
+        _check(load_library().qbvm_mlp_last_loss(self.handle, ctypes.byref(out), _stream(stream)),
+               "qbvm_mlp_last_loss")
+        return out.value
+
+    def unpack(self, flat):
+        """Split a flat parameter vector into the oracle's dict (float64)."""
+        import numpy as np
+        K, N = self.in_dim, self.width
+        f = np.asarray(flat, dtype=np.float64)
+        o = 0
+        out = {}
+        for name, shape in (("W1", (N, K)), ("b1", (N,)), ("W2", (N, N)), ("b2", (N,)), ("w3", (N,)), ("b3", ())):
+            size = int(np.prod(shape)) if shape else 1
+            out[name] = f[o:o + size].reshape(shape) if shape else np.array(f[o])
+            o += size
+        return out
+
+    def close(self):
+        if self.handle:
+            load_library().qbvm_mlp_destroy(self.handle)
+            self.handle = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+
+class Features:
+    """Spectrum features of g_delta for a batch of 2D instances of one grid."""
+
+    def __init__(self, m, T, nt, max_batch):
+        h = ctypes.c_void_p()
+        _check(load_library().qbvm_features_plan(int(m), float(T), int(nt), int(max_batch), ctypes.byref(h)),
+               "qbvm_features_plan")
+        self.handle = h.value
+
+    def run(self, g, delta, feats, stream=None):
+        import numpy as np
+        d = np.ascontiguousarray(delta, dtype=np.float64)
+        _check(load_library().qbvm_features_run(self.handle, _ptr(g), d.ctypes.data, int(d.size), _fptr(feats),
+                                                _stream(stream, g)), "qbvm_features_run")
+        return feats
+
+    def close(self):
+        if self.handle:
+            load_library().qbvm_features_destroy(self.handle)
+            self.handle = None
 
     def __del__(self):
         try:

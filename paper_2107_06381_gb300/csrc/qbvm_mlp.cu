@@ -1,0 +1,474 @@
+// qbvm_mlp.cu -- learned regularisation parameter: spectrum features of g_delta
+// and a small MLP (forward, backward, Adam) trained on solves of the method.
+//
+// The paper chooses alpha a priori (Section 5: alpha = delta for PinT-QBVM,
+// tau*delta for PinT-MQBVM).  Here a network predicts t = log10(alpha /
+// alpha_rule) from
+//   * 64 bins of the radial DST spectrum of g_delta: for the sine modes
+//     (k_x, k_y) of the 2D grid, bin b holds log10 of the mean of c_l^2, c_l the
+//     coefficient of mode l in g = sum_l c_l sin(k_x pi x) sin(k_y pi y) and
+//     b = floor(64 |k| / (sqrt(2) (n + 1)));
+//   * log10 delta, T and log2 N_t,
+// standardised with per-feature mean and deviation before the first layer.
+// Network: h1 = relu(W1 x + b1), h2 = relu(W2 h1 + b2), y = w3.h2 + b3 with
+// bfloat16 weights in the products and FP32 accumulation (FP32 master weights
+// for Adam); loss = (1/2B) sum (y - t)^2.
+#include <cuda_bf16.h>
+
+#include <cmath>
+#include <cstring>
+#include <new>
+#include <vector>
+
+#include "qbvm.h"
+#include "qbvm_internal.h"
+
+namespace {
+
+constexpr int MLP_THREADS = 256;
+
+// ------------------------------------------------------------------ features
+__global__ void k_spectrum_bins(const float* __restrict__ ghat, long long Nx, const unsigned char* __restrict__ bin,
+                                const float* __restrict__ inv_count, float coef_scale2, const double* __restrict__ delta,
+                                float T, float lg_nt, int in_dim, float* __restrict__ feats) {
+    __shared__ float acc[64];
+    const int b = blockIdx.x;
+    for (int i = threadIdx.x; i < 64; i += blockDim.x) acc[i] = 0.f;
+    __syncthreads();
+    const float* g = ghat + (long long)b * Nx;
+    for (long long l = threadIdx.x; l < Nx; l += blockDim.x) {
+        float c = g[l];
+        atomicAdd(&acc[bin[l]], c * c * coef_scale2);
+    }
+    __syncthreads();
+    float* f = feats + (long long)b * in_dim;
+    for (int i = threadIdx.x; i < 64; i += blockDim.x) f[i] = log10f(acc[i] * inv_count[i] + 1e-30f);
+    if (threadIdx.x == 0) {
+        f[64] = (float)log10(delta[b]);
+        f[65] = T;
+        f[66] = lg_nt;
+    }
+}
+
+// ------------------------------------------------------------------ MLP
+__device__ __forceinline__ float bf(const __nv_bfloat16* w, long long i) { return __bfloat162float(w[i]); }
+
+// Z = A W^T + b (A: B x K, W: N x K bf16), H = relu(Z); optional input standardisation.
+__global__ void k_dense_relu(const float* __restrict__ A, const __nv_bfloat16* __restrict__ W, const float* __restrict__ bias,
+                             int B, int K, int N, const float* __restrict__ mu, const float* __restrict__ inv_sd,
+                             float* __restrict__ Z, float* __restrict__ H) {
+    long long idx = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+    if (idx >= (long long)B * N) return;
+    int b = (int)(idx / N), n = (int)(idx - (long long)b * N);
+    const float* a = A + (long long)b * K;
+    const __nv_bfloat16* w = W + (long long)n * K;
+    float s = bias[n];
+    if (mu) {
+        for (int k = 0; k < K; ++k) s = fmaf((a[k] - mu[k]) * inv_sd[k], bf(w, k), s);
+    } else {
+        for (int k = 0; k < K; ++k) s = fmaf(a[k], bf(w, k), s);
+    }
+    Z[idx] = s;
+    H[idx] = fmaxf(s, 0.f);
+}
+
+// y = H w3 + b3 (one warp per row).
+__global__ void k_dense_out(const float* __restrict__ H, const __nv_bfloat16* __restrict__ w3, const float* __restrict__ b3,
+                            int B, int N, float* __restrict__ y) {
+    int warp = (int)(((long long)blockIdx.x * blockDim.x + threadIdx.x) >> 5), lane = threadIdx.x & 31;
+    if (warp >= B) return;
+    const float* h = H + (long long)warp * N;
+    float s = 0.f;
+    for (int n = lane; n < N; n += 32) s = fmaf(h[n], bf(w3, n), s);
+    for (int o = 16; o > 0; o >>= 1) s += __shfl_down_sync(0xffffffffu, s, o);
+    if (lane == 0) y[warp] = s + b3[0];
+}
+
+// dy = (y - t)/B and the loss sum (1/2B) sum (y - t)^2.
+__global__ void k_mse(const float* __restrict__ y, const float* __restrict__ t, int B, float* __restrict__ dy,
+                      double* __restrict__ loss) {
+    int b = blockIdx.x * blockDim.x + threadIdx.x;
+    float r = 0.f;
+    if (b < B) {
+        r = y[b] - t[b];
+        dy[b] = r / (float)B;
+    }
+    float s = 0.5f * r * r / (float)B;
+    for (int o = 16; o > 0; o >>= 1) s += __shfl_down_sync(0xffffffffu, s, o);
+    if ((threadIdx.x & 31) == 0) atomicAdd(loss, (double)s);
+}
+
+// dZ2 = dy w3^T masked by Z2 > 0.
+__global__ void k_back_out(const float* __restrict__ dy, const __nv_bfloat16* __restrict__ w3, const float* __restrict__ Z2,
+                           int B, int N, float* __restrict__ dZ2) {
+    long long idx = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+    if (idx >= (long long)B * N) return;
+    int b = (int)(idx / N), n = (int)(idx - (long long)b * N);
+    dZ2[idx] = Z2[idx] > 0.f ? dy[b] * bf(w3, n) : 0.f;
+}
+
+// dZ1 = (dZ2 W2) masked by Z1 > 0 (W2: N x K).
+__global__ void k_back_hidden(const float* __restrict__ dZ2, const __nv_bfloat16* __restrict__ W2, const float* __restrict__ Z1,
+                              int B, int N, int K, float* __restrict__ dZ1) {
+    long long idx = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+    if (idx >= (long long)B * K) return;
+    int b = (int)(idx / K), k = (int)(idx - (long long)b * K);
+    if (!(Z1[idx] > 0.f)) {
+        dZ1[idx] = 0.f;
+        return;
+    }
+    const float* d = dZ2 + (long long)b * N;
+    float s = 0.f;
+    for (int n = 0; n < N; ++n) s = fmaf(d[n], bf(W2, (long long)n * K + k), s);
+    dZ1[idx] = s;
+}
+
+// dW[n][k] = sum_b D[b][n] A'[b][k] (A' standardised input when mu != null), db[n] = sum_b D[b][n].
+__global__ void k_wgrad(const float* __restrict__ D, const float* __restrict__ A, int B, int N, int K,
+                        const float* __restrict__ mu, const float* __restrict__ inv_sd, float* __restrict__ dW,
+                        float* __restrict__ db) {
+    long long idx = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+    long long total = (long long)N * (K + 1);
+    if (idx >= total) return;
+    int n = (int)(idx / (K + 1)), k = (int)(idx - (long long)n * (K + 1));
+    float s = 0.f;
+    if (k == K) {
+        for (int b = 0; b < B; ++b) s += D[(long long)b * N + n];
+        db[n] = s;
+    } else {
+        const float m = mu ? mu[k] : 0.f, is = mu ? inv_sd[k] : 1.f;
+        for (int b = 0; b < B; ++b) s = fmaf(D[(long long)b * N + n], (A[(long long)b * K + k] - m) * is, s);
+        dW[(long long)n * K + k] = s;
+    }
+}
+
+// Adam (Kingma & Ba): FP32 master weights, bfloat16 copy for the products.
+__global__ void k_adam(float* __restrict__ p, const float* __restrict__ g, float* __restrict__ m, float* __restrict__ v,
+                       __nv_bfloat16* __restrict__ pb, long long n, float lr, float b1, float b2, float c1, float c2,
+                       float eps) {
+    long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= n) return;
+    float gi = g[i];
+    float mi = b1 * m[i] + (1.f - b1) * gi;
+    float vi = b2 * v[i] + (1.f - b2) * gi * gi;
+    m[i] = mi;
+    v[i] = vi;
+    float pi = p[i] - lr * (mi / c1) / (sqrtf(vi / c2) + eps);
+    p[i] = pi;
+    pb[i] = __float2bfloat16_rn(pi);
+}
+
+__global__ void k_to_bf16(const float* __restrict__ p, __nv_bfloat16* __restrict__ pb, long long n) {
+    long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i < n) pb[i] = __float2bfloat16_rn(p[i]);
+}
+
+unsigned nblk(long long n) { return (unsigned)((n + MLP_THREADS - 1) / MLP_THREADS); }
+
+}  // namespace
+
+struct qbvm_mlp {
+    int in_dim = 0, width = 0, bmax = 0;
+    long long nparam = 0;
+    long long oW1 = 0, ob1 = 0, oW2 = 0, ob2 = 0, ow3 = 0, ob3 = 0;
+    float* p = nullptr;       // FP32 master
+    float* g = nullptr;       // gradients
+    float* m = nullptr;
+    float* v = nullptr;
+    __nv_bfloat16* pb = nullptr;
+    float* mu = nullptr;
+    float* inv_sd = nullptr;
+    bool has_norm = false;
+    float *Z1 = nullptr, *H1 = nullptr, *Z2 = nullptr, *H2 = nullptr, *y = nullptr, *dy = nullptr, *dZ1 = nullptr,
+          *dZ2 = nullptr;
+    double* loss = nullptr;
+    long long step = 0;
+    std::vector<void*> allocs;
+};
+
+struct qbvm_features {
+    int n = 0, M = 0, lm = 0, bmax = 0;
+    double T = 0;
+    int nt = 0;
+    long long Nx = 0;
+    float* work = nullptr;
+    unsigned char* bin = nullptr;
+    float* inv_count = nullptr;
+    double* delta = nullptr;
+    float2* tw = nullptr;
+    float* sn = nullptr;
+    std::vector<void*> allocs;
+};
+
+namespace {
+
+template <typename T, typename H>
+int m_alloc(H* h, T** ptr, size_t count) {
+    *ptr = nullptr;
+    if (!count) return QBVM_OK;
+    void* q = nullptr;
+    if (cudaMalloc(&q, count * sizeof(T)) != cudaSuccess) {
+        cudaGetLastError();
+        return QBVM_ERR_OOM;
+    }
+    h->allocs.push_back(q);
+    *ptr = static_cast<T*>(q);
+    return QBVM_OK;
+}
+
+// splitmix64 (Steele, Lea & Flood 2014): deterministic initial weights
+unsigned long long splitmix(unsigned long long& s) {
+    unsigned long long z = (s += 0x9E3779B97F4A7C15ull);
+    z = (z ^ (z >> 30)) * 0xBF58476D1CE4E5B9ull;
+    z = (z ^ (z >> 27)) * 0x94D049BB133111EBull;
+    return z ^ (z >> 31);
+}
+
+int mlp_grads(qbvm_mlp_t* h, const float* x, const float* t, int B, cudaStream_t s) {
+    const int K = h->in_dim, N = h->width;
+    const float* mu = h->has_norm ? h->mu : nullptr;
+    const float* is = h->has_norm ? h->inv_sd : nullptr;
+    if (cudaMemsetAsync(h->loss, 0, sizeof(double), s) != cudaSuccess) return QBVM_ERR_CUDA;
+    k_dense_relu<<<nblk((long long)B * N), MLP_THREADS, 0, s>>>(x, h->pb + h->oW1, h->p + h->ob1, B, K, N, mu, is, h->Z1, h->H1);
+    k_dense_relu<<<nblk((long long)B * N), MLP_THREADS, 0, s>>>(h->H1, h->pb + h->oW2, h->p + h->ob2, B, N, N, nullptr,
+                                                                 nullptr, h->Z2, h->H2);
+    k_dense_out<<<nblk((long long)B * 32), MLP_THREADS, 0, s>>>(h->H2, h->pb + h->ow3, h->p + h->ob3, B, N, h->y);
+    k_mse<<<nblk(B), MLP_THREADS, 0, s>>>(h->y, t, B, h->dy, h->loss);
+    // w3, b3: dW = dy^T H2 (one output row)
+    k_wgrad<<<nblk((long long)(N + 1)), MLP_THREADS, 0, s>>>(h->dy, h->H2, B, 1, N, nullptr, nullptr, h->g + h->ow3,
+                                                            h->g + h->ob3);
+    k_back_out<<<nblk((long long)B * N), MLP_THREADS, 0, s>>>(h->dy, h->pb + h->ow3, h->Z2, B, N, h->dZ2);
+    k_wgrad<<<nblk((long long)N * (N + 1)), MLP_THREADS, 0, s>>>(h->dZ2, h->H1, B, N, N, nullptr, nullptr,
+                                                                h->g + h->oW2, h->g + h->ob2);
+    k_back_hidden<<<nblk((long long)B * N), MLP_THREADS, 0, s>>>(h->dZ2, h->pb + h->oW2, h->Z1, B, N, N, h->dZ1);
+    k_wgrad<<<nblk((long long)N * (K + 1)), MLP_THREADS, 0, s>>>(h->dZ1, x, B, N, K, mu, is, h->g + h->oW1,
+                                                                h->g + h->ob1);
+    return cudaGetLastError() == cudaSuccess ? QBVM_OK : QBVM_ERR_CUDA;
+}
+
+}  // namespace
+
+extern "C" {
+
+int qbvm_mlp_create(int in_dim, int width, int max_batch, unsigned long long seed, qbvm_mlp_t** out) {
+    if (!out || in_dim < 1 || in_dim > 4096 || width < 1 || width > 4096 || max_batch < 1) return QBVM_ERR_BAD_ARG;
+    *out = nullptr;
+    qbvm_mlp_t* h = new (std::nothrow) qbvm_mlp();
+    if (!h) return QBVM_ERR_OOM;
+    h->in_dim = in_dim;
+    h->width = width;
+    h->bmax = max_batch;
+    const long long K = in_dim, N = width;
+    h->oW1 = 0;
+    h->ob1 = N * K;
+    h->oW2 = h->ob1 + N;
+    h->ob2 = h->oW2 + N * N;
+    h->ow3 = h->ob2 + N;
+    h->ob3 = h->ow3 + N;
+    h->nparam = h->ob3 + 1;
+    // He-uniform weights, zero biases (deterministic from `seed`)
+    std::vector<float> init((size_t)h->nparam, 0.f);
+    unsigned long long st = seed;
+    auto uni = [&](double a) { return (float)((2.0 * ((splitmix(st) >> 11) * (1.0 / 9007199254740992.0)) - 1.0) * a); };
+    for (long long i = 0; i < N * K; ++i) init[h->oW1 + i] = uni(std::sqrt(6.0 / K));
+    for (long long i = 0; i < N * N; ++i) init[h->oW2 + i] = uni(std::sqrt(6.0 / N));
+    for (long long i = 0; i < N; ++i) init[h->ow3 + i] = uni(std::sqrt(3.0 / N));
+    int rc = m_alloc(h, &h->p, h->nparam);
+    if (!rc) rc = m_alloc(h, &h->g, h->nparam);
+    if (!rc) rc = m_alloc(h, &h->m, h->nparam);
+    if (!rc) rc = m_alloc(h, &h->v, h->nparam);
+    if (!rc) rc = m_alloc(h, &h->pb, h->nparam);
+    if (!rc) rc = m_alloc(h, &h->mu, K);
+    if (!rc) rc = m_alloc(h, &h->inv_sd, K);
+    if (!rc) rc = m_alloc(h, &h->Z1, (size_t)max_batch * N);
+    if (!rc) rc = m_alloc(h, &h->H1, (size_t)max_batch * N);
+    if (!rc) rc = m_alloc(h, &h->Z2, (size_t)max_batch * N);
+    if (!rc) rc = m_alloc(h, &h->H2, (size_t)max_batch * N);
+    if (!rc) rc = m_alloc(h, &h->dZ1, (size_t)max_batch * N);
+    if (!rc) rc = m_alloc(h, &h->dZ2, (size_t)max_batch * N);
+    if (!rc) rc = m_alloc(h, &h->y, (size_t)max_batch);
+    if (!rc) rc = m_alloc(h, &h->dy, (size_t)max_batch);
+    if (!rc) rc = m_alloc(h, &h->loss, 1);
+    if (!rc && cudaMemcpy(h->p, init.data(), sizeof(float) * init.size(), cudaMemcpyHostToDevice) != cudaSuccess)
+        rc = QBVM_ERR_CUDA;
+    if (!rc && (cudaMemset(h->m, 0, sizeof(float) * h->nparam) != cudaSuccess ||
+                cudaMemset(h->v, 0, sizeof(float) * h->nparam) != cudaSuccess))
+        rc = QBVM_ERR_CUDA;
+    if (!rc) {
+        k_to_bf16<<<nblk(h->nparam), MLP_THREADS>>>(h->p, h->pb, h->nparam);
+        if (cudaDeviceSynchronize() != cudaSuccess) rc = QBVM_ERR_CUDA;
+    }
+    if (rc) {
+        for (void* q : h->allocs) cudaFree(q);
+        delete h;
+        return rc;
+    }
+    *out = h;
+    return QBVM_OK;
+}
+
+long long qbvm_mlp_num_params(const qbvm_mlp_t* h) { return h ? h->nparam : -1; }
+
+int qbvm_mlp_set_norm(qbvm_mlp_t* h, const float* mean, const float* sd) {
+    if (!h || !mean || !sd) return QBVM_ERR_BAD_ARG;
+    std::vector<float> is(h->in_dim);
+    for (int k = 0; k < h->in_dim; ++k) is[k] = sd[k] > 0 ? 1.f / sd[k] : 1.f;
+    if (cudaMemcpy(h->mu, mean, sizeof(float) * h->in_dim, cudaMemcpyHostToDevice) != cudaSuccess ||
+        cudaMemcpy(h->inv_sd, is.data(), sizeof(float) * h->in_dim, cudaMemcpyHostToDevice) != cudaSuccess)
+        return QBVM_ERR_CUDA;
+    h->has_norm = true;
+    return QBVM_OK;
+}
+
+int qbvm_mlp_get_params(const qbvm_mlp_t* h, float* params, float* adam_m, float* adam_v, long long* step) {
+    if (!h) return QBVM_ERR_BAD_ARG;
+    const size_t b = sizeof(float) * h->nparam;
+    if (params && cudaMemcpy(params, h->p, b, cudaMemcpyDeviceToHost) != cudaSuccess) return QBVM_ERR_CUDA;
+    if (adam_m && cudaMemcpy(adam_m, h->m, b, cudaMemcpyDeviceToHost) != cudaSuccess) return QBVM_ERR_CUDA;
+    if (adam_v && cudaMemcpy(adam_v, h->v, b, cudaMemcpyDeviceToHost) != cudaSuccess) return QBVM_ERR_CUDA;
+    if (step) *step = h->step;
+    return QBVM_OK;
+}
+
+int qbvm_mlp_set_params(qbvm_mlp_t* h, const float* params, const float* adam_m, const float* adam_v, long long step) {
+    if (!h || !params) return QBVM_ERR_BAD_ARG;
+    const size_t b = sizeof(float) * h->nparam;
+    if (cudaMemcpy(h->p, params, b, cudaMemcpyHostToDevice) != cudaSuccess) return QBVM_ERR_CUDA;
+    if (adam_m && cudaMemcpy(h->m, adam_m, b, cudaMemcpyHostToDevice) != cudaSuccess) return QBVM_ERR_CUDA;
+    if (adam_v && cudaMemcpy(h->v, adam_v, b, cudaMemcpyHostToDevice) != cudaSuccess) return QBVM_ERR_CUDA;
+    h->step = step;
+    k_to_bf16<<<nblk(h->nparam), MLP_THREADS>>>(h->p, h->pb, h->nparam);
+    return cudaDeviceSynchronize() == cudaSuccess ? QBVM_OK : QBVM_ERR_CUDA;
+}
+
+int qbvm_mlp_forward(qbvm_mlp_t* h, const float* x, int B, float* y, void* stream) {
+    if (!h || !x || !y || B < 1 || B > h->bmax) return QBVM_ERR_BAD_ARG;
+    cudaStream_t s = static_cast<cudaStream_t>(stream);
+    const int K = h->in_dim, N = h->width;
+    k_dense_relu<<<nblk((long long)B * N), MLP_THREADS, 0, s>>>(x, h->pb + h->oW1, h->p + h->ob1, B, K, N,
+                                                                 h->has_norm ? h->mu : nullptr,
+                                                                 h->has_norm ? h->inv_sd : nullptr, h->Z1, h->H1);
+    k_dense_relu<<<nblk((long long)B * N), MLP_THREADS, 0, s>>>(h->H1, h->pb + h->oW2, h->p + h->ob2, B, N, N, nullptr,
+                                                                 nullptr, h->Z2, h->H2);
+    k_dense_out<<<nblk((long long)B * 32), MLP_THREADS, 0, s>>>(h->H2, h->pb + h->ow3, h->p + h->ob3, B, N, y);
+    return cudaGetLastError() == cudaSuccess ? QBVM_OK : QBVM_ERR_CUDA;
+}
+
+int qbvm_mlp_gradients(qbvm_mlp_t* h, const float* x, const float* t, int B, float* grads, double* loss_out,
+                       void* stream) {
+    if (!h || !x || !t || B < 1 || B > h->bmax) return QBVM_ERR_BAD_ARG;
+    cudaStream_t s = static_cast<cudaStream_t>(stream);
+    int rc = mlp_grads(h, x, t, B, s);
+    if (rc) return rc;
+    if (grads && cudaMemcpyAsync(grads, h->g, sizeof(float) * h->nparam, cudaMemcpyDeviceToHost, s) != cudaSuccess)
+        return QBVM_ERR_CUDA;
+    if (loss_out && cudaMemcpyAsync(loss_out, h->loss, sizeof(double), cudaMemcpyDeviceToHost, s) != cudaSuccess)
+        return QBVM_ERR_CUDA;
+    return cudaStreamSynchronize(s) == cudaSuccess ? QBVM_OK : QBVM_ERR_CUDA;
+}
+
+int qbvm_mlp_train_step(qbvm_mlp_t* h, const float* x, const float* t, int B, float lr, void* stream) {
+    if (!h || !x || !t || B < 1 || B > h->bmax || !(lr > 0)) return QBVM_ERR_BAD_ARG;
+    cudaStream_t s = static_cast<cudaStream_t>(stream);
+    int rc = mlp_grads(h, x, t, B, s);
+    if (rc) return rc;
+    h->step += 1;
+    const float b1 = 0.9f, b2 = 0.999f;
+    const float c1 = 1.f - std::pow(b1, (float)h->step), c2 = 1.f - std::pow(b2, (float)h->step);
+    k_adam<<<nblk(h->nparam), MLP_THREADS, 0, s>>>(h->p, h->g, h->m, h->v, h->pb, h->nparam, lr, b1, b2, c1, c2, 1e-8f);
+    return cudaGetLastError() == cudaSuccess ? QBVM_OK : QBVM_ERR_CUDA;
+}
+
+int qbvm_mlp_last_loss(qbvm_mlp_t* h, double* loss, void* stream) {
+    if (!h || !loss) return QBVM_ERR_BAD_ARG;
+    cudaStream_t s = static_cast<cudaStream_t>(stream);
+    if (cudaMemcpyAsync(loss, h->loss, sizeof(double), cudaMemcpyDeviceToHost, s) != cudaSuccess) return QBVM_ERR_CUDA;
+    return cudaStreamSynchronize(s) == cudaSuccess ? QBVM_OK : QBVM_ERR_CUDA;
+}
+
+int qbvm_mlp_destroy(qbvm_mlp_t* h) {
+    if (!h) return QBVM_OK;
+    for (void* q : h->allocs) cudaFree(q);
+    delete h;
+    return QBVM_OK;
+}
+
+// ------------------------------------------------------------------ features
+
+int qbvm_features_plan(int m, double T, int nt, int max_batch, qbvm_features_t** out) {
+    if (!out || m < 4 || m > 1024 || (m & (m - 1)) || max_batch < 1 || !(T > 0) || nt < 2) return QBVM_ERR_BAD_ARG;
+    *out = nullptr;
+    qbvm_features_t* f = new (std::nothrow) qbvm_features();
+    if (!f) return QBVM_ERR_OOM;
+    f->M = m;
+    f->n = m - 1;
+    f->lm = 0;
+    while ((1 << f->lm) < m) ++f->lm;
+    f->T = T;
+    f->nt = nt;
+    f->bmax = max_batch;
+    f->Nx = (long long)f->n * f->n;
+    std::vector<unsigned char> bin((size_t)f->Nx);
+    std::vector<float> cnt(64, 0.f), inv(64, 0.f);
+    const double rmax = std::sqrt(2.0) * (f->n + 1);
+    for (int ky = 1; ky <= f->n; ++ky)
+        for (int kx = 1; kx <= f->n; ++kx) {
+            int b = (int)std::floor(64.0 * std::sqrt((double)kx * kx + (double)ky * ky) / rmax);
+            b = b > 63 ? 63 : b;
+            bin[(size_t)(ky - 1) * f->n + (kx - 1)] = (unsigned char)b;
+            cnt[b] += 1.f;
+        }
+    for (int b = 0; b < 64; ++b) inv[b] = cnt[b] > 0 ? 1.f / cnt[b] : 0.f;
+    std::vector<float2> tw(m);
+    std::vector<float> sn(m / 2 + 2, 0.f);
+    for (int i = 0; i < m; ++i) {
+        double a = M_PI * (2.0 * i / m);
+        tw[i] = make_float2((float)std::cos(a), (float)-std::sin(a));
+    }
+    for (int j = 0; j <= m / 2; ++j) sn[j] = (float)std::sin(M_PI * j / m);
+    int rc = m_alloc(f, &f->work, (size_t)max_batch * f->Nx);
+    if (!rc) rc = m_alloc(f, &f->bin, (size_t)f->Nx);
+    if (!rc) rc = m_alloc(f, &f->inv_count, 64);
+    if (!rc) rc = m_alloc(f, &f->delta, (size_t)max_batch);
+    if (!rc) rc = m_alloc(f, &f->tw, (size_t)m);
+    if (!rc) rc = m_alloc(f, &f->sn, sn.size());
+    if (!rc && (cudaMemcpy(f->bin, bin.data(), bin.size(), cudaMemcpyHostToDevice) != cudaSuccess ||
+                cudaMemcpy(f->inv_count, inv.data(), 64 * sizeof(float), cudaMemcpyHostToDevice) != cudaSuccess ||
+                cudaMemcpy(f->tw, tw.data(), tw.size() * sizeof(float2), cudaMemcpyHostToDevice) != cudaSuccess ||
+                cudaMemcpy(f->sn, sn.data(), sn.size() * sizeof(float), cudaMemcpyHostToDevice) != cudaSuccess))
+        rc = QBVM_ERR_CUDA;
+    if (rc) {
+        for (void* q : f->allocs) cudaFree(q);
+        delete f;
+        return rc;
+    }
+    *out = f;
+    return QBVM_OK;
+}
+
+int qbvm_features_run(qbvm_features_t* f, const double* g, const double* delta_host, int B, float* feats,
+                      void* stream) {
+    if (!f || !g || !delta_host || !feats || B < 1 || B > f->bmax) return QBVM_ERR_BAD_ARG;
+    cudaStream_t s = static_cast<cudaStream_t>(stream);
+    const long long n = f->n;
+    if (cudaMemcpyAsync(f->delta, delta_host, sizeof(double) * B, cudaMemcpyHostToDevice, s) != cudaSuccess)
+        return QBVM_ERR_CUDA;
+    // unnormalised DST-I along x then y of every instance, FP32
+    if (qbvm::launch_dst<float, double, 0>(g, f->work, f->n, f->lm, (long long)B * n, 1, f->tw, f->sn, s) != cudaSuccess)
+        return QBVM_ERR_CUDA;
+    if (qbvm::launch_dst<float, float, 0>(f->work, f->work, f->n, f->lm, (long long)B, n, f->tw, f->sn, s) != cudaSuccess)
+        return QBVM_ERR_CUDA;
+    const float scale = (float)((2.0 / f->M) * (2.0 / f->M));       // DST coefficient -> sine-series coefficient
+    k_spectrum_bins<<<B, MLP_THREADS, 0, s>>>(f->work, f->Nx, f->bin, f->inv_count, scale * scale, f->delta,
+                                              (float)f->T, (float)std::log2((double)f->nt), 67, feats);
+    return cudaGetLastError() == cudaSuccess ? QBVM_OK : QBVM_ERR_CUDA;
+}
+
+int qbvm_features_destroy(qbvm_features_t* f) {
+    if (!f) return QBVM_OK;
+    for (void* q : f->allocs) cudaFree(q);
+    delete f;
+    return QBVM_OK;
+}
+
+}  // extern "C"

@@ -542,7 +542,40 @@ int qbvm_sweep_plan(const qbvm_sweep_desc* d, qbvm_sweep_t** out) {
     if (!rc) rc = sw_alloc(p, &p->d_inst, (size_t)d->count);
     std::vector<double> alphas_all((size_t)d->count * na);
     size_t smem = 0;
-    for (int i = 0; i < d->count && !rc; ++i) {
+    // All per-instance tables go into one host arena uploaded in one copy; the
+    // per-instance device scratch (DST of g, z0 and y^0) into a second arena.
+    // DST-I tables are shared by every instance with the same length.
+    std::vector<unsigned char> arena;
+    auto put = [&](const void* src, size_t bytes) {
+        size_t off = (arena.size() + 255) & ~(size_t)255;
+        arena.resize(off + bytes);
+        std::memcpy(arena.data() + off, src, bytes);
+        return off;
+    };
+    struct Offs { size_t lamx, lamy, dtab, dtab32, cn, coef, al, twx, twy, snx, sny, gh, zh, yh; };
+    std::vector<Offs> offs(d->count);
+    std::vector<std::pair<int, std::pair<size_t, size_t>>> dst_cache;   // M -> (tw, sn) offsets
+    auto dst_tables = [&](int M) {
+        for (auto& c : dst_cache)
+            if (c.first == M) return c.second;
+        std::vector<double2> w(M);
+        std::vector<double> sv(M / 2 + 2, 0.0);
+        for (int m = 0; m < M; ++m) {
+            double a = M_PI * (2.0 * m / M);
+            w[m] = make_double2(std::cos(a), -std::sin(a));
+        }
+        for (int j = 0; j <= M / 2; ++j) sv[j] = std::sin(M_PI * j / M);
+        std::pair<size_t, size_t> r(put(w.data(), w.size() * sizeof(double2)), put(sv.data(), sv.size() * sizeof(double)));
+        dst_cache.push_back({M, r});
+        return r;
+    };
+    size_t scratch = 0;
+    auto take = [&](size_t bytes) {
+        size_t off = (scratch + 255) & ~(size_t)255;
+        scratch = off + bytes;
+        return off;
+    };
+    for (int i = 0; i < d->count; ++i) {
         const qbvm_sweep_instance& in = d->inst[i];
         SwInst& I = p->host_inst[i];
         std::memset(&I, 0, sizeof(I));
@@ -575,21 +608,21 @@ int qbvm_sweep_plan(const qbvm_sweep_desc* d, qbvm_sweep_t** out) {
         smem = std::max(smem, qbvm::dst_smem<double>(I.lmx));
         if (in.dim == 2) smem = std::max(smem, qbvm::dst_smem<double>(I.lmy));
         smem = std::max(smem, sizeof(double2) * (size_t)I.H);
-        // tables (FP64 on the host)
         std::vector<double> lx(I.nx), ly(I.ny, 0.0);
         for (int k = 1; k <= I.nx; ++k) {
-            double s = std::sin(M_PI * k / (2.0 * in.m[0]));
-            lx[k - 1] = I.tau * 4.0 / (hx * hx) * s * s;
+            double sk = std::sin(M_PI * k / (2.0 * in.m[0]));
+            lx[k - 1] = I.tau * 4.0 / (hx * hx) * sk * sk;
         }
         if (in.dim == 2)
             for (int k = 1; k <= I.ny; ++k) {
-                double s = std::sin(M_PI * k / (2.0 * in.m[1]));
-                ly[k - 1] = I.tau * 4.0 / (hy * hy) * s * s;
+                double sk = std::sin(M_PI * k / (2.0 * in.m[1]));
+                ly[k - 1] = I.tau * 4.0 / (hy * hy) * sk * sk;
             }
         std::vector<double2> dtab((size_t)na * I.H);
         std::vector<float2> dtab32((size_t)na * I.H);
         std::vector<double> cn(na), coef(na), al(na);
-        const double rule = in.form == QBVM_FORM_PQ ? in.delta : I.tau * in.delta;   // Section 5
+        const double rule = in.alpha_base > 0 ? in.alpha_base
+                                              : (in.form == QBVM_FORM_PQ ? in.delta : I.tau * in.delta);   // Section 5
         for (int a = 0; a < na; ++a) {
             double ex = na > 1 ? d->log10_lo + (d->log10_hi - d->log10_lo) * a / (na - 1) : d->log10_lo;
             double alpha = rule * std::pow(10.0, ex);
@@ -607,51 +640,44 @@ int qbvm_sweep_plan(const qbvm_sweep_desc* d, qbvm_sweep_t** out) {
             cn[a] = 2.0 * (-omega) * I.zscale / in.nt;
             coef[a] = in.form == QBVM_FORM_PQ ? alpha : alpha / I.tau;
         }
-        double *dlx, *dly, *dcn, *dcoef, *dal, *sn_x, *sn_y;
-        double2 *ddt, *twx, *twy;
-        float2* ddt32;
-        rc = sw_upload(p, &dlx, lx);
-        if (!rc) rc = sw_upload(p, &dly, ly);
-        if (!rc) rc = sw_upload(p, &ddt, dtab);
-        if (!rc) rc = sw_upload(p, &ddt32, dtab32);
-        if (!rc) rc = sw_upload(p, &dcn, cn);
-        if (!rc) rc = sw_upload(p, &dcoef, coef);
-        if (!rc) rc = sw_upload(p, &dal, al);
-        auto dst_tables = [&](int M, double2** tw, double** sn) {
-            std::vector<double2> w(M);
-            std::vector<double> sv(M / 2 + 2, 0.0);
-            for (int m = 0; m < M; ++m) {
-                double a = M_PI * (2.0 * m / M);
-                w[m] = make_double2(std::cos(a), -std::sin(a));
-            }
-            for (int j = 0; j <= M / 2; ++j) sv[j] = std::sin(M_PI * j / M);
-            int r = sw_upload(p, tw, w);
-            if (!r) r = sw_upload(p, sn, sv);
-            return r;
-        };
-        if (!rc) rc = dst_tables(in.m[0], &twx, &sn_x);
-        twy = twx;
-        sn_y = sn_x;
-        if (!rc && in.dim == 2) rc = dst_tables(in.m[1], &twy, &sn_y);
-        double *gh, *zh = nullptr, *yh = nullptr;
-        if (!rc) rc = sw_alloc(p, &gh, (size_t)I.Nx);
-        if (!rc && I.has_z0) rc = sw_alloc(p, &zh, (size_t)I.Nx);
-        if (!rc && I.has_y0) rc = sw_alloc(p, &yh, (size_t)I.Nx);
-        if (rc) break;
-        I.lamx = dlx;
-        I.lamy = dly;
-        I.dtab = ddt;
-        I.dtab32 = ddt32;
-        I.cn = dcn;
-        I.coef = dcoef;
-        I.alphas = dal;
-        I.twx = twx;
-        I.twy = twy;
-        I.snx = sn_x;
-        I.sny = sn_y;
-        I.ghat = gh;
-        I.zhat = zh;
-        I.yhat = yh;
+        Offs& o = offs[i];
+        o.lamx = put(lx.data(), lx.size() * sizeof(double));
+        o.lamy = put(ly.data(), ly.size() * sizeof(double));
+        o.dtab = put(dtab.data(), dtab.size() * sizeof(double2));
+        o.dtab32 = put(dtab32.data(), dtab32.size() * sizeof(float2));
+        o.cn = put(cn.data(), cn.size() * sizeof(double));
+        o.coef = put(coef.data(), coef.size() * sizeof(double));
+        o.al = put(al.data(), al.size() * sizeof(double));
+        auto tx = dst_tables(in.m[0]);
+        o.twx = tx.first;
+        o.snx = tx.second;
+        auto ty = in.dim == 2 ? dst_tables(in.m[1]) : tx;
+        o.twy = ty.first;
+        o.sny = ty.second;
+        o.gh = take(sizeof(double) * (size_t)I.Nx);
+        o.zh = I.has_z0 ? take(sizeof(double) * (size_t)I.Nx) : 0;
+        o.yh = I.has_y0 ? take(sizeof(double) * (size_t)I.Nx) : 0;
+    }
+    unsigned char *tab = nullptr, *scr = nullptr;
+    if (!rc) rc = sw_upload(p, &tab, arena);
+    if (!rc) rc = sw_alloc(p, &scr, scratch);
+    for (int i = 0; i < d->count && !rc; ++i) {
+        SwInst& I = p->host_inst[i];
+        const Offs& o = offs[i];
+        I.lamx = reinterpret_cast<const double*>(tab + o.lamx);
+        I.lamy = reinterpret_cast<const double*>(tab + o.lamy);
+        I.dtab = reinterpret_cast<const double2*>(tab + o.dtab);
+        I.dtab32 = reinterpret_cast<const float2*>(tab + o.dtab32);
+        I.cn = reinterpret_cast<const double*>(tab + o.cn);
+        I.coef = reinterpret_cast<const double*>(tab + o.coef);
+        I.alphas = reinterpret_cast<const double*>(tab + o.al);
+        I.twx = reinterpret_cast<const double2*>(tab + o.twx);
+        I.twy = reinterpret_cast<const double2*>(tab + o.twy);
+        I.snx = reinterpret_cast<const double*>(tab + o.snx);
+        I.sny = reinterpret_cast<const double*>(tab + o.sny);
+        I.ghat = reinterpret_cast<double*>(scr + o.gh);
+        I.zhat = I.has_z0 ? reinterpret_cast<double*>(scr + o.zh) : nullptr;
+        I.yhat = I.has_y0 ? reinterpret_cast<double*>(scr + o.yh) : nullptr;
         I.stats = p->d_stats + (size_t)i * na * 2;
         I.disc = p->d_disc + (size_t)i * na;
         I.err = p->d_err_out + (size_t)i * na;
