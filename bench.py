@@ -66,6 +66,8 @@ def parse():
     ap.add_argument("--no-refine", action="store_true", help="skip the FP32+refinement variant")
     ap.add_argument("--refine-only", action="store_true",
                     help="profiling aid: run only the FP32+refinement variant (no JSON headline)")
+    ap.add_argument("--no-extra", action="store_true",
+                    help="skip the 3D (127^3 x 128) and batched-sweep (512 instances) measurements")
     return ap.parse_args()
 
 
@@ -252,10 +254,9 @@ def our_arm(args, rank, world, device):
     step_ms = [a.elapsed_time(b) for a, b in evs]
     total_ms = sum(step_ms)
     if world > 1:
-        t = torch.tensor([total_ms], dtype=torch.float64, device=device)
-        torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
+        from paper_2107_06381_gb300.replicas import max_over_ranks
+        total_ms = max_over_ranks(total_ms, device)
         torch.distributed.barrier()
-        total_ms = float(t.item())
     kstats = {}
     for plan in plans:
         for name, (launches, ms) in plan.profile_read().items():
@@ -354,9 +355,8 @@ def our_arm(args, rank, world, device):
         e2e_times.append(time.perf_counter() - t0)
     e2e_s = sum(e2e_times)
     if world > 1:
-        t = torch.tensor([e2e_s], dtype=torch.float64, device=device)
-        torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
-        e2e_s = float(t.item())
+        from paper_2107_06381_gb300.replicas import max_over_ranks
+        e2e_s = max_over_ranks(e2e_s, device)
     e2e = {"value": world * unknowns_step * len(e2e_times) / e2e_s, "unit": UNIT,
            "h2d_bytes_per_step": sum(x.numel() * 8 for x in inputs),
            "d2h_bytes_per_step": sum(y.numel() * 8 for y in outputs),
@@ -385,6 +385,11 @@ def our_arm(args, rank, world, device):
         if refine is not None:
             refine["rel_err_vs_oracle"] = max_err(routs)
 
+    extra = {}
+    if not args.no_extra and not args.refine_only:
+        extra["c3_3d"] = c3_leg(args, device, stream, flush, rank == 0 and world == 1 and not args.no_cpu_baseline)
+        extra["c4_sweep"] = c4_leg(args, device, stream)
+
     out = {
         "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
         "warmup": args.warmup, "ms_per_step": total_ms / args.steps, "higher_is_better": True,
@@ -403,9 +408,104 @@ def our_arm(args, rank, world, device):
         "cpu_baseline": cpu,
         "rel_err_vs_oracle": rel_err,
         "fp32_refine": refine,
+        **extra,
     }
     for plan in plans:
         plan.close()
+    return out
+
+
+# ------------------------------------------------- 3D and batched-sweep rows
+
+def _time_solves(plan, fin, yout, stream, steps, flush):
+    import torch
+    evs = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(steps)]
+    with torch.cuda.stream(stream):
+        plan.solve(fin, yout, stream=stream)                 # warm-up
+        for i in range(steps):
+            evs[i][0].record(stream)
+            plan.solve(fin, yout, stream=stream)
+            evs[i][1].record(stream)
+            flush.zero_()
+    torch.cuda.synchronize()
+    return sum(a.elapsed_time(b) for a, b in evs) / steps
+
+
+def c3_leg(args, device, stream, flush, with_oracle):
+    """3D unit cube, 127^3 interior points x 128 levels (262 M unknowns), delta
+    right-hand side from 8 Gaussian bumps + 0.1% noise: the plain FP64 path
+    against FP32 transforms with double-float refinement."""
+    import numpy as np
+    import torch
+    import bhcp_inputs as bi
+    import paper_2107_06381_gb300 as Q
+    p = bi.make_c3()
+    grid = p.grid
+    alpha = p.delta
+    g = torch.as_tensor(p.g_delta.ravel(), dtype=torch.float64, device=device)
+    out = {"workload": "c3_3d_127cube_x128_delta_rhs", "unknowns": grid.unknowns}
+    ys = {}
+    for name, prec in (("fp64", Q.FP64), ("fp32_refine", Q.FP32_REFINE)):
+        y = torch.empty(grid.unknowns, dtype=torch.float64, device=device)
+        with Q.Plan(3, grid.M, grid.L, grid.T, grid.nt, Q.FORM_PQ, alpha, 0.0, prec, Q.RHS_DELTA) as plan:
+            ms = _time_solves(plan, g, y, stream, max(2, args.steps // 5), flush)
+            info = plan.info
+            out[name] = {"ms_per_solve": ms, "value": grid.unknowns / (ms / 1e3), "unit": UNIT,
+                         "refine_steps": info.last_refine_iters if prec == Q.FP32_REFINE else 0,
+                         "rel_residual": info.last_rel_residual if prec == Q.FP32_REFINE else None}
+        ys[name] = y
+    if with_oracle:
+        import oracle as O
+        levels = [0, 1, 64, 127]
+        want = O.solve_spectral(grid, O.PQ, alpha, O.rhs_block0(O.PQ, alpha, grid.tau, p.g_delta), levels=levels)
+        for name, y in ys.items():
+            got = y.view(grid.full_shape)[levels].cpu().numpy()
+            out[name]["rel_err_vs_oracle_sampled_levels"] = O.rel_l2(got, want)
+    return out
+
+
+def c4_leg(args, device, stream):
+    """512 uneven instances (1D n in {63..2047}, 2D {63,127,255}^2, nt in {32..512},
+    relative noise log-uniform in [1e-4, 1e-2]) x 16 alphas, one persistent
+    launch per run from a captured CUDA graph, launch shape autotuned."""
+    import numpy as np
+    import torch
+    import bhcp_inputs as bi
+    import paper_2107_06381_gb300 as Q
+    specs = bi.batch_specs_c4()
+    insts, keep = [], []
+    alpha_solves_unknowns = 0
+    for s in specs:
+        grid = bi.Grid(s["dim"], tuple(s["M"]), 1.0, 0.1, s["nt"])
+        rng = np.random.default_rng(s["seed"])
+        modes = [(1,), (2,), (3,)] if grid.dim == 1 else [(1, 1), (2, 1), (1, 2)]
+        z0 = bi.sine_field(grid, modes, rng.uniform(0.3, 1.0, 3))
+        gd, delta = bi.add_noise_gaussian(grid, bi.forward_discrete(grid, z0), s["rel_noise"], rng)
+        g = torch.as_tensor(gd.ravel(), dtype=torch.float64, device=device)
+        y0 = torch.empty(grid.Nx, dtype=torch.float64, device=device)
+        keep.append((g, y0))
+        insts.append(dict(dim=grid.dim, m=grid.M, L=1.0, T=0.1, nt=grid.nt, form=Q.FORM_PQ, delta=delta, g=g, y0=y0))
+        alpha_solves_unknowns += grid.unknowns
+    out = {"workload": "c4_batch_512_uneven_x16_alpha", "instances": len(specs), "n_alpha": 16}
+    for name, prec in (("fp32_scan", Q.FP32_REFINE), ("fp64_scan", Q.FP64)):
+        with Q.Sweep(insts, n_alpha=16, log10_lo=-1.5, log10_hi=1.5, tau_dp=1.1, precision=prec) as sw:
+            cfg = sw.autotune(repeats=2, stream=stream)
+            steps = max(3, args.steps // 4)
+            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            with torch.cuda.stream(stream):
+                sw.run(stream)
+                e0.record(stream)
+                for _ in range(steps):
+                    sw.run(stream)
+                e1.record(stream)
+            torch.cuda.synchronize()
+            ms = e0.elapsed_time(e1) / steps
+            al, disc, err, pick = sw.read(stream)
+            out[name] = {"ms_per_run": ms, "alpha_solves_per_s": len(specs) * 16 / (ms / 1e3),
+                         "all_at_once_unknowns_per_s": 16 * alpha_solves_unknowns / (ms / 1e3),
+                         "config": {"modes_per_thread": cfg.modes_per_thread, "ctas_per_sm": cfg.ctas_per_sm,
+                                    "grid": cfg.grid},
+                         "graph_launches_per_run": 1, "kernel_launches_per_run": 1}
     return out
 
 
