@@ -39,6 +39,31 @@ k_dst(const TIN* in, void* out, int n, int lm, int lw, long long outer, long lon
     dst_tile<R, TIN, OMODE, MAXB4, false>(in, out, n, lm, lw, outer, inner, (long long)blockIdx.x, tw, sn, smem_raw);
 }
 
+// The same tile with the transform length fixed at compile time (the tile
+// width follows from it), so that the whole pipeline inlines with constant
+// sizes; used for the common lengths M = 64 ... 512.
+template <typename R, typename TIN, int OMODE, int LM>
+__global__ void __launch_bounds__(TILE_THREADS)
+k_dst_ct(const TIN* in, void* out, long long outer, long long inner, const cplx<R>* __restrict__ tw,
+         const R* __restrict__ sn) {
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    constexpr int LW = 11 - LM;                     // 2^LM * 2^LW = DST_TILE complex values
+    static_assert((1 << (LM + LW)) == DST_TILE, "DST tile size");
+    dst_tile<R, TIN, OMODE, DST_TILE / 4 / TILE_THREADS, false>(in, out, (1 << LM) - 1, LM, LW, outer, inner,
+                                                                (long long)blockIdx.x, tw, sn, smem_raw);
+}
+
+template <typename R, typename TIN, int OMODE, int LM>
+static cudaError_t launch_dst_ct(const TIN* in, void* out, long long outer, long long inner, const void* tw,
+                                 const void* sn, long long blocks, size_t smem, cudaStream_t s) {
+    auto kern = k_dst_ct<R, TIN, OMODE, LM>;
+    cudaError_t e = set_smem(kern, smem);
+    if (e != cudaSuccess) return e;
+    kern<<<(unsigned)blocks, TILE_THREADS, smem, s>>>(in, out, outer, inner, reinterpret_cast<const cplx<R>*>(tw),
+                                                      reinterpret_cast<const R*>(sn));
+    return cudaGetLastError();
+}
+
 template <typename R>
 size_t dst_smem_bytes(int lm) { return dst_smem<R>(lm); }
 template size_t dst_smem_bytes<double>(int);
@@ -53,6 +78,15 @@ cudaError_t launch_dst(const TIN* in, void* out, int n, int lm, long long outer,
     if (inner == 1) blocks = (outer + 2 * W - 1) / (2 * W);
     else blocks = outer * ((inner + 2 * W - 1) / (2 * W));
     size_t smem = dst_smem<R>(lm);
+    if (n == (1 << lm) - 1) {
+        switch (lm) {
+            case 6: return launch_dst_ct<R, TIN, OMODE, 6>(in, out, outer, inner, tw, sn, blocks, smem, s);
+            case 7: return launch_dst_ct<R, TIN, OMODE, 7>(in, out, outer, inner, tw, sn, blocks, smem, s);
+            case 8: return launch_dst_ct<R, TIN, OMODE, 8>(in, out, outer, inner, tw, sn, blocks, smem, s);
+            case 9: return launch_dst_ct<R, TIN, OMODE, 9>(in, out, outer, inner, tw, sn, blocks, smem, s);
+            default: break;
+        }
+    }
     auto kern = k_dst<R, TIN, OMODE, DST_TILE / 4 / TILE_THREADS>;
     cudaError_t e = set_smem(kern, smem);
     if (e != cudaSuccess) return e;
@@ -88,13 +122,12 @@ QBVM_DST_INST(float, float, 2)
 // The scaling, divide and unscaling use tables of the transform's precision
 // (the FP32 tables are the FP64 ones rounded once on the host).
 template <typename R, int MAXB4>
-__global__ void __launch_bounds__(TILE_THREADS)
-k_time_solve(const R* in, R* out, long long Nx, int lh, int lw, const cplx<R>* __restrict__ tw,
-             const cplx<R>* __restrict__ gpow, const cplx<R>* __restrict__ gipw,
-             const cplx<R>* __restrict__ ak, const R* __restrict__ lamtau, R cnorm,
-             R rho_h, R rho_hinv, int delta_rhs, int n0_only) {
+__device__ __forceinline__ void time_solve_tile(const R* in, R* out, long long Nx, int lh, int lw,
+                                                const cplx<R>* __restrict__ tw, const cplx<R>* __restrict__ gpow,
+                                                const cplx<R>* __restrict__ gipw, const cplx<R>* __restrict__ ak,
+                                                const R* __restrict__ lamtau, R cnorm, R rho_h, R rho_hinv,
+                                                int delta_rhs, int n0_only, unsigned char* smem_raw) {
     using C = cplx<R>;
-    extern __shared__ __align__(16) unsigned char smem_raw[];
     const int H = 1 << lh, W = 1 << lw;
     C* buf = reinterpret_cast<C*>(smem_raw);
     C* stw = buf + (H << lw);
@@ -146,25 +179,76 @@ k_time_solve(const R* in, R* out, long long Nx, int lh, int lw, const cplx<R>* _
     }
 }
 
-static int tile_lw(int lp) {
+template <typename R, int MAXB4>
+__global__ void __launch_bounds__(TILE_THREADS)
+k_time_solve(const R* in, R* out, long long Nx, int lh, int lw, const cplx<R>* __restrict__ tw,
+             const cplx<R>* __restrict__ gpow, const cplx<R>* __restrict__ gipw,
+             const cplx<R>* __restrict__ ak, const R* __restrict__ lamtau, R cnorm,
+             R rho_h, R rho_hinv, int delta_rhs, int n0_only) {
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    time_solve_tile<R, MAXB4>(in, out, Nx, lh, lw, tw, gpow, gipw, ak, lamtau, cnorm, rho_h, rho_hinv, delta_rhs,
+                              n0_only, smem_raw);
+}
+
+// Compile-time half length LH and tile width LW (H * W = 4 * MAXB4 * TILE_THREADS).
+template <typename R, int MAXB4, int LH>
+__global__ void __launch_bounds__(TILE_THREADS)
+k_time_solve_ct(const R* in, R* out, long long Nx, const cplx<R>* __restrict__ tw,
+                const cplx<R>* __restrict__ gpow, const cplx<R>* __restrict__ gipw,
+                const cplx<R>* __restrict__ ak, const R* __restrict__ lamtau, R cnorm,
+                R rho_h, R rho_hinv, int delta_rhs, int n0_only) {
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    constexpr int LT = (MAXB4 == 4 ? 12 : MAXB4 == 2 ? 11 : 10);     // log2 of the tile size
+    time_solve_tile<R, MAXB4>(in, out, Nx, LH, LT - LH, tw, gpow, gipw, ak, lamtau, cnorm, rho_h, rho_hinv,
+                              delta_rhs, n0_only, smem_raw);
+}
+
+static int tile_lw(int lp, int tile = TILE_ELEMS) {
     int lw = 0;
-    while (((1 << lp) << (lw + 1)) <= TILE_ELEMS) ++lw;
+    while (((1 << lp) << (lw + 1)) <= tile) ++lw;
     return lw;
 }
+
+// FP64 tiles hold 4096 complex values (the FP64 pipe is the limit); FP32
+// tiles 2048, which halves the registers and doubles the CTAs per SM that
+// hide global-memory latency.
+template <typename R>
+constexpr int time_tile_maxb4() { return std::is_same<R, double>::value ? 4 : 2; }
 
 template <typename R>
 cudaError_t launch_time_solve(const R* in, R* out, const Tables& tb, double cnorm, int delta_rhs,
                               int n0_only, cudaStream_t s) {
+    constexpr int MB = time_tile_maxb4<R>();
+    constexpr int TILE = 4 * MB * TILE_THREADS;
     const int lh = tb.lnt - 1, H = 1 << lh;
-    const int lw = tile_lw(lh), W = 1 << lw;
+    const int lw = tile_lw(lh, TILE), W = 1 << lw;
     long long blocks = (tb.Nx + W - 1) / W;
     size_t smem = sizeof(cplx<R>) * ((size_t)H * W + H);
-    auto kern = k_time_solve<R, TILE_ELEMS / 4 / TILE_THREADS>;
-    cudaError_t e = set_smem(kern, smem);
-    if (e != cudaSuccess) return e;
     const bool f64 = std::is_same<R, double>::value;
     auto pick = [f64](const void* a, const void* b) { return reinterpret_cast<const cplx<R>*>(f64 ? a : b); };
     const R* lt = reinterpret_cast<const R*>(f64 ? (const void*)tb.lamtau : (const void*)tb.lamtau32);
+#define QBVM_TS_CT(LHV)                                                                                        \
+    case LHV: {                                                                                                \
+        auto kern = k_time_solve_ct<R, MB, LHV>;                                                               \
+        cudaError_t e = set_smem(kern, smem);                                                                  \
+        if (e != cudaSuccess) return e;                                                                        \
+        kern<<<(unsigned)blocks, TILE_THREADS, smem, s>>>(in, out, tb.Nx, pick(tb.tw_t, tb.tw_t32),            \
+                                                          pick(tb.gpow, tb.gpow32), pick(tb.gipw, tb.gipw32),  \
+                                                          pick(tb.ak, tb.ak32), lt, R(cnorm), R(tb.rho_h),     \
+                                                          R(tb.rho_hinv), delta_rhs, n0_only);                 \
+        return cudaGetLastError();                                                                             \
+    }
+    switch (lh) {
+        QBVM_TS_CT(5)
+        QBVM_TS_CT(6)
+        QBVM_TS_CT(7)
+        QBVM_TS_CT(8)
+        default: break;
+    }
+#undef QBVM_TS_CT
+    auto kern = k_time_solve<R, MB>;
+    cudaError_t e = set_smem(kern, smem);
+    if (e != cudaSuccess) return e;
     kern<<<(unsigned)blocks, TILE_THREADS, smem, s>>>(in, out, tb.Nx, lh, lw, pick(tb.tw_t, tb.tw_t32),
                                                       pick(tb.gpow, tb.gpow32), pick(tb.gipw, tb.gipw32),
                                                       pick(tb.ak, tb.ak32), lt, R(cnorm), R(tb.rho_h),
@@ -399,16 +483,19 @@ __global__ void k_reduce_pairs(const double* partials, int n, double* sums) {
 }
 
 // Double-float residual for the refinement: y is a double-float array (hi, lo),
-// f is FP64 (split exactly on load, one FP64 subtraction per value); the
-// stencil runs in double-float on the FP32 pipes.  Writes r.hi (FP32: the
-// right-hand side of the next FP32 correction solve) and per-block partial
-// sums of ||r||^2, ||f||^2 (r.hi^2, f.hi^2; enough digits for a stopping test).
-//   (A y)^n = c0 y^n - cp y^{n-1} - sum_d c_d (y_{i-e_d} + y_{i+e_d}),
-//   c0 = 1/tau + sum_d 2/h_d^2, cp = 1/tau (n >= 1) or omega/tau with y^{N} (n = 0).
+// f is FP64 (split exactly on load, integer pipes); the stencil runs in
+// double-float on the FP32 pipes.  Writes r.hi (FP32: the right-hand side of
+// the next FP32 correction solve) and per-block partial sums of ||r||^2,
+// ||f||^2 (r.hi^2, f.hi^2; enough digits for a stopping test).
+//   (A y)^n = ct (y^n - p^n) + sum_d c_d (2 y^n - y_{i-e_d} - y_{i+e_d}),
+//   ct = 1/tau, c_d = 1/h_d^2, p^n = y^{n-1} (n >= 1) or omega y^{N} (n = 0).
+// Differences are formed before the (inexact) scalings; with equal spacing on
+// every axis (EQ) the axes share one product: c (2d y - sum of neighbours).
 struct DfCoef {
-    dfloat c0, ct, cw, cx, cy, cz;
+    dfloat ct, omega, cx, cy, cz;
 };
 
+template <bool EQ>
 __global__ void __launch_bounds__(RES_THREADS)
 k_residual_df(const float2* __restrict__ y, const double* __restrict__ f, int delta_rhs, int nt, int nx, int ny,
               int nz, DfCoef k, double f0_scale, float* __restrict__ r_out, double* partials) {
@@ -416,6 +503,7 @@ k_residual_df(const float2* __restrict__ y, const double* __restrict__ f, int de
     const long long Nx = (long long)nx * ny * nz;
     const long long pl = (long long)nx * ny;
     const int rows = nt * ny * nz;
+    const int dims = 1 + (ny > 1) + (nz > 1);
     float rr = 0.f, ff = 0.f;
     auto ld = [&](long long i) { float2 v = y[i]; return dfloat{v.x, v.y}; };
     for (int row = blockIdx.x; row < rows; row += gridDim.x) {
@@ -425,24 +513,36 @@ k_residual_df(const float2* __restrict__ y, const double* __restrict__ f, int de
         const long long sbase = base - (long long)t * Nx;
         for (int ix = threadIdx.x; ix < nx; ix += blockDim.x) {
             const long long idx = base + ix;
-            dfloat Ay = df_mul(k.c0, ld(idx));
-            dfloat prev = t > 0 ? ld(idx - Nx) : ld((long long)(nt - 1) * Nx + sbase + ix);
-            Ay = df_add(Ay, df_neg(df_mul(t > 0 ? k.ct : k.cw, prev)));
-            dfloat s = {0.f, 0.f};
-            if (ix > 0) s = ld(idx - 1);
-            if (ix < nx - 1) s = df_add(s, ld(idx + 1));
-            Ay = df_add(Ay, df_neg(df_mul(k.cx, s)));
+            const dfloat yv = ld(idx);
+            dfloat d1;
+            if (t > 0) d1 = df_add(yv, df_neg(ld(idx - Nx)));
+            else d1 = df_add(yv, df_neg(df_mul(k.omega, ld((long long)(nt - 1) * Nx + sbase + ix))));
+            dfloat Ay = df_mul(k.ct, d1);
+            dfloat sx = {0.f, 0.f};
+            if (ix > 0) sx = ld(idx - 1);
+            if (ix < nx - 1) sx = df_add(sx, ld(idx + 1));
+            dfloat sy = {0.f, 0.f}, sz = {0.f, 0.f};
             if (ny > 1) {
-                s = {0.f, 0.f};
-                if (iy > 0) s = ld(idx - nx);
-                if (iy < ny - 1) s = df_add(s, ld(idx + nx));
-                Ay = df_add(Ay, df_neg(df_mul(k.cy, s)));
+                if (iy > 0) sy = ld(idx - nx);
+                if (iy < ny - 1) sy = df_add(sy, ld(idx + nx));
             }
             if (nz > 1) {
-                s = {0.f, 0.f};
-                if (iz > 0) s = ld(idx - pl);
-                if (iz < nz - 1) s = df_add(s, ld(idx + pl));
-                Ay = df_add(Ay, df_neg(df_mul(k.cz, s)));
+                if (iz > 0) sz = ld(idx - pl);
+                if (iz < nz - 1) sz = df_add(sz, ld(idx + pl));
+            }
+            if (EQ) {
+                dfloat S = sx;
+                if (ny > 1) S = df_add(S, sy);
+                if (nz > 1) S = df_add(S, sz);
+                // 2 d y: scalings by 2 and 4 are exact; 6 y = 4 y + 2 y in double-float
+                dfloat my = dims == 3 ? df_add(dfloat{4.f * yv.hi, 4.f * yv.lo}, dfloat{2.f * yv.hi, 2.f * yv.lo})
+                                      : dfloat{2.f * dims * yv.hi, 2.f * dims * yv.lo};
+                dfloat lap = df_add(my, df_neg(S));
+                Ay = df_add(Ay, df_mul(k.cx, lap));
+            } else {
+                Ay = df_add(Ay, df_mul(k.cx, df_add(dfloat{2.f * yv.hi, 2.f * yv.lo}, df_neg(sx))));
+                if (ny > 1) Ay = df_add(Ay, df_mul(k.cy, df_add(dfloat{2.f * yv.hi, 2.f * yv.lo}, df_neg(sy))));
+                if (nz > 1) Ay = df_add(Ay, df_mul(k.cz, df_add(dfloat{2.f * yv.hi, 2.f * yv.lo}, df_neg(sz))));
             }
             dfloat fv = {0.f, 0.f};
             if (delta_rhs) {
@@ -484,14 +584,20 @@ cudaError_t launch_residual_df(const void* y_df, const double* f, int delta_rhs,
                                cudaStream_t s) {
     DfCoef k;
     const double it = 1.0 / tb.tau;
-    k.c0 = df_const(it + 2.0 * (h2inv[0] + h2inv[1] + h2inv[2]));
     k.ct = df_const(it);
-    k.cw = df_const(tb.omega * it);
+    k.omega = df_const(tb.omega);
     k.cx = df_const(h2inv[0]);
     k.cy = df_const(h2inv[1]);
     k.cz = df_const(h2inv[2]);
-    k_residual_df<<<nblocks, RES_THREADS, 0, s>>>(reinterpret_cast<const float2*>(y_df), f, delta_rhs, tb.nt,
-                                                  tb.n[0], tb.n[1], tb.n[2], k, -tb.omega * it, r_out, partials);
+    const bool eq = (tb.dim < 2 || h2inv[1] == h2inv[0]) && (tb.dim < 3 || h2inv[2] == h2inv[0]);
+    if (eq)
+        k_residual_df<true><<<nblocks, RES_THREADS, 0, s>>>(reinterpret_cast<const float2*>(y_df), f, delta_rhs, tb.nt,
+                                                            tb.n[0], tb.n[1], tb.n[2], k, -tb.omega * it, r_out,
+                                                            partials);
+    else
+        k_residual_df<false><<<nblocks, RES_THREADS, 0, s>>>(reinterpret_cast<const float2*>(y_df), f, delta_rhs,
+                                                             tb.nt, tb.n[0], tb.n[1], tb.n[2], k, -tb.omega * it,
+                                                             r_out, partials);
     cudaError_t e = cudaGetLastError();
     if (e != cudaSuccess) return e;
     k_reduce_pairs<<<1, 1024, 0, s>>>(partials, nblocks, sums);

@@ -67,6 +67,11 @@ SMALL = [
     bi.Grid(2, (64, 64), math.pi, 1.0, 16),
     bi.Grid(3, (4, 8, 4), 1.0, 0.05, 4),
     bi.Grid(3, (16, 16, 16), 1.0, 0.05, 16),
+    # register-resident time transforms: N_t/2 = 32, 64, 128, 256
+    bi.Grid(2, (8, 32), 1.0, 0.1, 64),
+    bi.Grid(3, (8, 8, 8), 1.0, 0.1, 128),
+    bi.Grid(2, (16, 16), 1.0, 0.1, 256),
+    bi.Grid(2, (16, 8), 1.0, 0.2, 512),
 ]
 
 

@@ -44,6 +44,8 @@ GRIDS = [
     bi.Grid(2, (64, 64), 1.0, 0.1, 64),
     bi.Grid(3, (8, 4, 16), 1.0, 0.05, 8),
     bi.Grid(3, (32, 32, 32), 1.0, 0.05, 32),
+    bi.Grid(2, (32, 16), 1.0, 0.1, 512),
+    bi.Grid(3, (16, 16, 8), 1.0, 0.05, 128),
 ]
 
 
