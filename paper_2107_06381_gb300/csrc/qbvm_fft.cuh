@@ -173,6 +173,14 @@ __device__ __forceinline__ dfloat df_add(dfloat a, dfloat b) {
     s.lo += t.lo;
     return df_fast_two_sum(s.hi, s.lo);
 }
+// Double-float sum with one two-sum of the high parts: the absolute error is
+// O(u^2 (|a| + |b|)) (u = 2^-24) rather than O(u^2 |a + b|) -- the bound a
+// residual needs, since its inputs carry representation errors of that size.
+__device__ __forceinline__ dfloat df_add_sloppy(dfloat a, dfloat b) {
+    dfloat s = df_two_sum(a.hi, b.hi);
+    s.lo += a.lo + b.lo;
+    return df_fast_two_sum(s.hi, s.lo);
+}
 __device__ __forceinline__ dfloat df_neg(dfloat a) { return {-a.hi, -a.lo}; }
 __device__ __forceinline__ dfloat df_add_f(dfloat a, float b) {
     dfloat s = df_two_sum(a.hi, b);

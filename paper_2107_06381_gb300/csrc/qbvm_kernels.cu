@@ -15,6 +15,7 @@
 // FFT + unscaling.
 #include "qbvm_dst.cuh"
 #include "qbvm_fft.cuh"
+#include "qbvm_regdst.cuh"
 #include "qbvm_internal.h"
 
 #include <cstdint>
@@ -64,6 +65,43 @@ static cudaError_t launch_dst_ct(const TIN* in, void* out, long long outer, long
     return cudaGetLastError();
 }
 
+// FP32 DST with the transform in registers (rd::tile), M = 64, 128, 256.
+template <typename TIN, int OMODE, int LM, bool XAX>
+__global__ void __launch_bounds__(rd::threads<LM>())
+k_dst_reg(const TIN* in, void* out, long long outer, long long inner, const float2* __restrict__ tw,
+          const float* __restrict__ sn) {
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    rd::tile<TIN, OMODE, LM, XAX>(in, out, outer, inner, (long long)blockIdx.x, tw, sn, smem_raw);
+}
+
+template <typename TIN, int OMODE, int LM, bool XAX>
+static cudaError_t launch_dst_reg(const TIN* in, void* out, long long outer, long long inner, const void* tw,
+                                  const void* sn, cudaStream_t s) {
+    auto kern = k_dst_reg<TIN, OMODE, LM, XAX>;
+    constexpr size_t smem = rd::smem_bytes<LM, XAX>();
+    cudaError_t e = set_smem(kern, smem);
+    if (e != cudaSuccess) return e;
+    const long long blocks = XAX ? (outer + rd::NCOL - 1) / rd::NCOL : outer * ((inner + rd::NCOL - 1) / rd::NCOL);
+    kern<<<(unsigned)blocks, rd::threads<LM>(), smem, s>>>(in, out, outer, inner,
+                                                           reinterpret_cast<const float2*>(tw),
+                                                           reinterpret_cast<const float*>(sn));
+    return cudaGetLastError();
+}
+
+template <typename TIN, int OMODE>
+static cudaError_t launch_dst_reg_any(const TIN* in, void* out, int lm, long long outer, long long inner,
+                                      const void* tw, const void* sn, cudaStream_t s) {
+    const bool x = inner == 1;
+    switch (lm) {
+        case 6: return x ? launch_dst_reg<TIN, OMODE, 6, true>(in, out, outer, inner, tw, sn, s)
+                         : launch_dst_reg<TIN, OMODE, 6, false>(in, out, outer, inner, tw, sn, s);
+        case 7: return x ? launch_dst_reg<TIN, OMODE, 7, true>(in, out, outer, inner, tw, sn, s)
+                         : launch_dst_reg<TIN, OMODE, 7, false>(in, out, outer, inner, tw, sn, s);
+        default: return x ? launch_dst_reg<TIN, OMODE, 8, true>(in, out, outer, inner, tw, sn, s)
+                          : launch_dst_reg<TIN, OMODE, 8, false>(in, out, outer, inner, tw, sn, s);
+    }
+}
+
 template <typename R>
 size_t dst_smem_bytes(int lm) { return dst_smem<R>(lm); }
 template size_t dst_smem_bytes<double>(int);
@@ -78,6 +116,8 @@ cudaError_t launch_dst(const TIN* in, void* out, int n, int lm, long long outer,
     if (inner == 1) blocks = (outer + 2 * W - 1) / (2 * W);
     else blocks = outer * ((inner + 2 * W - 1) / (2 * W));
     size_t smem = dst_smem<R>(lm);
+    if (std::is_same<R, float>::value && n == (1 << lm) - 1 && lm >= 6 && lm <= 8)
+        return launch_dst_reg_any<TIN, OMODE>(in, out, lm, outer, inner, tw, sn, s);
     if (n == (1 << lm) - 1) {
         switch (lm) {
             case 6: return launch_dst_ct<R, TIN, OMODE, 6>(in, out, outer, inner, tw, sn, blocks, smem, s);
@@ -491,6 +531,8 @@ __global__ void k_reduce_pairs(const double* partials, int n, double* sums) {
 //   ct = 1/tau, c_d = 1/h_d^2, p^n = y^{n-1} (n >= 1) or omega y^{N} (n = 0).
 // Differences are formed before the (inexact) scalings; with equal spacing on
 // every axis (EQ) the axes share one product: c (2d y - sum of neighbours).
+// Sums use df_add_sloppy: its error, O(u^2) times the magnitudes of the terms,
+// is of the size the double-float inputs already carry.
 struct DfCoef {
     dfloat ct, omega, cx, cy, cz;
 };
@@ -515,34 +557,34 @@ k_residual_df(const float2* __restrict__ y, const double* __restrict__ f, int de
             const long long idx = base + ix;
             const dfloat yv = ld(idx);
             dfloat d1;
-            if (t > 0) d1 = df_add(yv, df_neg(ld(idx - Nx)));
-            else d1 = df_add(yv, df_neg(df_mul(k.omega, ld((long long)(nt - 1) * Nx + sbase + ix))));
+            if (t > 0) d1 = df_add_sloppy(yv, df_neg(ld(idx - Nx)));
+            else d1 = df_add_sloppy(yv, df_neg(df_mul(k.omega, ld((long long)(nt - 1) * Nx + sbase + ix))));
             dfloat Ay = df_mul(k.ct, d1);
             dfloat sx = {0.f, 0.f};
             if (ix > 0) sx = ld(idx - 1);
-            if (ix < nx - 1) sx = df_add(sx, ld(idx + 1));
+            if (ix < nx - 1) sx = df_add_sloppy(sx, ld(idx + 1));
             dfloat sy = {0.f, 0.f}, sz = {0.f, 0.f};
             if (ny > 1) {
                 if (iy > 0) sy = ld(idx - nx);
-                if (iy < ny - 1) sy = df_add(sy, ld(idx + nx));
+                if (iy < ny - 1) sy = df_add_sloppy(sy, ld(idx + nx));
             }
             if (nz > 1) {
                 if (iz > 0) sz = ld(idx - pl);
-                if (iz < nz - 1) sz = df_add(sz, ld(idx + pl));
+                if (iz < nz - 1) sz = df_add_sloppy(sz, ld(idx + pl));
             }
             if (EQ) {
                 dfloat S = sx;
-                if (ny > 1) S = df_add(S, sy);
-                if (nz > 1) S = df_add(S, sz);
+                if (ny > 1) S = df_add_sloppy(S, sy);
+                if (nz > 1) S = df_add_sloppy(S, sz);
                 // 2 d y: scalings by 2 and 4 are exact; 6 y = 4 y + 2 y in double-float
-                dfloat my = dims == 3 ? df_add(dfloat{4.f * yv.hi, 4.f * yv.lo}, dfloat{2.f * yv.hi, 2.f * yv.lo})
+                dfloat my = dims == 3 ? df_add_sloppy(dfloat{4.f * yv.hi, 4.f * yv.lo}, dfloat{2.f * yv.hi, 2.f * yv.lo})
                                       : dfloat{2.f * dims * yv.hi, 2.f * dims * yv.lo};
-                dfloat lap = df_add(my, df_neg(S));
-                Ay = df_add(Ay, df_mul(k.cx, lap));
+                dfloat lap = df_add_sloppy(my, df_neg(S));
+                Ay = df_add_sloppy(Ay, df_mul(k.cx, lap));
             } else {
-                Ay = df_add(Ay, df_mul(k.cx, df_add(dfloat{2.f * yv.hi, 2.f * yv.lo}, df_neg(sx))));
-                if (ny > 1) Ay = df_add(Ay, df_mul(k.cy, df_add(dfloat{2.f * yv.hi, 2.f * yv.lo}, df_neg(sy))));
-                if (nz > 1) Ay = df_add(Ay, df_mul(k.cz, df_add(dfloat{2.f * yv.hi, 2.f * yv.lo}, df_neg(sz))));
+                Ay = df_add_sloppy(Ay, df_mul(k.cx, df_add_sloppy(dfloat{2.f * yv.hi, 2.f * yv.lo}, df_neg(sx))));
+                if (ny > 1) Ay = df_add_sloppy(Ay, df_mul(k.cy, df_add_sloppy(dfloat{2.f * yv.hi, 2.f * yv.lo}, df_neg(sy))));
+                if (nz > 1) Ay = df_add_sloppy(Ay, df_mul(k.cz, df_add_sloppy(dfloat{2.f * yv.hi, 2.f * yv.lo}, df_neg(sz))));
             }
             dfloat fv = {0.f, 0.f};
             if (delta_rhs) {
@@ -550,7 +592,7 @@ k_residual_df(const float2* __restrict__ y, const double* __restrict__ f, int de
             } else {
                 fv = df_from_double(f[idx]);
             }
-            dfloat r = df_add(fv, df_neg(Ay));
+            dfloat r = df_add_sloppy(fv, df_neg(Ay));
             r_out[idx] = r.hi;
             rr = fmaf(r.hi, r.hi, rr);
             ff = fmaf(fv.hi, fv.hi, ff);

@@ -46,6 +46,12 @@ GRIDS = [
     bi.Grid(3, (32, 32, 32), 1.0, 0.05, 32),
     bi.Grid(2, (32, 16), 1.0, 0.1, 512),
     bi.Grid(3, (16, 16, 8), 1.0, 0.05, 128),
+    # register-resident FP32 DST lengths (M = 64, 128, 256) along x and along y / z,
+    # with ragged row and column tiles
+    bi.Grid(2, (256, 128), 1.0, 0.1, 8),
+    bi.Grid(2, (128, 256), 1.0, 0.1, 16),
+    bi.Grid(3, (128, 64, 256), 1.0, 0.05, 4),
+    bi.Grid(3, (64, 256, 128), 1.0, 0.05, 2),
 ]
 
 
@@ -62,6 +68,24 @@ def test_refined_solution_matches_oracle(grid, form, rhs_kind):
     assert O.rel_l2(got, want) <= TOL, (iters, rel)
     # the double-float residual floors near 1e-12 (FP64 would floor near 1e-14)
     assert iters >= 1 and rel <= 1e-11
+
+
+@pytest.mark.parametrize("grid", [bi.Grid(2, (256, 64), 1.0, 0.1, 32), bi.Grid(3, (64, 128, 64), 1.0, 0.05, 8)],
+                         ids=["d2-M256x64", "d3-M64x128x64"])
+def test_fp32_solve_alone_is_fp32_accurate(grid):
+    """With a tolerance of 1 the first residual check passes, so y is the bare
+    FP32 solve: its error against the oracle is that of FP32 transforms
+    amplified by cond(V) = |omega|^(1 - 1/nt) (here 1e3), far from the O(1) of a
+    wrong transform.  Its relative residual is FP32 rounding times the spatial
+    condition number (about 4 M^2 / pi^2 = 2.7e4 at M = 256)."""
+    alpha = 1e-3
+    F = bi.random_general_rhs(grid, seed=35)
+    want = O.solve_spectral(grid, Q.FORM_PQ, alpha, F)
+    got, iters, rel = refine_solve(grid, Q.FORM_PQ, alpha, F, Q.RHS_GENERAL, tol=1.0)
+    err = O.rel_l2(got, want)
+    assert iters == 0
+    assert err <= 1e-3, err
+    assert rel <= 1e-2
 
 
 def test_refined_n0_only():
