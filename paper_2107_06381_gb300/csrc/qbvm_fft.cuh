@@ -240,6 +240,13 @@ QBVM_HD int qbvm_clzll(unsigned long long a) {
     return __builtin_clzll(a);
 #endif
 }
+QBVM_HD int qbvm_clz(unsigned int a) {
+#ifdef __CUDA_ARCH__
+    return __clz((int)a);
+#else
+    return __builtin_clz(a);
+#endif
+}
 QBVM_HD float qbvm_bitsf(unsigned int u) {
 #ifdef __CUDA_ARCH__
     return __uint_as_float(u);
@@ -250,52 +257,88 @@ QBVM_HD float qbvm_bitsf(unsigned int u) {
 #endif
 }
 
+// The hardware conversions for the rare operands outside the integer paths
+// range.  Out of line on the device, so that the compiler cannot evaluate them
+// speculatively (as a predicated select) for every element.
+#ifdef __CUDA_ARCH__
+static __device__ __noinline__ float qbvm_rem_hw(double x, float h) { return (float)(x - (double)h); }
+static __device__ __noinline__ float qbvm_f_hw(double x) { return (float)x; }
+static __device__ __noinline__ double qbvm_join_hw(float hi, float lo) { return (double)hi + (double)lo; }
+#else
+inline float qbvm_rem_hw(double x, float h) { return (float)(x - (double)h); }
+inline float qbvm_f_hw(double x) { return (float)x; }
+inline double qbvm_join_hw(float hi, float lo) { return (double)hi + (double)lo; }
+#endif
+
+// High and low 32-bit words of a double.  On the device these are register
+// moves the compiler cannot see through: tests on the bits of the reinterpreted
+// 64-bit value were turned into FP64 compares (FP64-pipe instructions).
+QBVM_HD unsigned int qbvm_dhi(double x) {
+#ifdef __CUDA_ARCH__
+    return (unsigned int)__double2hiint(x);
+#else
+    return (unsigned int)(qbvm_dbits(x) >> 32);
+#endif
+}
+QBVM_HD unsigned int qbvm_dlo(double x) {
+#ifdef __CUDA_ARCH__
+    return (unsigned int)__double2loint(x);
+#else
+    return (unsigned int)qbvm_dbits(x);
+#endif
+}
+
 // Round-to-nearest-even FP64 -> FP32 of x, and the exact remainder x - hi as
 // an FP32 (rounded to nearest; the remainder has at most 29 significant bits).
+// 32-bit integer arithmetic on the two words of x.
 QBVM_HD void qbvm_split_d(double x, float* hi, float* lo) {
-    const unsigned long long b = qbvm_dbits(x);
-    if ((b << 1) == 0) {                                  // +-0: exact, integer path
-        *hi = qbvm_bitsf((unsigned int)(b >> 32));
+    const unsigned int H = qbvm_dhi(x), L = qbvm_dlo(x);
+    if (((H << 1) | L) == 0) {                            // +-0: exact, integer path
+        *hi = qbvm_bitsf(H);
         *lo = 0.0f;
         return;
     }
-    const int e = (int)((b >> 52) & 0x7FF);
+    const int e = (int)((H >> 20) & 0x7FF);
     const int fe = e - 1023 + 127;                       // FP32 biased exponent of hi
     if (fe < 30 || fe > 253) {                           // tiny, huge, Inf, NaN: hardware path
-        float h = (float)x;
+        float h = qbvm_f_hw(x);
         *hi = h;
-        *lo = (float)(x - (double)h);
+        *lo = qbvm_rem_hw(x, h);
         return;
     }
-    const unsigned int sign = (unsigned int)(b >> 32) & 0x80000000u;
-    const unsigned long long mm = (b & 0xFFFFFFFFFFFFFull) | (1ull << 52);   // 53-bit significand
-    unsigned long long q = mm >> 29;                      // 24 bits
-    const unsigned long long rem = mm & ((1ull << 29) - 1);
-    if (rem > (1ull << 28) || (rem == (1ull << 28) && (q & 1))) ++q;
-    // remainder in units of 2^(e - 1075): mm - q * 2^29, |r| <= 2^28
-    const long long r = (long long)mm - (long long)(q << 29);
+    const unsigned int sign = H & 0x80000000u;
+    // 53-bit significand = [1 | 20 bits of H | 32 bits of L]; its top 24 bits:
+    unsigned int q = (((H & 0xFFFFFu) | 0x100000u) << 3) | (L >> 29);
+    const unsigned int rem = L & 0x1FFFFFFFu;            // the 29 bits below
+    int r;                                                // remainder in units of 2^(e - 1075), |r| <= 2^28
+    if (rem > 0x10000000u || (rem == 0x10000000u && (q & 1))) {
+        ++q;
+        r = (int)rem - 0x20000000;
+    } else {
+        r = (int)rem;
+    }
     int he = fe;
-    if (q == (1ull << 24)) {                               // rounding carried into a new binade
+    if (q == 0x1000000u) {                                // rounding carried into a new binade
         q >>= 1;
         ++he;
     }
-    *hi = qbvm_bitsf(sign | ((unsigned int)he << 23) | ((unsigned int)q & 0x7FFFFFu));
+    *hi = qbvm_bitsf(sign | ((unsigned int)he << 23) | (q & 0x7FFFFFu));
     if (r == 0) {
         *lo = 0.0f;
         return;
     }
     // lo = sign * r * 2^(e - 1075): normalise |r| (<= 29 bits) to 24 bits, RNE
-    unsigned long long a = (unsigned long long)(r < 0 ? -r : r);
+    const unsigned int a = (unsigned int)(r < 0 ? -r : r);
     const unsigned int lsign = sign ^ (r < 0 ? 0x80000000u : 0u);
-    int top = 63 - qbvm_clzll(a);                    // position of the leading bit (0..28)
+    const int top = 31 - qbvm_clz(a);                    // position of the leading bit (0..28)
     int le = (e - 1075) + top + 127;                      // FP32 biased exponent of lo
-    unsigned long long lq;
+    unsigned int lq;
     if (top > 23) {
         const int sh = top - 23;
         lq = a >> sh;
-        const unsigned long long lr = a & ((1ull << sh) - 1), half = 1ull << (sh - 1);
+        const unsigned int lr = a & ((1u << sh) - 1), half = 1u << (sh - 1);
         if (lr > half || (lr == half && (lq & 1))) ++lq;
-        if (lq == (1ull << 24)) {
+        if (lq == 0x1000000u) {
             lq >>= 1;
             ++le;
         }
@@ -303,11 +346,10 @@ QBVM_HD void qbvm_split_d(double x, float* hi, float* lo) {
         lq = a << (23 - top);
     }
     if (le < 1) {                                         // below the FP32 normal range: hardware path
-        float h = *hi;
-        *lo = (float)(x - (double)h);
+        *lo = qbvm_rem_hw(x, *hi);
         return;
     }
-    *lo = qbvm_bitsf(lsign | ((unsigned int)le << 23) | ((unsigned int)lq & 0x7FFFFFu));
+    *lo = qbvm_bitsf(lsign | ((unsigned int)le << 23) | (lq & 0x7FFFFFu));
 }
 
 // (double)hi + (double)lo, correctly rounded, for a pair with |lo| <= |hi|
@@ -323,7 +365,7 @@ QBVM_HD double qbvm_join_df(float hi, float lo) {
                           ((unsigned long long)(e2 - 127 + 1023) << 52) |
                           ((unsigned long long)(lb & 0x7FFFFFu) << 29));
     if (e1 == 0 || e1 == 255 || e2 == 255 || (e2 == 0 && (lb & 0x7FFFFFu)) || e2 > e1)
-        return (double)hi + (double)lo;                   // zero/denormal/Inf/NaN/unnormalised: hardware
+        return qbvm_join_hw(hi, lo);                      // zero/denormal/Inf/NaN/unnormalised: hardware
     const unsigned long long sign = (unsigned long long)(hb & 0x80000000u) << 32;
     long long S = (long long)((unsigned long long)((hb & 0x7FFFFFu) | 0x800000u) << 39);   // < 2^63
     if (e2 != 0) {

@@ -243,6 +243,153 @@ k_time_solve_ct(const R* in, R* out, long long Nx, const cplx<R>* __restrict__ t
                               delta_rhs, n0_only, smem_raw);
 }
 
+// FP32 time solve with the transforms in registers, H = nt/2 = 32 ... 256.
+// The same three steps as time_solve_tile, per spatial mode l, with the
+// length-H DFT split as N1 x N2 (n = N2 n1 + n2, k = k1 + N1 k2): thread n2 of
+// the T = N2 threads of mode l does the length-N1 DFT over n1 of its time
+// indices, the padded shared-memory transpose hands each thread the k1 rows it
+// owns, and the length-N2 DFTs give it the frequencies k1 + N1 k2.  After the
+// divide the inverse runs in mirror order (length-N2 DFTs over k2, twiddle,
+// transpose back, length-N1 DFTs over k1), which leaves each thread holding
+// exactly the time indices it loaded.  Loads and stores go straight between
+// global memory and registers (a warp reads 32/T consecutive modes of T rows).
+// With the delta right-hand side the forward transform of f^0 e_0 is the
+// constant f^0 and is not computed.
+template <int LH> struct TsCfg;
+template <> struct TsCfg<8> { static constexpr int N1 = 16, N2 = 16, BS = 17, FB = 272; };
+template <> struct TsCfg<7> { static constexpr int N1 = 16, N2 = 8, BS = 9, FB = 152; };
+template <> struct TsCfg<6> { static constexpr int N1 = 8, N2 = 8, BS = 9, FB = 72; };
+template <> struct TsCfg<5> { static constexpr int N1 = 8, N2 = 4, BS = 5, FB = 52; };
+constexpr int TS_MODES = 32;     // spatial modes per CTA
+
+template <int LH>
+constexpr size_t ts_reg_smem() { return (size_t)(4 * (1 << LH) + TS_MODES * TsCfg<LH>::FB) * sizeof(float2); }
+
+template <int LH>
+__global__ void __launch_bounds__(TS_MODES * TsCfg<LH>::N2)
+k_time_solve_reg(const float* in, float* out, long long Nx, const float2* __restrict__ tw,
+                 const float2* __restrict__ gpow, const float2* __restrict__ gipw, const float2* __restrict__ ak,
+                 const float* __restrict__ lamtau, float cnorm, float rho_h, float rho_hinv, int delta_rhs,
+                 int n0_only) {
+    using G = TsCfg<LH>;
+    constexpr int H = 1 << LH, N1 = G::N1, N2 = G::N2, T = N2, NTH = TS_MODES * T, Q = N1 / T;
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    float2* stw = reinterpret_cast<float2*>(smem_raw);
+    float2* sgp = stw + H;
+    float2* sgi = sgp + H;
+    float2* sak = sgi + H;
+    float2* fbuf = sak + H;
+    const int tid = threadIdx.x;
+    for (int i = tid; i < H; i += NTH) {
+        stw[i] = tw[i];
+        sgp[i] = gpow[i];
+        sgi[i] = gipw[i];
+        sak[i] = ak[i];
+    }
+    const int c = tid / T, n2 = tid % T;
+    const long long l = (long long)blockIdx.x * TS_MODES + c;
+    const bool ok = l < Nx;
+    float2* buf = fbuf + c * G::FB;
+    float2 X[Q][N2];
+    if (delta_rhs) {
+        const float f0 = ok ? in[l] : 0.f;
+#pragma unroll
+        for (int q = 0; q < Q; ++q)
+#pragma unroll
+            for (int k2 = 0; k2 < N2; ++k2) X[q][k2] = make_float2(f0, 0.f);
+        __syncthreads();
+    } else {
+        float fa[N1], fh[N1];
+#pragma unroll
+        for (int n1 = 0; n1 < N1; ++n1) {
+            const long long n = N2 * n1 + n2;
+            fa[n1] = ok ? in[n * Nx + l] : 0.f;
+            fh[n1] = ok ? in[(n + H) * Nx + l] : 0.f;
+        }
+        __syncthreads();                                   // tables
+        float2 v[N1];
+#pragma unroll
+        for (int n1 = 0; n1 < N1; ++n1) {                  // gamma^t (f_t + i rho^H f_{t+H})
+            const float2 g = sgp[N2 * n1 + n2];
+            const float f1 = rho_h * fh[n1];
+            v[n1] = make_float2(fmaf(g.x, fa[n1], -g.y * f1), fmaf(g.y, fa[n1], g.x * f1));
+        }
+        rd::rdft<N1, +1>(v);
+#pragma unroll
+        for (int k1 = 1; k1 < N1; ++k1)
+            if (n2) v[k1] = cmulc(v[k1], stw[n2 * k1]);    // exp(+2 pi i n2 k1 / H)
+#pragma unroll
+        for (int k1 = 0; k1 < N1; ++k1) buf[k1 * G::BS + n2] = v[k1];
+        __syncwarp();
+#pragma unroll
+        for (int q = 0; q < Q; ++q) {
+            const int k1 = n2 + T * q;
+#pragma unroll
+            for (int j = 0; j < N2; ++j) X[q][j] = buf[k1 * G::BS + j];
+            rd::rdft<N2, +1>(X[q]);
+        }
+    }
+    // Step (b): divide by d_{2k} + tau Lambda_l
+    const float lt = ok ? lamtau[l] : 0.f;
+#pragma unroll
+    for (int q = 0; q < Q; ++q) {
+        const int k1 = n2 + T * q;
+#pragma unroll
+        for (int k2 = 0; k2 < N2; ++k2) {
+            const float2 a = sak[k1 + N1 * k2];
+            const float zr = a.x + lt, zi = a.y;
+            const float inv = cnorm / fmaf(zr, zr, zi * zi);
+            const float2 u = X[q][k2];
+            X[q][k2] = make_float2(fmaf(u.x, zr, u.y * zi) * inv, fmaf(u.y, zr, -u.x * zi) * inv);
+        }
+    }
+    // Step (c): inverse DFT in mirror order
+#pragma unroll
+    for (int q = 0; q < Q; ++q) {
+        const int k1 = n2 + T * q;
+        rd::rdft<N2, -1>(X[q]);
+#pragma unroll
+        for (int j = 1; j < N2; ++j)
+            if (k1) X[q][j] = cmul(X[q][j], stw[j * k1]);  // exp(-2 pi i j k1 / H)
+    }
+    __syncwarp();
+#pragma unroll
+    for (int q = 0; q < Q; ++q) {
+        const int k1 = n2 + T * q;
+#pragma unroll
+        for (int j = 0; j < N2; ++j) buf[k1 * G::BS + j] = X[q][j];
+    }
+    __syncwarp();
+    float2 w[N1];
+#pragma unroll
+    for (int k1 = 0; k1 < N1; ++k1) w[k1] = buf[k1 * G::BS + n2];
+    rd::rdft<N1, -1>(w);
+    if (!ok) return;
+#pragma unroll
+    for (int n1 = 0; n1 < N1; ++n1) {
+        const int n = N2 * n1 + n2;
+        if (n0_only && n != 0) continue;
+        const float2 gi = sgi[n], qv = w[n1];
+        out[(long long)n * Nx + l] = fmaf(gi.x, qv.x, -gi.y * qv.y);
+        if (!n0_only) out[(long long)(n + H) * Nx + l] = rho_hinv * fmaf(gi.x, qv.y, gi.y * qv.x);
+    }
+}
+
+template <int LH>
+static cudaError_t launch_time_solve_reg(const float* in, float* out, const Tables& tb, float cnorm, int delta_rhs,
+                                         int n0_only, cudaStream_t s) {
+    auto kern = k_time_solve_reg<LH>;
+    constexpr size_t smem = ts_reg_smem<LH>();
+    cudaError_t e = set_smem(kern, smem);
+    if (e != cudaSuccess) return e;
+    const long long blocks = (tb.Nx + TS_MODES - 1) / TS_MODES;
+    kern<<<(unsigned)blocks, TS_MODES * TsCfg<LH>::N2, smem, s>>>(
+        in, out, tb.Nx, reinterpret_cast<const float2*>(tb.tw_t32), reinterpret_cast<const float2*>(tb.gpow32),
+        reinterpret_cast<const float2*>(tb.gipw32), reinterpret_cast<const float2*>(tb.ak32),
+        reinterpret_cast<const float*>(tb.lamtau32), cnorm, (float)tb.rho_h, (float)tb.rho_hinv, delta_rhs, n0_only);
+    return cudaGetLastError();
+}
+
 static int tile_lw(int lp, int tile = TILE_ELEMS) {
     int lw = 0;
     while (((1 << lp) << (lw + 1)) <= tile) ++lw;
@@ -267,6 +414,17 @@ cudaError_t launch_time_solve(const R* in, R* out, const Tables& tb, double cnor
     const bool f64 = std::is_same<R, double>::value;
     auto pick = [f64](const void* a, const void* b) { return reinterpret_cast<const cplx<R>*>(f64 ? a : b); };
     const R* lt = reinterpret_cast<const R*>(f64 ? (const void*)tb.lamtau : (const void*)tb.lamtau32);
+    if (std::is_same<R, float>::value) {
+        const float* fin = reinterpret_cast<const float*>(in);
+        float* fout = reinterpret_cast<float*>(out);
+        switch (lh) {
+            case 5: return launch_time_solve_reg<5>(fin, fout, tb, (float)cnorm, delta_rhs, n0_only, s);
+            case 6: return launch_time_solve_reg<6>(fin, fout, tb, (float)cnorm, delta_rhs, n0_only, s);
+            case 7: return launch_time_solve_reg<7>(fin, fout, tb, (float)cnorm, delta_rhs, n0_only, s);
+            case 8: return launch_time_solve_reg<8>(fin, fout, tb, (float)cnorm, delta_rhs, n0_only, s);
+            default: break;
+        }
+    }
 #define QBVM_TS_CT(LHV)                                                                                        \
     case LHV: {                                                                                                \
         auto kern = k_time_solve_ct<R, MB, LHV>;                                                               \
