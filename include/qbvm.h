@@ -129,8 +129,12 @@ int qbvm_plan(const qbvm_desc* desc, qbvm_plan_t** out);
  * eq. 3.8.  `g_or_F` is g (one level, rhs_kind DELTA) or F (nt levels,
  * rhs_kind GENERAL); `y` receives all nt levels, or only y^0 (the first
  * level, n_z*n_y*n_x values) when n0_only != 0.  In and out may alias for
- * rhs_kind GENERAL.  Errors: BAD_ARG (NULL arguments, mixed host/device),
- * DIVERGED (FP32_REFINE only; y holds the last iterate), CUDA. */
+ * rhs_kind GENERAL (FP32_REFINE then copies F into plan memory first, since
+ * the refinement re-reads it).  FP32_REFINE solves data whose root-mean-square
+ * magnitude lies outside [1e-18, 1e28] (where FP32 cannot carry the residuals)
+ * with the FP64 pipeline; last_refine_iters is then 0.  Errors: BAD_ARG (NULL
+ * arguments, mixed host/device), DIVERGED (FP32_REFINE only; y holds the last
+ * iterate), NONFINITE, CUDA. */
 int qbvm_solve(qbvm_plan_t* plan, const double* g_or_F, double* y, int n0_only, void* stream);
 
 /* qbvm_residual -- the relative all-at-once residual ||f - A y||_2 / ||f||_2

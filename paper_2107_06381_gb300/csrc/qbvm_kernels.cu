@@ -764,6 +764,179 @@ k_residual_df(const float2* __restrict__ y, const double* __restrict__ f, int de
     }
 }
 
+// Sum of squares in FP32 with a power-of-two scale that follows the largest
+// magnitude seen (sum = ssq * 4^e, every term scaled by 2^-e first), so that
+// neither tiny nor huge data underflow or overflow; rescaling is exact.
+struct ScaledSsq {
+    float ssq = 0.f, inv = 0x1p100f, lim = 0x1p-99f;
+    int e = -100;
+    // 2^k as an FP32 for -126 <= k <= 127
+    static __device__ __forceinline__ float p2(int k) { return __uint_as_float((unsigned)(127 + k) << 23); }
+    __device__ __forceinline__ void add(float x) {
+        const float a = fabsf(x);
+        if (a >= lim) {                                   // a is normal: lim >= 2^-99
+            const int ne = (int)((__float_as_uint(a) >> 23) & 0xFF) - 127;
+            const int d = 2 * (e - ne);                  // < 0
+            ssq = d >= -126 ? ssq * p2(d) : 0.f;         // terms below 2^-126 of the new scale vanish
+            e = ne;
+            inv = ne <= 126 ? p2(-ne) : 0x1p-127f;
+            lim = ne <= 126 ? p2(ne + 1) : __uint_as_float(0x7F800000u);
+        }
+        const float xs = x * inv;
+        ssq = fmaf(xs, xs, ssq);
+    }
+    __device__ __forceinline__ double value() const {
+        return (double)ssq * __longlong_as_double((long long)(1023 + 2 * e) << 52);
+    }
+};
+
+// The same residual, four consecutive unknowns of the flattened [nt][nz][ny][nx]
+// array per thread: the iterate, f and r move as 16-byte vectors, the x
+// neighbours across a group boundary come from the adjacent lanes, and the
+// (t, z, y, x) position is advanced incrementally (no divisions in the loop).
+// Requires 16-byte aligned y, f and r_out.
+template <bool EQ, int DIMS>
+__global__ void __launch_bounds__(RES_THREADS)
+k_residual_df4(const float2* __restrict__ y, const double* __restrict__ f, int delta_rhs, int nt, int nx, int ny,
+               int nz, DfCoef k, double f0_scale, float* __restrict__ r_out, double* partials) {
+    __shared__ double sh[32];
+    const long long Nx = (long long)nx * ny * nz, N = (long long)nt * Nx, pl = (long long)nx * ny;
+    const long long ngroups = (N + 3) >> 2;
+    const int lane = threadIdx.x & 31;
+    const long long wid = ((long long)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+    const long long nw = ((long long)gridDim.x * blockDim.x) >> 5;
+    auto split = [&](long long i, int& t, int& z, int& yy, int& x) {
+        t = (int)(i / Nx);
+        long long r = i - (long long)t * Nx;
+        z = (int)(r / pl);
+        r -= (long long)z * pl;
+        yy = (int)(r / nx);
+        x = (int)(r - (long long)yy * nx);
+    };
+    int t, iz, iy, ix, St, Sz, Sy, Sx;
+    split((wid * 32 + lane) * 4, t, iz, iy, ix);
+    split(nw * 128, St, Sz, Sy, Sx);
+    auto ld = [&](long long i) { float2 v = y[i]; return dfloat{v.x, v.y}; };
+    const float4* y4 = reinterpret_cast<const float4*>(y);
+    const double2* f2 = reinterpret_cast<const double2*>(f);
+    ScaledSsq nr, nf;
+    for (long long gb = wid * 32; gb < ngroups; gb += nw * 32) {
+        const long long g = gb + lane, i0 = 4 * g;
+        const bool act = g < ngroups, full = act && i0 + 3 < N;
+        dfloat yv[4];
+        if (full) {
+            const float4 a = y4[2 * g], b = y4[2 * g + 1];
+            yv[0] = {a.x, a.y};
+            yv[1] = {a.z, a.w};
+            yv[2] = {b.x, b.y};
+            yv[3] = {b.z, b.w};
+        } else {
+#pragma unroll
+            for (int e = 0; e < 4; ++e) yv[e] = (act && i0 + e < N) ? ld(i0 + e) : dfloat{0.f, 0.f};
+        }
+        double fd[4] = {0.0, 0.0, 0.0, 0.0};
+        if (!delta_rhs) {
+            if (full) {
+                const double2 a = f2[2 * g], b = f2[2 * g + 1];
+                fd[0] = a.x;
+                fd[1] = a.y;
+                fd[2] = b.x;
+                fd[3] = b.y;
+            } else {
+#pragma unroll
+                for (int e = 0; e < 4; ++e)
+                    if (act && i0 + e < N) fd[e] = f[i0 + e];
+            }
+        }
+        // x neighbours of the group's first and last element
+        dfloat xl = {__shfl_up_sync(0xffffffffu, yv[3].hi, 1), __shfl_up_sync(0xffffffffu, yv[3].lo, 1)};
+        dfloat xr = {__shfl_down_sync(0xffffffffu, yv[0].hi, 1), __shfl_down_sync(0xffffffffu, yv[0].lo, 1)};
+        if (lane == 0) xl = (act && i0 >= 1) ? ld(i0 - 1) : dfloat{0.f, 0.f};
+        if (lane == 31) xr = (act && i0 + 4 < N) ? ld(i0 + 4) : dfloat{0.f, 0.f};
+        float rv[4];
+        int et = t, ez = iz, ey = iy, ex = ix;
+#pragma unroll
+        for (int e = 0; e < 4; ++e) {
+            if (e > 0 && ++ex == nx) {
+                ex = 0;
+                if (++ey == ny) {
+                    ey = 0;
+                    if (++ez == nz) {
+                        ez = 0;
+                        ++et;
+                    }
+                }
+            }
+            const long long idx = i0 + e;
+            rv[e] = 0.f;
+            if (!(act && idx < N)) continue;
+            const dfloat yc = yv[e];
+            const dfloat pv = et > 0 ? ld(idx - Nx) : df_mul(k.omega, ld(idx + (long long)(nt - 1) * Nx));
+            dfloat Ay = df_mul(k.ct, df_add_sloppy(yc, df_neg(pv)));
+            const dfloat L = e > 0 ? yv[e - 1] : xl, R = e < 3 ? yv[e + 1] : xr;
+            dfloat sx = ex > 0 ? L : dfloat{0.f, 0.f};
+            if (ex < nx - 1) sx = df_add_sloppy(sx, R);
+            dfloat sy = {0.f, 0.f}, sz = {0.f, 0.f};
+            if (DIMS >= 2) {
+                if (ey > 0) sy = ld(idx - nx);
+                if (ey < ny - 1) sy = df_add_sloppy(sy, ld(idx + nx));
+            }
+            if (DIMS >= 3) {
+                if (ez > 0) sz = ld(idx - pl);
+                if (ez < nz - 1) sz = df_add_sloppy(sz, ld(idx + pl));
+            }
+            if (EQ) {
+                dfloat S = sx;
+                if (DIMS >= 2) S = df_add_sloppy(S, sy);
+                if (DIMS >= 3) S = df_add_sloppy(S, sz);
+                // 2 d y: scalings by 2 and 4 are exact; 6 y = 4 y + 2 y in double-float
+                const dfloat my = DIMS == 3 ? df_add_sloppy(dfloat{4.f * yc.hi, 4.f * yc.lo}, dfloat{2.f * yc.hi, 2.f * yc.lo})
+                                            : dfloat{2.f * DIMS * yc.hi, 2.f * DIMS * yc.lo};
+                Ay = df_add_sloppy(Ay, df_mul(k.cx, df_add_sloppy(my, df_neg(S))));
+            } else {
+                const dfloat y2 = {2.f * yc.hi, 2.f * yc.lo};
+                Ay = df_add_sloppy(Ay, df_mul(k.cx, df_add_sloppy(y2, df_neg(sx))));
+                if (DIMS >= 2) Ay = df_add_sloppy(Ay, df_mul(k.cy, df_add_sloppy(y2, df_neg(sy))));
+                if (DIMS >= 3) Ay = df_add_sloppy(Ay, df_mul(k.cz, df_add_sloppy(y2, df_neg(sz))));
+            }
+            dfloat fv = {0.f, 0.f};
+            if (delta_rhs) {
+                if (et == 0) fv = df_from_double(f0_scale * f[((long long)ez * ny + ey) * nx + ex]);
+            } else {
+                fv = df_from_double(fd[e]);
+            }
+            const dfloat r = df_add_sloppy(fv, df_neg(Ay));
+            rv[e] = r.hi;
+            nr.add(r.hi);
+            nf.add(fv.hi);
+        }
+        if (full) {
+            reinterpret_cast<float4*>(r_out)[g] = make_float4(rv[0], rv[1], rv[2], rv[3]);
+        } else if (act) {
+#pragma unroll
+            for (int e = 0; e < 4; ++e)
+                if (i0 + e < N) r_out[i0 + e] = rv[e];
+        }
+        // advance (t, z, y, x) by the grid stride (each component wraps at most once)
+        ix += Sx;
+        int c = ix >= nx;
+        if (c) ix -= nx;
+        iy += Sy + c;
+        c = iy >= ny;
+        if (c) iy -= ny;
+        iz += Sz + c;
+        c = iz >= nz;
+        if (c) iz -= nz;
+        t += St + c;
+    }
+    double a = block_sum(nr.value(), sh);
+    double b = block_sum(nf.value(), sh);
+    if (threadIdx.x == 0) {
+        partials[2 * blockIdx.x] = a;
+        partials[2 * blockIdx.x + 1] = b;
+    }
+}
+
 // In place: a double-float array (8 bytes per value) becomes the FP64 array.
 __global__ void k_df_to_double(void* buf, long long n) {
     const float2* src = reinterpret_cast<const float2*>(buf);
@@ -790,6 +963,27 @@ cudaError_t launch_residual_df(const void* y_df, const double* f, int delta_rhs,
     k.cy = df_const(h2inv[1]);
     k.cz = df_const(h2inv[2]);
     const bool eq = (tb.dim < 2 || h2inv[1] == h2inv[0]) && (tb.dim < 3 || h2inv[2] == h2inv[0]);
+    const bool aligned = ((reinterpret_cast<uintptr_t>(y_df) | reinterpret_cast<uintptr_t>(f) |
+                           reinterpret_cast<uintptr_t>(r_out)) & 15) == 0;
+    if (aligned && (tb.dim == 2 || tb.dim == 3)) {
+        const long long groups = ((long long)tb.nt * tb.Nx + 3) / 4;
+        long long nb = (groups + RES_THREADS - 1) / RES_THREADS;
+        if (nb > nblocks) nb = nblocks;
+        const float2* yy = reinterpret_cast<const float2*>(y_df);
+        const double fs = -tb.omega * it;
+        const int nx = tb.n[0], ny = tb.n[1], nz = tb.n[2];
+        if (tb.dim == 2) {
+            if (eq) k_residual_df4<true, 2><<<(unsigned)nb, RES_THREADS, 0, s>>>(yy, f, delta_rhs, tb.nt, nx, ny, nz, k, fs, r_out, partials);
+            else k_residual_df4<false, 2><<<(unsigned)nb, RES_THREADS, 0, s>>>(yy, f, delta_rhs, tb.nt, nx, ny, nz, k, fs, r_out, partials);
+        } else {
+            if (eq) k_residual_df4<true, 3><<<(unsigned)nb, RES_THREADS, 0, s>>>(yy, f, delta_rhs, tb.nt, nx, ny, nz, k, fs, r_out, partials);
+            else k_residual_df4<false, 3><<<(unsigned)nb, RES_THREADS, 0, s>>>(yy, f, delta_rhs, tb.nt, nx, ny, nz, k, fs, r_out, partials);
+        }
+        cudaError_t e = cudaGetLastError();
+        if (e != cudaSuccess) return e;
+        k_reduce_pairs<<<1, 1024, 0, s>>>(partials, (int)nb, sums);
+        return cudaGetLastError();
+    }
     if (eq)
         k_residual_df<true><<<nblocks, RES_THREADS, 0, s>>>(reinterpret_cast<const float2*>(y_df), f, delta_rhs, tb.nt,
                                                             tb.n[0], tb.n[1], tb.n[2], k, -tb.omega * it, r_out,

@@ -36,6 +36,7 @@ struct qbvm_plan {
     double* stage_out = nullptr;
     // FP32 refinement workspace
     float* f32 = nullptr;         // [nt][Nx] FP32 work array (and the residual's r.hi)
+    double* fcopy = nullptr;      // FP32_REFINE: copy of an F that aliases y
     float* g32 = nullptr;         // Nx FP32 (delta rhs)
     long long ws_bytes = 0;
     int last_iters = 0;
@@ -274,15 +275,22 @@ int fp32_solve(qbvm_plan_t* p, const void* rhs, int rhs_fp64, int delta, void* y
     return QBVM_OK;
 }
 
-int residual_norm_df(qbvm_plan_t* p, const void* ydf, const double* in, int delta, double* rel, cudaStream_t s) {
+int residual_norm_df(qbvm_plan_t* p, const void* ydf, const double* in, int delta, double* rel, double* fnorm2,
+                     cudaStream_t s) {
     { Span sp_(p, "residual_df", s); CK(qbvm::launch_residual_df(ydf, in, delta, p->tb, p->h2inv, p->f32, p->partials, p->nres, p->sums, s)); }
     double h[2] = {0, 0};
     CK(cudaMemcpyAsync(h, p->sums, sizeof(h), cudaMemcpyDeviceToHost, s));
     CK(cudaStreamSynchronize(s));
     if (!std::isfinite(h[0]) || !std::isfinite(h[1])) return QBVM_ERR_NONFINITE;
     *rel = h[1] > 0 ? std::sqrt(h[0] / h[1]) : std::sqrt(h[0]);
+    *fnorm2 = h[1];
     return QBVM_OK;
 }
+
+// FP32 holds the right-hand side and the residuals of the refinement only for
+// data of moderate magnitude; outside [FP32_RMS_LO, FP32_RMS_HI] (root mean
+// square of f over its nonzero-capable entries) the plan's FP64 pipeline solves.
+constexpr double FP32_RMS_LO = 1e-18, FP32_RMS_HI = 1e28;
 
 int solve_fp32r_dev(qbvm_plan_t* p, const double* in, double* y, int n0_only, cudaStream_t s) {
     const Tables& tb = p->tb;
@@ -297,10 +305,30 @@ int solve_fp32r_dev(qbvm_plan_t* p, const double* in, double* y, int n0_only, cu
     double rel = 0.0, prev = INFINITY;
     int it = 0;
     int status = QBVM_OK;
+    bool first = true;
     for (;;) {
-        rc = residual_norm_df(p, yfull, in, delta, &rel, s);     // r.hi lands in p->f32
+        double fn2 = 0.0;
+        rc = residual_norm_df(p, yfull, in, delta, &rel, &fn2, s);     // r.hi lands in p->f32
         launches += 2;
-        if (rc) return rc;
+        if (rc && !(first && rc == QBVM_ERR_NONFINITE)) return rc;
+        if (first) {
+            first = false;
+            const double cnt = (double)tb.Nx * (delta ? 1 : tb.nt);
+            const double rms = std::sqrt(fn2 / cnt);
+            if (rc == QBVM_ERR_NONFINITE || (rms > 0 && (rms < FP32_RMS_LO || rms > FP32_RMS_HI))) {
+                rc = solve_fp64_dev(p, in, y, n0_only, s);     // wreal exists for n0_only (solve_dev)
+                if (rc) return rc;
+                double r64 = 0.0;
+                if (!n0_only) {
+                    rc = qbvm_residual(p, y, in, &r64, s);
+                    if (rc) return rc;
+                }
+                p->last_iters = 0;
+                p->last_relres = n0_only ? NAN : r64;
+                p->kernels_per_solve = launches + p->kernels_per_solve;
+                return QBVM_OK;
+            }
+        }
         if (rel <= tol) break;
         if (rel > 0.5 * prev) {
             // no contraction: the double-float floor if the residual is already tiny,
@@ -575,6 +603,19 @@ static int solve_dev(qbvm_plan_t* p, const double* in, double* y, int n0_only, c
     if (p->tb.dim == 1) return QBVM_ERR_UNSUPPORTED;
     int rc = ensure_fp32(p);
     if (rc) return rc;
+    if (p->d.rhs_kind == QBVM_RHS_GENERAL) {
+        // the refinement re-reads F after y has been written: an F that overlaps
+        // y is copied first (the FP64 path is alias-safe as it stands)
+        const size_t total = (size_t)p->tb.Nx * p->tb.nt;
+        const char *a = reinterpret_cast<const char*>(in), *b = reinterpret_cast<const char*>(y);
+        const size_t na = total * sizeof(double), nb = (n0_only ? (size_t)p->tb.Nx : total) * sizeof(double);
+        if (a < b + nb && b < a + na) {
+            if (!p->fcopy) rc = dalloc(p, &p->fcopy, total);
+            if (rc) return rc;
+            CK(cudaMemcpyAsync(p->fcopy, in, na, cudaMemcpyDeviceToDevice, s));
+            in = p->fcopy;
+        }
+    }
     return solve_fp32r_dev(p, in, y, n0_only, s);
 }
 

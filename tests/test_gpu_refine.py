@@ -88,6 +88,36 @@ def test_fp32_solve_alone_is_fp32_accurate(grid):
     assert rel <= 1e-2
 
 
+def test_refined_inplace_general_rhs():
+    """F and y in one buffer: the refinement, which re-reads F after y is
+    written, gives the out-of-place answer bit for bit."""
+    grid = bi.Grid(2, (64, 32), 1.0, 0.1, 16)
+    F = bi.random_general_rhs(grid, seed=36)
+    want, _, _ = refine_solve(grid, Q.FORM_PQ, 1e-3, F, Q.RHS_GENERAL)
+    with Q.Plan(2, grid.M, grid.L, grid.T, grid.nt, Q.FORM_PQ, 1e-3, 0.0, Q.FP32_REFINE, Q.RHS_GENERAL) as plan:
+        buf = torch.as_tensor(F.ravel(), dtype=torch.float64).cuda()
+        plan.solve(buf, buf)
+        torch.cuda.synchronize()
+        np.testing.assert_array_equal(buf.cpu().numpy().reshape(grid.full_shape), want)
+
+
+@pytest.mark.parametrize("scale", [1e-30, 1e-12, 1e12, 1e30])
+def test_refinement_at_extreme_data_scales(scale):
+    """The solve is linear: data scaled by 1e+-12 stay on the FP32 path and
+    give the scaled answer; at 1e+-30 FP32 cannot hold the residuals and the
+    plan solves in FP64 (no refinement steps) -- the answer is right either way."""
+    grid = bi.Grid(2, (64, 64), 1.0, 0.1, 32)
+    g = bi.random_general_rhs(grid, seed=37)[0]
+    alpha = 1e-3
+    want = O.solve_spectral(grid, Q.FORM_PQ, alpha, O.delta_rhs(grid, Q.FORM_PQ, alpha, g))
+    got, iters, rel = refine_solve(grid, Q.FORM_PQ, alpha, g * scale, Q.RHS_DELTA)
+    assert O.rel_l2(got / scale, want) <= TOL
+    if abs(np.log10(scale)) < 20:
+        assert iters >= 1
+    else:
+        assert iters == 0 and rel <= 1e-13
+
+
 def test_refined_n0_only():
     grid = bi.Grid(2, (32, 32), 1.0, 0.1, 32)
     F = bi.random_general_rhs(grid, seed=32)
