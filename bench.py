@@ -165,12 +165,13 @@ class ClockSampler:
 def _fft_ops(lm: int) -> float:
     """FP64 operations per complex element of the radix-4/2 Stockham FFT of
     length 2^lm: 4 per element in the first radix-4 pass (16 adds per
-    butterfly), 7 in later radix-4 passes (+3 complex twiddle products of 4
-    operations), 4 in the closing radix-2 pass (1 product + 2 complex adds)."""
+    butterfly), 6 in later radix-4 passes (four fused twiddle butterflies of 6
+    operations, with w3 = w1 w2 factored out), 3 in the closing radix-2 pass
+    (one fused twiddle butterfly)."""
     if lm == 0:
         return 0.0
     r4, r2 = lm // 2, lm % 2
-    return (4.0 + 7.0 * (r4 - 1) if r4 else 0.0) + 4.0 * r2
+    return (4.0 + 6.0 * (r4 - 1) if r4 else 0.0) + 3.0 * r2
 
 
 def kernel_model(name, grid, rhs):

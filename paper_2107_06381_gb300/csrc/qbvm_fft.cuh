@@ -55,6 +55,17 @@ template <int S, typename C> __device__ __forceinline__ C twiddle(const C* tw, i
     return w;
 }
 
+// a + w b and a - w b with fused multiply-adds (the difference as 2a - (a + w b)):
+// 6 operations instead of the 8 of a complex product and two complex sums.
+__device__ __forceinline__ void fma_bfly(double2 a, double2 b, double2 w, double2& p, double2& m) {
+    p = make_double2(fma(w.x, b.x, fma(-w.y, b.y, a.x)), fma(w.x, b.y, fma(w.y, b.x, a.y)));
+    m = make_double2(fma(2.0, a.x, -p.x), fma(2.0, a.y, -p.y));
+}
+__device__ __forceinline__ void fma_bfly(float2 a, float2 b, float2 w, float2& p, float2& m) {
+    p = make_float2(fmaf(w.x, b.x, fmaf(-w.y, b.y, a.x)), fmaf(w.x, b.y, fmaf(w.y, b.x, a.y)));
+    m = make_float2(fmaf(2.f, a.x, -p.x), fmaf(2.f, a.y, -p.y));
+}
+
 // Radix-4 DFT with kernel exp(S * 2 pi i / 4) in registers.
 template <int S, typename C> __device__ __forceinline__ void dft4(C& v0, C& v1, C& v2, C& v3) {
     C a0 = cadd(v0, v2), a1 = csub(v0, v2);
@@ -99,12 +110,18 @@ __device__ __forceinline__ void fft_tile(C* buf, const C* tw, int lp, int lw) {
                 int c = b & (W - 1), j = b >> lw;
                 int k = j & (Ns - 1);
                 if (Ns > 1) {
+                    // twiddled radix-4 with w3 = w1 w2 factored out:
+                    //   x0 +- w2 x2,  x1 +- w2 x3,  then (a0 +- w1 b0), (a1 +- S i w1 b1)
                     int step = P / (Ns * 4);        // exp(S 2 pi i k r/(4 Ns)) = tw^(k r step)
-                    v[i][1] = cmul(v[i][1], twiddle<S>(tw, k * step));
-                    v[i][2] = cmul(v[i][2], twiddle<S>(tw, 2 * k * step));
-                    v[i][3] = cmul(v[i][3], twiddle<S>(tw, 3 * k * step));
+                    const C w1 = twiddle<S>(tw, k * step), w2 = twiddle<S>(tw, 2 * k * step);
+                    C a0, a1, b0, b1;
+                    fma_bfly(v[i][0], v[i][2], w2, a0, a1);
+                    fma_bfly(v[i][1], v[i][3], w2, b0, b1);
+                    fma_bfly(a0, b0, w1, v[i][0], v[i][2]);
+                    fma_bfly(a1, b1, cmul_si<S>(w1), v[i][1], v[i][3]);
+                } else {
+                    dft4<S>(v[i][0], v[i][1], v[i][2], v[i][3]);
                 }
-                dft4<S>(v[i][0], v[i][1], v[i][2], v[i][3]);
                 int d = (j - k) * 4 + k;
 #pragma unroll
                 for (int r = 0; r < 4; ++r) buf[(d + r * Ns) * W + c] = v[i][r];
@@ -135,11 +152,16 @@ __device__ __forceinline__ void fft_tile(C* buf, const C* tw, int lp, int lw) {
                 int b = tid + i * nth;
                 int c = b & (W - 1), j = b >> lw;
                 int k = j & (Ns - 1);
-                C t = v[i][1];
-                if (Ns > 1) t = cmul(t, twiddle<S>(tw, k * (P / (Ns * 2))));
                 int d = (j - k) * 2 + k;
-                buf[d * W + c] = cadd(v[i][0], t);
-                buf[(d + Ns) * W + c] = csub(v[i][0], t);
+                C y0, y1;
+                if (Ns > 1) {
+                    fma_bfly(v[i][0], v[i][1], twiddle<S>(tw, k * (P / (Ns * 2))), y0, y1);
+                } else {
+                    y0 = cadd(v[i][0], v[i][1]);
+                    y1 = csub(v[i][0], v[i][1]);
+                }
+                buf[d * W + c] = y0;
+                buf[(d + Ns) * W + c] = y1;
             }
         }
         __syncthreads();
