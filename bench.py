@@ -178,22 +178,24 @@ def kernel_model(name, grid, rhs):
     """Algorithmic HBM bytes and FP64 operations (DADD, DMUL, DFMA count one each)
     of one launch of `name` in a full solve, from the kernels' arithmetic:
 
-    time_solve, per real element: 2.5 (omega-scaling) + 2 x FFT(nt/2)/2
-      + 8 (complex divide by d_k + tau Lambda) + 2.5 (unscaling).
-    dst (length M per real column), per real element: 3 (pair pre-processing)
-      + FFT(M)/2 + 2 (column separation) + 1 (prefix sum).
+    time_solve, per real element: 2 (omega-scaling, rho^H folded into the
+      table) + 2 x FFT(nt/2)/2 + 8 (complex divide by d_k + tau Lambda)
+      + 2 (unscaling).
+    dst (length M per real column; the FP64 passes compute 4x the DST), per
+      real element: 2 (pair pre-processing, one fused multiply-add each)
+      + FFT(M)/2 + 1 (column separation) + 1 (prefix sum).
     Bytes: each pass reads and writes every FP64 value once."""
     nt, Nx = grid.nt, grid.Nx
     if name == "time_solve":
         reads = Nx if rhs == "delta" else nt * Nx
         byts = 8 * (reads + nt * Nx)
-        ops = (2.5 + _fft_ops(int(math.log2(nt // 2))) + 8.0 + 2.5) * nt * Nx
+        ops = (2.0 + _fft_ops(int(math.log2(nt // 2))) + 8.0 + 2.0) * nt * Nx
         return byts, ops
     if name.startswith("dst_"):
         ax = "xyz".index(name[-1])
         M = grid.M[ax]
         byts = 16 * nt * Nx
-        ops = (3.0 + _fft_ops(int(math.log2(M))) / 2 + 2.0 + 1.0) * nt * Nx
+        ops = (2.0 + _fft_ops(int(math.log2(M))) / 2 + 1.0 + 1.0) * nt * Nx
         return byts, ops
     return None, None
 

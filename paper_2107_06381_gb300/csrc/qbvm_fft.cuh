@@ -55,6 +55,9 @@ template <int S, typename C> __device__ __forceinline__ C twiddle(const C* tw, i
     return w;
 }
 
+__device__ __forceinline__ double rfma(double a, double b, double c) { return fma(a, b, c); }
+__device__ __forceinline__ float rfma(float a, float b, float c) { return fmaf(a, b, c); }
+
 // a + w b and a - w b with fused multiply-adds (the difference as 2a - (a + w b)):
 // 6 operations instead of the 8 of a complex product and two complex sums.
 __device__ __forceinline__ void fma_bfly(double2 a, double2 b, double2 w, double2& p, double2& m) {

@@ -27,10 +27,14 @@ struct Tables {
     float*   sn_s32[3] = {nullptr, nullptr, nullptr};
     double2* gpow = nullptr;         // scale * gamma^t (t < H), gamma = omega^{1/nt} principal
     double2* gipw = nullptr;         // 2 gamma^{-t} (t < H)
+    double2* gpowr = nullptr;        // i rho^H gpow[t]: the second half's scaling, folded
+    double2* gipr = nullptr;         // rho^{-H} gipw[t]: the second half's unscaling, folded
     double2* ak = nullptr;           // d_{2m} = 1 - gamma theta^{2m}, m < H (eigenvalues of C_omega)
     double*  lamtau = nullptr;       // tau * Lambda_l for every spatial mode (2D/3D)
     float2*  gpow32 = nullptr;       // FP32 roundings of gpow, gipw, ak, lamtau
     float2*  gipw32 = nullptr;
+    float2*  gpowr32 = nullptr;
+    float2*  gipr32 = nullptr;
     float2*  ak32 = nullptr;
     float*   lamtau32 = nullptr;
     double2* bk = nullptr;           // 1D Thomas diagonal for frequency 2m: h^2 d_{2m} / tau + 2
@@ -41,7 +45,8 @@ struct Tables {
 // lm = log2(n + 1); tw = roots of length n+1, sn = sin(j pi/(n+1)) tables of
 // precision R.  TIN: element type read.  OMODE: 0 store R, 1 accumulate into
 // a double-float (float2 hi, lo) array, 2 store into a double-float array.
-template <typename R, typename TIN, int OMODE>
+// X4: the output is 4 times the DST (two operations fewer per element).
+template <typename R, typename TIN, int OMODE, bool X4 = false>
 cudaError_t launch_dst(const TIN* in, void* out, int n, int lm, long long outer, long long inner,
                        const void* tw, const void* sn, cudaStream_t s);
 

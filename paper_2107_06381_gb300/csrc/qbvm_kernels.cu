@@ -32,32 +32,33 @@ static cudaError_t set_smem(K kern, size_t smem) {
     return cudaFuncSetAttribute(kern, cudaFuncAttributePreferredSharedMemoryCarveout, 100);
 }
 
-template <typename R, typename TIN, int OMODE, int MAXB4>
+template <typename R, typename TIN, int OMODE, int MAXB4, bool X4>
 __global__ void __launch_bounds__(TILE_THREADS)
 k_dst(const TIN* in, void* out, int n, int lm, int lw, long long outer, long long inner,
       const cplx<R>* __restrict__ tw, const R* __restrict__ sn) {
     extern __shared__ __align__(16) unsigned char smem_raw[];
-    dst_tile<R, TIN, OMODE, MAXB4, false>(in, out, n, lm, lw, outer, inner, (long long)blockIdx.x, tw, sn, smem_raw);
+    dst_tile<R, TIN, OMODE, MAXB4, false, X4>(in, out, n, lm, lw, outer, inner, (long long)blockIdx.x, tw, sn,
+                                              smem_raw);
 }
 
 // The same tile with the transform length fixed at compile time (the tile
 // width follows from it), so that the whole pipeline inlines with constant
 // sizes; used for the common lengths M = 64 ... 512.
-template <typename R, typename TIN, int OMODE, int LM>
+template <typename R, typename TIN, int OMODE, int LM, bool X4>
 __global__ void __launch_bounds__(TILE_THREADS)
 k_dst_ct(const TIN* in, void* out, long long outer, long long inner, const cplx<R>* __restrict__ tw,
          const R* __restrict__ sn) {
     extern __shared__ __align__(16) unsigned char smem_raw[];
     constexpr int LW = 11 - LM;                     // 2^LM * 2^LW = DST_TILE complex values
     static_assert((1 << (LM + LW)) == DST_TILE, "DST tile size");
-    dst_tile<R, TIN, OMODE, DST_TILE / 4 / TILE_THREADS, false>(in, out, (1 << LM) - 1, LM, LW, outer, inner,
-                                                                (long long)blockIdx.x, tw, sn, smem_raw);
+    dst_tile<R, TIN, OMODE, DST_TILE / 4 / TILE_THREADS, false, X4>(in, out, (1 << LM) - 1, LM, LW, outer, inner,
+                                                                    (long long)blockIdx.x, tw, sn, smem_raw);
 }
 
-template <typename R, typename TIN, int OMODE, int LM>
+template <typename R, typename TIN, int OMODE, int LM, bool X4>
 static cudaError_t launch_dst_ct(const TIN* in, void* out, long long outer, long long inner, const void* tw,
                                  const void* sn, long long blocks, size_t smem, cudaStream_t s) {
-    auto kern = k_dst_ct<R, TIN, OMODE, LM>;
+    auto kern = k_dst_ct<R, TIN, OMODE, LM, X4>;
     cudaError_t e = set_smem(kern, smem);
     if (e != cudaSuccess) return e;
     kern<<<(unsigned)blocks, TILE_THREADS, smem, s>>>(in, out, outer, inner, reinterpret_cast<const cplx<R>*>(tw),
@@ -108,7 +109,7 @@ template size_t dst_smem_bytes<double>(int);
 template size_t dst_smem_bytes<float>(int);
 int dst_tile_lw(int lm) { return dst_lw(lm); }
 
-template <typename R, typename TIN, int OMODE>
+template <typename R, typename TIN, int OMODE, bool X4>
 cudaError_t launch_dst(const TIN* in, void* out, int n, int lm, long long outer, long long inner,
                        const void* tw, const void* sn, cudaStream_t s) {
     const int lw = dst_lw(lm), W = 1 << lw;
@@ -116,18 +117,18 @@ cudaError_t launch_dst(const TIN* in, void* out, int n, int lm, long long outer,
     if (inner == 1) blocks = (outer + 2 * W - 1) / (2 * W);
     else blocks = outer * ((inner + 2 * W - 1) / (2 * W));
     size_t smem = dst_smem<R>(lm);
-    if (std::is_same<R, float>::value && n == (1 << lm) - 1 && lm >= 6 && lm <= 8)
+    if (std::is_same<R, float>::value && !X4 && n == (1 << lm) - 1 && lm >= 6 && lm <= 8)
         return launch_dst_reg_any<TIN, OMODE>(in, out, lm, outer, inner, tw, sn, s);
     if (n == (1 << lm) - 1) {
         switch (lm) {
-            case 6: return launch_dst_ct<R, TIN, OMODE, 6>(in, out, outer, inner, tw, sn, blocks, smem, s);
-            case 7: return launch_dst_ct<R, TIN, OMODE, 7>(in, out, outer, inner, tw, sn, blocks, smem, s);
-            case 8: return launch_dst_ct<R, TIN, OMODE, 8>(in, out, outer, inner, tw, sn, blocks, smem, s);
-            case 9: return launch_dst_ct<R, TIN, OMODE, 9>(in, out, outer, inner, tw, sn, blocks, smem, s);
+            case 6: return launch_dst_ct<R, TIN, OMODE, 6, X4>(in, out, outer, inner, tw, sn, blocks, smem, s);
+            case 7: return launch_dst_ct<R, TIN, OMODE, 7, X4>(in, out, outer, inner, tw, sn, blocks, smem, s);
+            case 8: return launch_dst_ct<R, TIN, OMODE, 8, X4>(in, out, outer, inner, tw, sn, blocks, smem, s);
+            case 9: return launch_dst_ct<R, TIN, OMODE, 9, X4>(in, out, outer, inner, tw, sn, blocks, smem, s);
             default: break;
         }
     }
-    auto kern = k_dst<R, TIN, OMODE, DST_TILE / 4 / TILE_THREADS>;
+    auto kern = k_dst<R, TIN, OMODE, DST_TILE / 4 / TILE_THREADS, X4>;
     cudaError_t e = set_smem(kern, smem);
     if (e != cudaSuccess) return e;
     kern<<<(unsigned)blocks, TILE_THREADS, smem, s>>>(in, out, n, lm, lw, outer, inner,
@@ -136,14 +137,14 @@ cudaError_t launch_dst(const TIN* in, void* out, int n, int lm, long long outer,
     return cudaGetLastError();
 }
 
-#define QBVM_DST_INST(R, TIN, OM)                                                                       \
-    template cudaError_t launch_dst<R, TIN, OM>(const TIN*, void*, int, int, long long, long long,     \
-                                                const void*, const void*, cudaStream_t);
-QBVM_DST_INST(double, double, 0)
-QBVM_DST_INST(float, float, 0)
-QBVM_DST_INST(float, double, 0)
-QBVM_DST_INST(float, float, 1)
-QBVM_DST_INST(float, float, 2)
+#define QBVM_DST_INST(R, TIN, OM, X4)                                                                   \
+    template cudaError_t launch_dst<R, TIN, OM, X4>(const TIN*, void*, int, int, long long, long long, \
+                                                    const void*, const void*, cudaStream_t);
+QBVM_DST_INST(double, double, 0, true)
+QBVM_DST_INST(float, float, 0, false)
+QBVM_DST_INST(float, double, 0, false)
+QBVM_DST_INST(float, float, 1, false)
+QBVM_DST_INST(float, float, 2, false)
 #undef QBVM_DST_INST
 
 // --------------------------------------------------------- time solve (2D/3D)
@@ -161,11 +162,14 @@ QBVM_DST_INST(float, float, 2)
 // cnorm carries tau, 1/nt and the inverse-DST normalisation.
 // The scaling, divide and unscaling use tables of the transform's precision
 // (the FP32 tables are the FP64 ones rounded once on the host).
+// gpowr = i rho^H gpow and gipr = rho^{-H} gipw fold the second half's factors
+// into the tables (one operation fewer per element on each side).
 template <typename R, int MAXB4>
 __device__ __forceinline__ void time_solve_tile(const R* in, R* out, long long Nx, int lh, int lw,
                                                 const cplx<R>* __restrict__ tw, const cplx<R>* __restrict__ gpow,
                                                 const cplx<R>* __restrict__ gipw, const cplx<R>* __restrict__ ak,
-                                                const R* __restrict__ lamtau, R cnorm, R rho_h, R rho_hinv,
+                                                const R* __restrict__ lamtau, R cnorm,
+                                                const cplx<R>* __restrict__ gpowr, const cplx<R>* __restrict__ gipr,
                                                 int delta_rhs, int n0_only, unsigned char* smem_raw) {
     using C = cplx<R>;
     const int H = 1 << lh, W = 1 << lw;
@@ -184,11 +188,11 @@ __device__ __forceinline__ void time_solve_tile(const R* in, R* out, long long N
                 if (t == 0) f0 = in[l];
             } else {
                 f0 = in[(long long)t * Nx + l];
-                f1 = rho_h * in[(long long)(t + H) * Nx + l];
+                f1 = in[(long long)(t + H) * Nx + l];
             }
         }
-        C g = gpow[t];
-        buf[e] = mkc(g.x * f0 - g.y * f1, g.y * f0 + g.x * f1);
+        const C g = gpow[t], gr = gpowr[t];          // gamma^t f0 + i rho^H gamma^t f1
+        buf[e] = mkc(rfma(g.x, f0, gr.x * f1), rfma(g.y, f0, gr.y * f1));
     }
     __syncthreads();
     fft_tile<+1, MAXB4>(buf, stw, lh, lw);
@@ -211,10 +215,13 @@ __device__ __forceinline__ void time_solve_tile(const R* in, R* out, long long N
         int t = e >> lw, c = e & (W - 1);
         long long l = l0 + c;
         if (l < Nx) {
-            C gi = gipw[t];
-            C w = buf[e];
-            out[(long long)t * Nx + l] = gi.x * w.x - gi.y * w.y;
-            if (!n0_only) out[(long long)(t + H) * Nx + l] = rho_hinv * (gi.x * w.y + gi.y * w.x);
+            const C w = buf[e];
+            const C gi = gipw[t];
+            out[(long long)t * Nx + l] = rfma(gi.x, w.x, -gi.y * w.y);
+            if (!n0_only) {
+                const C gr = gipr[t];
+                out[(long long)(t + H) * Nx + l] = rfma(gr.x, w.y, gr.y * w.x);
+            }
         }
     }
 }
@@ -224,9 +231,9 @@ __global__ void __launch_bounds__(TILE_THREADS)
 k_time_solve(const R* in, R* out, long long Nx, int lh, int lw, const cplx<R>* __restrict__ tw,
              const cplx<R>* __restrict__ gpow, const cplx<R>* __restrict__ gipw,
              const cplx<R>* __restrict__ ak, const R* __restrict__ lamtau, R cnorm,
-             R rho_h, R rho_hinv, int delta_rhs, int n0_only) {
+             const cplx<R>* __restrict__ gpowr, const cplx<R>* __restrict__ gipr, int delta_rhs, int n0_only) {
     extern __shared__ __align__(16) unsigned char smem_raw[];
-    time_solve_tile<R, MAXB4>(in, out, Nx, lh, lw, tw, gpow, gipw, ak, lamtau, cnorm, rho_h, rho_hinv, delta_rhs,
+    time_solve_tile<R, MAXB4>(in, out, Nx, lh, lw, tw, gpow, gipw, ak, lamtau, cnorm, gpowr, gipr, delta_rhs,
                               n0_only, smem_raw);
 }
 
@@ -236,10 +243,10 @@ __global__ void __launch_bounds__(TILE_THREADS)
 k_time_solve_ct(const R* in, R* out, long long Nx, const cplx<R>* __restrict__ tw,
                 const cplx<R>* __restrict__ gpow, const cplx<R>* __restrict__ gipw,
                 const cplx<R>* __restrict__ ak, const R* __restrict__ lamtau, R cnorm,
-                R rho_h, R rho_hinv, int delta_rhs, int n0_only) {
+                const cplx<R>* __restrict__ gpowr, const cplx<R>* __restrict__ gipr, int delta_rhs, int n0_only) {
     extern __shared__ __align__(16) unsigned char smem_raw[];
     constexpr int LT = (MAXB4 == 4 ? 12 : MAXB4 == 2 ? 11 : 10);     // log2 of the tile size
-    time_solve_tile<R, MAXB4>(in, out, Nx, LH, LT - LH, tw, gpow, gipw, ak, lamtau, cnorm, rho_h, rho_hinv,
+    time_solve_tile<R, MAXB4>(in, out, Nx, LH, LT - LH, tw, gpow, gipw, ak, lamtau, cnorm, gpowr, gipr,
                               delta_rhs, n0_only, smem_raw);
 }
 
@@ -432,8 +439,9 @@ cudaError_t launch_time_solve(const R* in, R* out, const Tables& tb, double cnor
         if (e != cudaSuccess) return e;                                                                        \
         kern<<<(unsigned)blocks, TILE_THREADS, smem, s>>>(in, out, tb.Nx, pick(tb.tw_t, tb.tw_t32),            \
                                                           pick(tb.gpow, tb.gpow32), pick(tb.gipw, tb.gipw32),  \
-                                                          pick(tb.ak, tb.ak32), lt, R(cnorm), R(tb.rho_h),     \
-                                                          R(tb.rho_hinv), delta_rhs, n0_only);                 \
+                                                          pick(tb.ak, tb.ak32), lt, R(cnorm),                  \
+                                                          pick(tb.gpowr, tb.gpowr32), pick(tb.gipr, tb.gipr32), \
+                                                          delta_rhs, n0_only);                                 \
         return cudaGetLastError();                                                                             \
     }
     switch (lh) {
@@ -449,8 +457,8 @@ cudaError_t launch_time_solve(const R* in, R* out, const Tables& tb, double cnor
     if (e != cudaSuccess) return e;
     kern<<<(unsigned)blocks, TILE_THREADS, smem, s>>>(in, out, tb.Nx, lh, lw, pick(tb.tw_t, tb.tw_t32),
                                                       pick(tb.gpow, tb.gpow32), pick(tb.gipw, tb.gipw32),
-                                                      pick(tb.ak, tb.ak32), lt, R(cnorm), R(tb.rho_h),
-                                                      R(tb.rho_hinv), delta_rhs, n0_only);
+                                                      pick(tb.ak, tb.ak32), lt, R(cnorm), pick(tb.gpowr, tb.gpowr32),
+                                                      pick(tb.gipr, tb.gipr32), delta_rhs, n0_only);
     return cudaGetLastError();
 }
 

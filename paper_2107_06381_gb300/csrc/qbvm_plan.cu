@@ -192,14 +192,17 @@ int solve_fp64_dev(qbvm_plan_t* p, const double* in, double* y, int n0_only, cud
         double cn = 1.0;
         for (int i = 0; i < tb.dim; ++i) cn *= 2.0 / (tb.n[i] + 1);
         cn /= tb.nt;
+        // the FP64 DSTs produce 4x the transform (X4): 4^(2 dim) over the forward
+        // and inverse passes, an exact power of two
+        cn = std::ldexp(cn, -4 * tb.dim);
         double* work;
         if (delta) {
             // DST of g along x, y (, z) -> ghat, then the time solve reads level 0
-            { Span sp_(p, "dst_x", s); CK(qbvm::launch_dst<double, double, 0>(in, p->ghat, tb.n[0], p->lp[0], ny * nz, 1, tb.tw_s[0], tb.sn_s[0], s)); }
-            { Span sp_(p, "dst_y", s); CK(qbvm::launch_dst<double, double, 0>(p->ghat, p->ghat, tb.n[1], p->lp[1], nz, nx, tb.tw_s[1], tb.sn_s[1], s)); }
+            { Span sp_(p, "dst_x", s); CK(qbvm::launch_dst<double, double, 0, true>(in, p->ghat, tb.n[0], p->lp[0], ny * nz, 1, tb.tw_s[0], tb.sn_s[0], s)); }
+            { Span sp_(p, "dst_y", s); CK(qbvm::launch_dst<double, double, 0, true>(p->ghat, p->ghat, tb.n[1], p->lp[1], nz, nx, tb.tw_s[1], tb.sn_s[1], s)); }
             launches += 2;
             if (tb.dim == 3) {
-                { Span sp_(p, "dst_z", s); CK(qbvm::launch_dst<double, double, 0>(p->ghat, p->ghat, tb.n[2], p->lp[2], 1, nx * ny, tb.tw_s[2], tb.sn_s[2], s)); }
+                { Span sp_(p, "dst_z", s); CK(qbvm::launch_dst<double, double, 0, true>(p->ghat, p->ghat, tb.n[2], p->lp[2], 1, nx * ny, tb.tw_s[2], tb.sn_s[2], s)); }
                 ++launches;
             }
             // f^0 = -omega g / tau: fold -omega/tau into the time-solve constant
@@ -209,11 +212,11 @@ int solve_fp64_dev(qbvm_plan_t* p, const double* in, double* y, int n0_only, cud
         } else {
             work = n0_only ? p->wreal : y;
             const long long nt = tb.nt;
-            { Span sp_(p, "dst_x", s); CK(qbvm::launch_dst<double, double, 0>(in, work, tb.n[0], p->lp[0], nt * ny * nz, 1, tb.tw_s[0], tb.sn_s[0], s)); }
-            { Span sp_(p, "dst_y", s); CK(qbvm::launch_dst<double, double, 0>(work, work, tb.n[1], p->lp[1], nt * nz, nx, tb.tw_s[1], tb.sn_s[1], s)); }
+            { Span sp_(p, "dst_x", s); CK(qbvm::launch_dst<double, double, 0, true>(in, work, tb.n[0], p->lp[0], nt * ny * nz, 1, tb.tw_s[0], tb.sn_s[0], s)); }
+            { Span sp_(p, "dst_y", s); CK(qbvm::launch_dst<double, double, 0, true>(work, work, tb.n[1], p->lp[1], nt * nz, nx, tb.tw_s[1], tb.sn_s[1], s)); }
             launches += 2;
             if (tb.dim == 3) {
-                { Span sp_(p, "dst_z", s); CK(qbvm::launch_dst<double, double, 0>(work, work, tb.n[2], p->lp[2], nt, nx * ny, tb.tw_s[2], tb.sn_s[2], s)); }
+                { Span sp_(p, "dst_z", s); CK(qbvm::launch_dst<double, double, 0, true>(work, work, tb.n[2], p->lp[2], nt, nx * ny, tb.tw_s[2], tb.sn_s[2], s)); }
                 ++launches;
             }
             { Span sp_(p, "time_solve", s); CK(qbvm::launch_time_solve<double>(work, y, tb, tb.tau * cn, 0, n0_only, s)); }
@@ -221,11 +224,11 @@ int solve_fp64_dev(qbvm_plan_t* p, const double* in, double* y, int n0_only, cud
         }
         // inverse DST (the (2/M) factors are in the time-solve constant)
         const long long lev = n0_only ? 1 : tb.nt;
-        { Span sp_(p, "dst_x", s); CK(qbvm::launch_dst<double, double, 0>(y, y, tb.n[0], p->lp[0], lev * ny * nz, 1, tb.tw_s[0], tb.sn_s[0], s)); }
-        { Span sp_(p, "dst_y", s); CK(qbvm::launch_dst<double, double, 0>(y, y, tb.n[1], p->lp[1], lev * nz, nx, tb.tw_s[1], tb.sn_s[1], s)); }
+        { Span sp_(p, "dst_x", s); CK(qbvm::launch_dst<double, double, 0, true>(y, y, tb.n[0], p->lp[0], lev * ny * nz, 1, tb.tw_s[0], tb.sn_s[0], s)); }
+        { Span sp_(p, "dst_y", s); CK(qbvm::launch_dst<double, double, 0, true>(y, y, tb.n[1], p->lp[1], lev * nz, nx, tb.tw_s[1], tb.sn_s[1], s)); }
         launches += 2;
         if (tb.dim == 3) {
-            { Span sp_(p, "dst_z", s); CK(qbvm::launch_dst<double, double, 0>(y, y, tb.n[2], p->lp[2], lev, nx * ny, tb.tw_s[2], tb.sn_s[2], s)); }
+            { Span sp_(p, "dst_z", s); CK(qbvm::launch_dst<double, double, 0, true>(y, y, tb.n[2], p->lp[2], lev, nx * ny, tb.tw_s[2], tb.sn_s[2], s)); }
             ++launches;
         }
     }
@@ -418,7 +421,7 @@ int qbvm_plan(const qbvm_desc* desc, qbvm_plan_t** out) {
     const int nt = d.nt, H = nt / 2;
     const double mag = std::fabs(p->omega);
     // principal root of omega < 0: gamma = |omega|^{1/nt} exp(i pi/nt)
-    std::vector<double2> tw64, gpow(H), gipw(H), ak(H), bk;
+    std::vector<double2> tw64, gpow(H), gipw(H), gpowr(H), gipr(H), ak(H), bk;
     std::vector<float2> tw32;
     roots(H, tw64, tw32);
     const double scale1d = d.dim == 1 ? p->h[0] * p->h[0] / nt : 1.0;
@@ -428,6 +431,10 @@ int qbvm_plan(const qbvm_desc* desc, qbvm_plan_t** out) {
         gpow[t] = make_double2(scale1d * r * std::cos(a), scale1d * r * std::sin(a));
         double ri = 2.0 * std::pow(mag, -(double)t / nt);
         gipw[t] = make_double2(ri * std::cos(a), -ri * std::sin(a));
+        // with rho^H = |omega|^{1/2} folded in: i rho^H gamma^t and rho^{-H} 2 gamma^{-t}
+        double rr = std::pow(mag, (double)(t + H) / nt), rir = 2.0 * std::pow(mag, -(double)(t + H) / nt);
+        gpowr[t] = make_double2(-scale1d * rr * std::sin(a), scale1d * rr * std::cos(a));
+        gipr[t] = make_double2(rir * std::cos(a), -rir * std::sin(a));
     }
     tb.rho_h = std::sqrt(mag);
     tb.rho_hinv = 1.0 / tb.rho_h;
@@ -448,6 +455,10 @@ int qbvm_plan(const qbvm_desc* desc, qbvm_plan_t** out) {
     if (!rc) rc = upload(p, &tb.ak, ak);
     if (!rc) rc = upload(p, &tb.gpow32, to32(gpow));
     if (!rc) rc = upload(p, &tb.gipw32, to32(gipw));
+    if (!rc) rc = upload(p, &tb.gpowr, gpowr);
+    if (!rc) rc = upload(p, &tb.gipr, gipr);
+    if (!rc) rc = upload(p, &tb.gpowr32, to32(gpowr));
+    if (!rc) rc = upload(p, &tb.gipr32, to32(gipr));
     if (!rc) rc = upload(p, &tb.ak32, to32(ak));
     if (!rc && d.dim == 1) {
         bk.resize(H);
