@@ -42,7 +42,7 @@ UNIT = "unknowns/s"
 FP64_PEAK_TOPS = 152 * 2 * 2.07e9 / 1e12
 # DRAM bytes (read + write) per launch from one ncu capture of the current
 # kernels on this workload (profiles/); None once a kernel changes.
-PROFILED_TRAFFIC = {"time_solve": 133.826048e6 + 75.166208e6, "dst_x": 133.250048e6 + 85.027072e6}
+PROFILED_TRAFFIC = {}
 
 
 def _peaks():
@@ -179,8 +179,8 @@ def kernel_model(name, grid, rhs):
     of one launch of `name` in a full solve, from the kernels' arithmetic:
 
     time_solve, per real element: 2 (omega-scaling, rho^H folded into the
-      table) + 2 x FFT(nt/2)/2 + 8 (complex divide by d_k + tau Lambda)
-      + 2 (unscaling).
+      table) + 2 x FFT(nt/2)/2 + 2 (one complex product by the plan's table
+      cnorm / (d_k + tau Lambda_l), read as 8 more bytes) + 2 (unscaling).
     dst (length M per real column; the FP64 passes compute 4x the DST), per
       real element: 2 (pair pre-processing, one fused multiply-add each)
       + FFT(M)/2 + 1 (column separation) + 1 (prefix sum).
@@ -188,8 +188,8 @@ def kernel_model(name, grid, rhs):
     nt, Nx = grid.nt, grid.Nx
     if name == "time_solve":
         reads = Nx if rhs == "delta" else nt * Nx
-        byts = 8 * (reads + nt * Nx)
-        ops = (2.0 + _fft_ops(int(math.log2(nt // 2))) + 8.0 + 2.0) * nt * Nx
+        byts = 8 * (reads + nt * Nx) + 16 * (nt // 2) * Nx
+        ops = (2.0 + _fft_ops(int(math.log2(nt // 2))) + 2.0 + 2.0) * nt * Nx
         return byts, ops
     if name.startswith("dst_"):
         ax = "xyz".index(name[-1])

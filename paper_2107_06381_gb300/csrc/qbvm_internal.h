@@ -38,6 +38,7 @@ struct Tables {
     float2*  ak32 = nullptr;
     float*   lamtau32 = nullptr;
     double2* bk = nullptr;           // 1D Thomas diagonal for frequency 2m: h^2 d_{2m} / tau + 2
+    double2* qinv = nullptr;         // FP64 2D/3D: cnorm / (d_{2m} + tau Lambda_l), [H][Nx]
 };
 
 // DST-I (unnormalised, S_{jk} = sin(pi j k /(n+1))) along one axis of an
@@ -56,6 +57,10 @@ cudaError_t launch_dst(const TIN* in, void* out, int n, int lm, long long outer,
 template <typename R>
 cudaError_t launch_time_solve(const R* in, R* out, const Tables& tb, double cnorm, int delta_rhs,
                               int n0_only, cudaStream_t s);
+
+// tb.qinv[m][l] = cnorm / (d_{2m} + tau Lambda_l) (IEEE FP64 division), built
+// once per plan so that Step (b) of the FP64 time solve is one complex product.
+cudaError_t launch_make_qinv(const Tables& tb, double cnorm, double2* q, cudaStream_t s);
 
 // 1D time-first path (Section 3.3 order): forward time transform to complex
 // workspace, Thomas per frequency, inverse transform.

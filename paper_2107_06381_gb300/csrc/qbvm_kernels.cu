@@ -170,7 +170,8 @@ __device__ __forceinline__ void time_solve_tile(const R* in, R* out, long long N
                                                 const cplx<R>* __restrict__ gipw, const cplx<R>* __restrict__ ak,
                                                 const R* __restrict__ lamtau, R cnorm,
                                                 const cplx<R>* __restrict__ gpowr, const cplx<R>* __restrict__ gipr,
-                                                int delta_rhs, int n0_only, unsigned char* smem_raw) {
+                                                const cplx<R>* __restrict__ qinv, int delta_rhs, int n0_only,
+                                                unsigned char* smem_raw) {
     using C = cplx<R>;
     const int H = 1 << lh, W = 1 << lw;
     C* buf = reinterpret_cast<C*>(smem_raw);
@@ -197,15 +198,23 @@ __device__ __forceinline__ void time_solve_tile(const R* in, R* out, long long N
     __syncthreads();
     fft_tile<+1, MAXB4>(buf, stw, lh, lw);
 
-    for (int e = tid; e < (H << lw); e += nth) {
-        int k = e >> lw, c = e & (W - 1);
-        long long l = l0 + c;
-        R lt = l < Nx ? lamtau[l] : R(0);
-        C a = ak[k];
-        R zr = a.x + lt, zi = a.y;
-        R inv = cnorm / (zr * zr + zi * zi);
-        C u = buf[e];
-        buf[e] = mkc((u.x * zr + u.y * zi) * inv, (u.y * zr - u.x * zi) * inv);
+    if (qinv) {                                          // the plan's table of cnorm / (d_{2m} + tau Lambda_l)
+        for (int e = tid; e < (H << lw); e += nth) {
+            int k = e >> lw, c = e & (W - 1);
+            long long l = l0 + c;
+            if (l < Nx) buf[e] = cmul(buf[e], qinv[(long long)k * Nx + l]);
+        }
+    } else {
+        for (int e = tid; e < (H << lw); e += nth) {
+            int k = e >> lw, c = e & (W - 1);
+            long long l = l0 + c;
+            R lt = l < Nx ? lamtau[l] : R(0);
+            C a = ak[k];
+            R zr = a.x + lt, zi = a.y;
+            R inv = cnorm / (zr * zr + zi * zi);
+            C u = buf[e];
+            buf[e] = mkc((u.x * zr + u.y * zi) * inv, (u.y * zr - u.x * zi) * inv);
+        }
     }
     __syncthreads();
     fft_tile<-1, MAXB4>(buf, stw, lh, lw);
@@ -231,9 +240,10 @@ __global__ void __launch_bounds__(TILE_THREADS)
 k_time_solve(const R* in, R* out, long long Nx, int lh, int lw, const cplx<R>* __restrict__ tw,
              const cplx<R>* __restrict__ gpow, const cplx<R>* __restrict__ gipw,
              const cplx<R>* __restrict__ ak, const R* __restrict__ lamtau, R cnorm,
-             const cplx<R>* __restrict__ gpowr, const cplx<R>* __restrict__ gipr, int delta_rhs, int n0_only) {
+             const cplx<R>* __restrict__ gpowr, const cplx<R>* __restrict__ gipr, const cplx<R>* __restrict__ qinv,
+             int delta_rhs, int n0_only) {
     extern __shared__ __align__(16) unsigned char smem_raw[];
-    time_solve_tile<R, MAXB4>(in, out, Nx, lh, lw, tw, gpow, gipw, ak, lamtau, cnorm, gpowr, gipr, delta_rhs,
+    time_solve_tile<R, MAXB4>(in, out, Nx, lh, lw, tw, gpow, gipw, ak, lamtau, cnorm, gpowr, gipr, qinv, delta_rhs,
                               n0_only, smem_raw);
 }
 
@@ -243,10 +253,11 @@ __global__ void __launch_bounds__(TILE_THREADS)
 k_time_solve_ct(const R* in, R* out, long long Nx, const cplx<R>* __restrict__ tw,
                 const cplx<R>* __restrict__ gpow, const cplx<R>* __restrict__ gipw,
                 const cplx<R>* __restrict__ ak, const R* __restrict__ lamtau, R cnorm,
-                const cplx<R>* __restrict__ gpowr, const cplx<R>* __restrict__ gipr, int delta_rhs, int n0_only) {
+                const cplx<R>* __restrict__ gpowr, const cplx<R>* __restrict__ gipr,
+                const cplx<R>* __restrict__ qinv, int delta_rhs, int n0_only) {
     extern __shared__ __align__(16) unsigned char smem_raw[];
     constexpr int LT = (MAXB4 == 4 ? 12 : MAXB4 == 2 ? 11 : 10);     // log2 of the tile size
-    time_solve_tile<R, MAXB4>(in, out, Nx, LH, LT - LH, tw, gpow, gipw, ak, lamtau, cnorm, gpowr, gipr,
+    time_solve_tile<R, MAXB4>(in, out, Nx, LH, LT - LH, tw, gpow, gipw, ak, lamtau, cnorm, gpowr, gipr, qinv,
                               delta_rhs, n0_only, smem_raw);
 }
 
@@ -397,6 +408,25 @@ static cudaError_t launch_time_solve_reg(const float* in, float* out, const Tabl
     return cudaGetLastError();
 }
 
+__global__ void k_make_qinv(const double2* __restrict__ ak, const double* __restrict__ lamtau, double cnorm, int H,
+                            long long Nx, double2* __restrict__ q) {
+    const long long n = (long long)H * Nx;
+    for (long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (long long)gridDim.x * blockDim.x) {
+        const long long k = i / Nx, l = i - k * Nx;
+        const double zr = ak[k].x + lamtau[l], zi = ak[k].y;
+        const double inv = cnorm / (zr * zr + zi * zi);
+        q[i] = make_double2(zr * inv, -zi * inv);
+    }
+}
+
+cudaError_t launch_make_qinv(const Tables& tb, double cnorm, double2* q, cudaStream_t s) {
+    const long long n = (long long)(tb.nt / 2) * tb.Nx;
+    long long blocks = (n + 255) / 256;
+    if (blocks > 152 * 64) blocks = 152 * 64;
+    k_make_qinv<<<(unsigned)blocks, 256, 0, s>>>(tb.ak, tb.lamtau, cnorm, tb.nt / 2, tb.Nx, q);
+    return cudaGetLastError();
+}
+
 static int tile_lw(int lp, int tile = TILE_ELEMS) {
     int lw = 0;
     while (((1 << lp) << (lw + 1)) <= tile) ++lw;
@@ -421,6 +451,7 @@ cudaError_t launch_time_solve(const R* in, R* out, const Tables& tb, double cnor
     const bool f64 = std::is_same<R, double>::value;
     auto pick = [f64](const void* a, const void* b) { return reinterpret_cast<const cplx<R>*>(f64 ? a : b); };
     const R* lt = reinterpret_cast<const R*>(f64 ? (const void*)tb.lamtau : (const void*)tb.lamtau32);
+    const cplx<R>* qv = f64 ? reinterpret_cast<const cplx<R>*>(tb.qinv) : nullptr;
     if (std::is_same<R, float>::value) {
         const float* fin = reinterpret_cast<const float*>(in);
         float* fout = reinterpret_cast<float*>(out);
@@ -441,7 +472,7 @@ cudaError_t launch_time_solve(const R* in, R* out, const Tables& tb, double cnor
                                                           pick(tb.gpow, tb.gpow32), pick(tb.gipw, tb.gipw32),  \
                                                           pick(tb.ak, tb.ak32), lt, R(cnorm),                  \
                                                           pick(tb.gpowr, tb.gpowr32), pick(tb.gipr, tb.gipr32), \
-                                                          delta_rhs, n0_only);                                 \
+                                                          qv, delta_rhs, n0_only);                             \
         return cudaGetLastError();                                                                             \
     }
     switch (lh) {
@@ -458,7 +489,7 @@ cudaError_t launch_time_solve(const R* in, R* out, const Tables& tb, double cnor
     kern<<<(unsigned)blocks, TILE_THREADS, smem, s>>>(in, out, tb.Nx, lh, lw, pick(tb.tw_t, tb.tw_t32),
                                                       pick(tb.gpow, tb.gpow32), pick(tb.gipw, tb.gipw32),
                                                       pick(tb.ak, tb.ak32), lt, R(cnorm), pick(tb.gpowr, tb.gpowr32),
-                                                      pick(tb.gipr, tb.gipr32), delta_rhs, n0_only);
+                                                      pick(tb.gipr, tb.gipr32), qv, delta_rhs, n0_only);
     return cudaGetLastError();
 }
 

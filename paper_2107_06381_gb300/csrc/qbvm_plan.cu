@@ -177,6 +177,21 @@ int ptr_kind(const void* ptr) {
 
 // --- FP64 pipeline on device pointers -------------------------------------
 
+// Normalisation of the FP64 space-first solve: the inverse-DST factors 2/(n+1)
+// per axis, 1/nt of the inverse time DFT, and 4^(-2 dim) for the FP64 DSTs,
+// which produce 4x the transform (an exact power of two).
+double fp64_cn(const Tables& tb) {
+    double cn = 1.0;
+    for (int i = 0; i < tb.dim; ++i) cn *= 2.0 / (tb.n[i] + 1);
+    cn /= tb.nt;
+    return std::ldexp(cn, -4 * tb.dim);
+}
+// The time-solve constant of the plan's right-hand side kind.
+double fp64_cnorm(const qbvm_plan_t* p) {
+    const double cn = fp64_cn(p->tb);
+    return p->d.rhs_kind == QBVM_RHS_DELTA ? -p->tb.omega * cn : p->tb.tau * cn;
+}
+
 int solve_fp64_dev(qbvm_plan_t* p, const double* in, double* y, int n0_only, cudaStream_t s) {
     const Tables& tb = p->tb;
     const int delta = p->d.rhs_kind == QBVM_RHS_DELTA;
@@ -189,12 +204,7 @@ int solve_fp64_dev(qbvm_plan_t* p, const double* in, double* y, int n0_only, cud
         launches = 3;
     } else {
         const long long nx = tb.n[0], ny = tb.n[1], nz = tb.n[2];
-        double cn = 1.0;
-        for (int i = 0; i < tb.dim; ++i) cn *= 2.0 / (tb.n[i] + 1);
-        cn /= tb.nt;
-        // the FP64 DSTs produce 4x the transform (X4): 4^(2 dim) over the forward
-        // and inverse passes, an exact power of two
-        cn = std::ldexp(cn, -4 * tb.dim);
+        const double cn = fp64_cn(tb);
         double* work;
         if (delta) {
             // DST of g along x, y (, z) -> ghat, then the time solve reads level 0
@@ -513,6 +523,13 @@ int qbvm_plan(const qbvm_desc* desc, qbvm_plan_t** out) {
         if (!rc) rc = dalloc(p, &p->wcp, total);
     }
     if (!rc && d.dim > 1) rc = dalloc(p, &p->ghat, (size_t)tb.Nx);
+    if (!rc && d.dim > 1 && d.precision == QBVM_FP64) {
+        // Step (b) reciprocals, once per plan
+        rc = dalloc(p, &tb.qinv, (size_t)(nt / 2) * (size_t)tb.Nx);
+        if (!rc && (qbvm::launch_make_qinv(tb, fp64_cnorm(p), tb.qinv, 0) != cudaSuccess ||
+                    cudaStreamSynchronize(0) != cudaSuccess))
+            rc = QBVM_ERR_CUDA;
+    }
     if (!rc) {
         p->nres = qbvm::residual_blocks(tb);
         rc = dalloc(p, &p->partials, (size_t)2 * p->nres);
