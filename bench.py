@@ -66,6 +66,9 @@ def parse():
     ap.add_argument("--no-refine", action="store_true", help="skip the FP32+refinement variant")
     ap.add_argument("--refine-only", action="store_true",
                     help="profiling aid: run only the FP32+refinement variant (no JSON headline)")
+    ap.add_argument("--c5", action="store_true",
+                    help="only the learned-alpha workload at its full size (200k labelled 2D 127^2 x 128 "
+                         "instances, 4096 held out); several minutes")
     ap.add_argument("--no-extra", action="store_true",
                     help="skip the 3D (127^3 x 128) and batched-sweep (512 instances) measurements")
     return ap.parse_args()
@@ -540,8 +543,48 @@ def reference_arm(args):
             "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
 
 
+def c5_leg(n_train=200_000, n_eval=4096, seed=5):
+    """Learned alpha at its full size: 2D 127^2 x 128 instances (16 decaying sine
+    modes, relative noise log-uniform in [1e-4, 1e-2]); labels from the batched
+    32-alpha sweep (the alpha with the smallest ||y^0 - z0||), features and the
+    MLP on the GPU; evaluation on held-out instances against the a-priori rule
+    alpha = delta, the discrepancy principle and the scan's best."""
+    import numpy as np
+    import torch
+    import paper_2107_06381_gb300 as Q
+    from paper_2107_06381_gb300 import learned_alpha as LA
+    Q.build_library()
+    Q.load_library()
+    t0 = time.perf_counter()
+    data = LA.make_dataset(n_train, seed=seed, chunk=4096)
+    t_label = time.perf_counter() - t0
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    mlp, hist = LA.train(data, epochs=12, batch=1024, lr=2e-3, seed=seed)
+    torch.cuda.synchronize()
+    t_train = time.perf_counter() - t0
+    ev = LA.evaluate(mlp, n_eval, seed=seed + 1, chunk=4096)
+    mlp.close()
+    return {"workload": "c5_learned_alpha_2d_127sq_x128", "train_instances": n_train, "eval_instances": n_eval,
+            "labels_from": "batched sweep, 32 alphas in [alpha_rule/100, 100 alpha_rule], min ||y0 - z0||",
+            "label_and_feature_seconds": round(t_label, 2), "train_seconds": round(t_train, 2),
+            "train_loss_first_last": [round(hist[0][1], 4), round(hist[-1][1], 4)],
+            "mean_e_h": {"learned": float(ev["learned"].mean()), "a_priori_rule": float(ev["rule"].mean()),
+                         "discrepancy_principle": float(ev["morozov"].mean()), "best_of_scan": float(ev["best"].mean())},
+            "learned_better_than_rule_fraction": float(np.mean(ev["learned"] < ev["rule"])),
+            "one_alpha_solves_per_s": float(ev["one_alpha_solves_per_s"]),
+            "scan_alpha_solves_per_s": float(ev["scan_solves_per_s"]),
+            "scan_instances_per_s": float(ev["scan_instances_per_s"]),
+            "data": "synthetic"}
+
+
 def main():
     args = parse()
+    if args.c5:
+        import torch
+        torch.cuda.set_device(0)
+        print(json.dumps(c5_leg()), flush=True)
+        return 0
     world = int(os.environ.get("WORLD_SIZE", "1"))
     rank = int(os.environ.get("RANK", "0"))
     local_rank = int(os.environ.get("LOCAL_RANK", "0"))
