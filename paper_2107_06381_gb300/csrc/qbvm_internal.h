@@ -39,6 +39,16 @@ struct Tables {
     float*   lamtau32 = nullptr;
     double2* bk = nullptr;           // 1D Thomas diagonal for frequency 2m: h^2 d_{2m} / tau + 2
     double2* qinv = nullptr;         // FP64 2D/3D: cnorm / (d_{2m} + tau Lambda_l), [H][Nx]
+    // general nt (not a power of two): Bluestein tables, every frequency k < nt
+    int gen = 0;                     // 1: the time DFTs use k_bluestein
+    int lL = 0;                      // log2 L, L >= 2 nt - 1
+    double2* tw_L = nullptr;         // exp(-2 pi i m / L), m < L
+    double2* chirp = nullptr;        // exp(i pi m^2 / nt), m < nt
+    double2* bs_fwd = nullptr;       // FFT_L of conj(chirp) wrapped, / L (for the +theta transform)
+    double2* bs_inv = nullptr;       // FFT_L of chirp wrapped, / L (for the -theta transform)
+    double2* gpw_full = nullptr;     // scale * gamma^t, t < nt
+    double2* gip_full = nullptr;     // gamma^{-t}, t < nt
+    double2* dk_full = nullptr;      // d_k = 1 - gamma theta^k, k < nt
 };
 
 // DST-I (unnormalised, S_{jk} = sin(pi j k /(n+1))) along one axis of an
@@ -57,6 +67,13 @@ cudaError_t launch_dst(const TIN* in, void* out, int n, int lm, long long outer,
 template <typename R>
 cudaError_t launch_time_solve(const R* in, R* out, const Tables& tb, double cnorm, int delta_rhs,
                               int n0_only, cudaStream_t s);
+
+// Time DFTs of length nt for a general nt (tb.gen): mode 0 = Step (a) + the
+// divide of Step (b) (real [nt][N] in, complex out), 1 = Step (a) only (1D),
+// 2 = Step (c) (complex in, real out).  N columns, in place not allowed.
+cudaError_t launch_bluestein(int mode, const void* in, void* out, long long N, const Tables& tb, double cnorm,
+                             int delta_rhs, int n0_only, cudaStream_t s);
+cudaError_t launch_thomas_1d_n(double2* wk, double2* cp, int nsys, const Tables& tb, cudaStream_t s);
 
 // tb.qinv[m][l] = cnorm / (d_{2m} + tau Lambda_l) (IEEE FP64 division), built
 // once per plan so that Step (b) of the FP64 time solve is one complex product.

@@ -633,6 +633,131 @@ cudaError_t launch_time_inv_1d(const double2* wk, double* out, const Tables& tb,
     return cudaGetLastError();
 }
 
+// ------------------------------------------------------- general nt (Bluestein)
+//
+// For a number of time levels P that is not a power of two (the paper's meshes
+// have N_t = N + 1) the length-P DFTs of Steps (a) and (c) use Bluestein's
+// chirp-z identity (L. I. Bluestein, "A linear filtering approach to the
+// computation of the discrete Fourier transform", 1970): with
+// c_m = exp(S i pi m^2 / P),
+//     sum_{t<P} x_t exp(S 2 pi i k t / P) = c_k sum_t (x_t c_t) conj(c_{k-t}),
+// a linear convolution, evaluated as a cyclic one of power-of-two length
+// L >= 2P - 1 with the FFT engine: FFT(x c), times the plan's table
+// B = FFT(conj c, wrapped) / L, inverse FFT, times c_k.  Every frequency is
+// formed (no half-spectrum shortcut).  Modes:
+//   BS_FWD_DIV  Step (a) + Step (b) of the space-first solve: real [P][N] in
+//               (one level for the delta right-hand side), pre-factor
+//               gamma^t, out [P][N] complex cnorm u^_k / (d_k + tau Lambda_l);
+//   BS_FWD      Step (a) of the 1D solve: as above without the divide
+//               (cnorm scales the delta right-hand side);
+//   BS_INV      Step (c): complex [P][N] in, out y_t = Re(post_t q_t) real.
+// The forward transform of the delta right-hand side f^0 e_0 is the constant
+// f^0 and is written without transforming.
+enum { BS_FWD_DIV = 0, BS_FWD = 1, BS_INV = 2 };
+
+template <int S, int MODE>
+__global__ void __launch_bounds__(TILE_THREADS)
+k_bluestein(const void* in, void* out, long long N, int P, int lL, int lw, const double2* __restrict__ tw,
+            const double2* __restrict__ chirp, const double2* __restrict__ B, const double2* __restrict__ fac,
+            const double2* __restrict__ dk, const double* __restrict__ lamtau, double cnorm, int delta_rhs,
+            int n0_only) {
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    const int L = 1 << lL, W = 1 << lw;
+    double2* buf = reinterpret_cast<double2*>(smem_raw);
+    double2* stw = buf + ((size_t)L << lw);
+    const int tid = threadIdx.x, nth = blockDim.x;
+    const long long l0 = (long long)blockIdx.x * W;
+    auto csgn = [](double2 c) { return S > 0 ? c : make_double2(c.x, -c.y); };   // c_m of sign S
+    auto epilogue = [&](int k, long long l, double2 v) {
+        if (MODE == BS_FWD_DIV) {
+            const double2 a = dk[k];
+            const double zr = a.x + lamtau[l], zi = a.y;
+            const double inv = cnorm / (zr * zr + zi * zi);
+            reinterpret_cast<double2*>(out)[(long long)k * N + l] =
+                make_double2((v.x * zr + v.y * zi) * inv, (v.y * zr - v.x * zi) * inv);
+        } else if (MODE == BS_FWD) {
+            reinterpret_cast<double2*>(out)[(long long)k * N + l] = v;
+        } else {
+            const double2 g = fac[k];
+            reinterpret_cast<double*>(out)[(long long)k * N + l] = g.x * v.x - g.y * v.y;
+        }
+    };
+    if (MODE != BS_INV && delta_rhs) {
+        const double sc = MODE == BS_FWD ? cnorm : 1.0;
+        for (int e = tid; e < (P << lw); e += nth) {
+            const int k = e >> lw, c = e & (W - 1);
+            const long long l = l0 + c;
+            if (l < N) {
+                const double f0 = sc * reinterpret_cast<const double*>(in)[l];
+                epilogue(k, l, make_double2(fac[0].x * f0, fac[0].y * f0));
+            }
+        }
+        return;
+    }
+    for (int i = tid; i < L; i += nth) stw[i] = tw[i];
+    for (int e = tid; e < (L << lw); e += nth) {
+        const int t = e >> lw, c = e & (W - 1);
+        const long long l = l0 + c;
+        double2 v = make_double2(0.0, 0.0);
+        if (t < P && l < N) {
+            if (MODE == BS_INV) {
+                v = reinterpret_cast<const double2*>(in)[(long long)t * N + l];
+            } else {
+                const double f = reinterpret_cast<const double*>(in)[(long long)t * N + l];
+                v = make_double2(fac[t].x * f, fac[t].y * f);
+            }
+            v = cmul(v, csgn(chirp[t]));
+        }
+        buf[e] = v;
+    }
+    __syncthreads();
+    fft_tile<-1, TILE_ELEMS / 4 / TILE_THREADS>(buf, stw, lL, lw);
+    for (int e = tid; e < (L << lw); e += nth) buf[e] = cmul(buf[e], B[e >> lw]);
+    __syncthreads();
+    fft_tile<+1, TILE_ELEMS / 4 / TILE_THREADS>(buf, stw, lL, lw);
+    const int kmax = (MODE == BS_INV && n0_only) ? 1 : P;
+    for (int e = tid; e < (kmax << lw); e += nth) {
+        const int k = e >> lw, c = e & (W - 1);
+        const long long l = l0 + c;
+        if (l < N) epilogue(k, l, cmul(buf[e], csgn(chirp[k])));
+    }
+}
+
+cudaError_t launch_bluestein(int mode, const void* in, void* out, long long N, const Tables& tb, double cnorm,
+                             int delta_rhs, int n0_only, cudaStream_t s) {
+    const int lL = tb.lL, L = 1 << lL;
+    int lw = 0;
+    while ((L << (lw + 1)) <= TILE_ELEMS) ++lw;
+    const long long blocks = (N + (1 << lw) - 1) >> lw;
+    const size_t smem = sizeof(double2) * (((size_t)L << lw) + L);
+    cudaError_t e = cudaSuccess;
+    const int P = tb.nt;
+    if (mode == BS_FWD_DIV) {
+        auto kern = k_bluestein<+1, BS_FWD_DIV>;
+        if ((e = set_smem(kern, smem)) != cudaSuccess) return e;
+        kern<<<(unsigned)blocks, TILE_THREADS, smem, s>>>(in, out, N, P, lL, lw, tb.tw_L, tb.chirp, tb.bs_fwd,
+                                                          tb.gpw_full, tb.dk_full, tb.lamtau, cnorm, delta_rhs, 0);
+    } else if (mode == BS_FWD) {
+        auto kern = k_bluestein<+1, BS_FWD>;
+        if ((e = set_smem(kern, smem)) != cudaSuccess) return e;
+        kern<<<(unsigned)blocks, TILE_THREADS, smem, s>>>(in, out, N, P, lL, lw, tb.tw_L, tb.chirp, tb.bs_fwd,
+                                                          tb.gpw_full, nullptr, nullptr, cnorm, delta_rhs, 0);
+    } else {
+        auto kern = k_bluestein<-1, BS_INV>;
+        if ((e = set_smem(kern, smem)) != cudaSuccess) return e;
+        kern<<<(unsigned)blocks, TILE_THREADS, smem, s>>>(in, out, N, P, lL, lw, tb.tw_L, tb.chirp, tb.bs_inv,
+                                                          tb.gip_full, nullptr, nullptr, 0.0, 0, n0_only);
+    }
+    return cudaGetLastError();
+}
+
+cudaError_t launch_thomas_1d_n(double2* wk, double2* cp, int nsys, const Tables& tb, cudaStream_t s) {
+    int threads = 64;
+    int blocks = (nsys + threads - 1) / threads;
+    k_thomas_1d<<<blocks, threads, 0, s>>>(wk, cp, nsys, tb.Nx, tb.bk);
+    return cudaGetLastError();
+}
+
 // ------------------------------------------------------------------ residual
 //
 // (A y)^n = (y^n - y^{n-1})/tau - Delta_h y^n for n >= 1 and

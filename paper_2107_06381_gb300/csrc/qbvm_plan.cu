@@ -69,7 +69,12 @@ int validate(const qbvm_desc* d) {
     if (!std::isfinite(d->alpha) || std::isnan(d->delta)) return QBVM_ERR_BAD_ARG;
     if (!(d->alpha > 0) && !(d->delta > 0 && std::isfinite(d->delta))) return QBVM_ERR_BAD_ARG;
     // sizes the kernels implement
-    if (!is_pow2(d->nt) || d->nt > 1024) return QBVM_ERR_UNSUPPORTED;
+    if (is_pow2(d->nt)) {
+        if (d->nt > 1024) return QBVM_ERR_UNSUPPORTED;
+    } else {
+        // other lengths: FP64, Bluestein time DFTs of power-of-two length L >= 2 nt - 1 <= 4096
+        if (d->precision != QBVM_FP64 || d->nt > 2048) return QBVM_ERR_UNSUPPORTED;
+    }
     if (d->precision == QBVM_FP32_REFINE && d->dim == 1) return QBVM_ERR_UNSUPPORTED;
     if (d->dim == 1) {
         if (d->m[0] - 1 > (1 << 20)) return QBVM_ERR_UNSUPPORTED;
@@ -114,6 +119,69 @@ void roots(int P, std::vector<double2>& w64, std::vector<float2>& w32) {
         w64[m] = make_double2(c, s);
         w32[m] = make_float2((float)c, (float)s);
     }
+}
+
+// Tables of the Bluestein time DFTs for nt not a power of two (Section 3.3,
+// Steps (a) and (c) with every frequency): chirp c_m = exp(i pi m^2/nt), the
+// transforms B = DFT_L(b)/L of the wrapped kernels b_m = conj(c_|m|) (for the
+// +theta transform) and c_|m| (for -theta), gamma^t and gamma^{-t} for t < nt,
+// d_k = 1 - gamma theta^k.  Angles are reduced exactly in integers
+// (m^2 mod 2 nt, j m mod L) before the FP64 sine and cosine.
+int bluestein_tables(qbvm_plan_t* p, double mag, double scale1d) {
+    Tables& tb = p->tb;
+    const int P = tb.nt;
+    int lL = 0;
+    while ((1 << lL) < 2 * P - 1) ++lL;
+    const int L = 1 << lL;
+    tb.gen = 1;
+    tb.lL = lL;
+    std::vector<double2> twL, chirp(P), bf(L), bi(L), gp(P), gi(P), dk(P);
+    std::vector<float2> tw32;
+    roots(L, twL, tw32);
+    for (int m = 0; m < P; ++m) {
+        const long long r = ((long long)m * m) % (2LL * P);
+        const double a = M_PI * ((double)r / P);
+        chirp[m] = make_double2(std::cos(a), std::sin(a));
+    }
+    std::vector<double2> kf(L, make_double2(0, 0)), ki(L, make_double2(0, 0));
+    for (int m = 0; m < P; ++m) {
+        const double2 c = chirp[m], cc = make_double2(c.x, -c.y);
+        kf[m] = cc;
+        ki[m] = c;
+        if (m > 0) {
+            kf[L - m] = cc;
+            ki[L - m] = c;
+        }
+    }
+    for (int j = 0; j < L; ++j) {                         // direct DFT_L with exp(-2 pi i j m / L)
+        double fr = 0, fi = 0, ir = 0, ii = 0;
+        for (int m = 0; m < L; ++m) {
+            const double2 w = twL[((long long)j * m) % L];
+            fr += kf[m].x * w.x - kf[m].y * w.y;
+            fi += kf[m].x * w.y + kf[m].y * w.x;
+            ir += ki[m].x * w.x - ki[m].y * w.y;
+            ii += ki[m].x * w.y + ki[m].y * w.x;
+        }
+        bf[j] = make_double2(fr / L, fi / L);
+        bi[j] = make_double2(ir / L, ii / L);
+    }
+    const double g1 = std::pow(mag, 1.0 / P);
+    for (int t = 0; t < P; ++t) {
+        const double a = M_PI * ((double)t / P);
+        const double r = std::pow(mag, (double)t / P), ri = std::pow(mag, -(double)t / P);
+        gp[t] = make_double2(scale1d * r * std::cos(a), scale1d * r * std::sin(a));
+        gi[t] = make_double2(ri * std::cos(a), -ri * std::sin(a));
+        const double b = M_PI * ((2.0 * t + 1.0) / P);   // arg(gamma theta^k), k = t
+        dk[t] = make_double2(1.0 - g1 * std::cos(b), -g1 * std::sin(b));
+    }
+    int rc = upload(p, &tb.tw_L, twL);
+    if (!rc) rc = upload(p, &tb.chirp, chirp);
+    if (!rc) rc = upload(p, &tb.bs_fwd, bf);
+    if (!rc) rc = upload(p, &tb.bs_inv, bi);
+    if (!rc) rc = upload(p, &tb.gpw_full, gp);
+    if (!rc) rc = upload(p, &tb.gip_full, gi);
+    if (!rc) rc = upload(p, &tb.dk_full, dk);
+    return rc;
 }
 
 void destroy_plan(qbvm_plan_t* p) {
@@ -196,7 +264,13 @@ int solve_fp64_dev(qbvm_plan_t* p, const double* in, double* y, int n0_only, cud
     const Tables& tb = p->tb;
     const int delta = p->d.rhs_kind == QBVM_RHS_DELTA;
     int launches = 0;
-    if (tb.dim == 1) {
+    if (tb.dim == 1 && tb.gen) {
+        // general nt: Bluestein time DFTs over every frequency, Thomas for each
+        { Span sp_(p, "time_fwd_1d", s); CK(qbvm::launch_bluestein(1, in, p->wk, tb.Nx, tb, delta ? -tb.omega / tb.tau : 1.0, delta, 0, s)); }
+        { Span sp_(p, "thomas_1d", s); CK(qbvm::launch_thomas_1d_n(p->wk, p->wcp, tb.nt, tb, s)); }
+        { Span sp_(p, "time_inv_1d", s); CK(qbvm::launch_bluestein(2, p->wk, y, tb.Nx, tb, 0.0, 0, n0_only, s)); }
+        launches = 3;
+    } else if (tb.dim == 1) {
         // Step (a), Step (b) (Thomas per frequency), Step (c)
         { Span sp_(p, "time_fwd_1d", s); CK(qbvm::launch_time_fwd_1d(in, p->wk, tb, delta, delta ? -tb.omega / tb.tau : 1.0, s)); }
         { Span sp_(p, "thomas_1d", s); CK(qbvm::launch_thomas_1d(p->wk, p->wcp, tb, s)); }
@@ -216,8 +290,14 @@ int solve_fp64_dev(qbvm_plan_t* p, const double* in, double* y, int n0_only, cud
                 ++launches;
             }
             // f^0 = -omega g / tau: fold -omega/tau into the time-solve constant
-            { Span sp_(p, "time_solve", s); CK(qbvm::launch_time_solve<double>(p->ghat, y, tb, -tb.omega * cn, 1, n0_only, s)); }
-            ++launches;
+            if (tb.gen) {
+                { Span sp_(p, "time_fwd", s); CK(qbvm::launch_bluestein(0, p->ghat, p->wk, tb.Nx, tb, -tb.omega * cn, 1, 0, s)); }
+                { Span sp_(p, "time_inv", s); CK(qbvm::launch_bluestein(2, p->wk, y, tb.Nx, tb, 0.0, 0, n0_only, s)); }
+                launches += 2;
+            } else {
+                { Span sp_(p, "time_solve", s); CK(qbvm::launch_time_solve<double>(p->ghat, y, tb, -tb.omega * cn, 1, n0_only, s)); }
+                ++launches;
+            }
             work = y;
         } else {
             work = n0_only ? p->wreal : y;
@@ -229,8 +309,14 @@ int solve_fp64_dev(qbvm_plan_t* p, const double* in, double* y, int n0_only, cud
                 { Span sp_(p, "dst_z", s); CK(qbvm::launch_dst<double, double, 0, true>(work, work, tb.n[2], p->lp[2], nt, nx * ny, tb.tw_s[2], tb.sn_s[2], s)); }
                 ++launches;
             }
-            { Span sp_(p, "time_solve", s); CK(qbvm::launch_time_solve<double>(work, y, tb, tb.tau * cn, 0, n0_only, s)); }
-            ++launches;
+            if (tb.gen) {
+                { Span sp_(p, "time_fwd", s); CK(qbvm::launch_bluestein(0, work, p->wk, tb.Nx, tb, tb.tau * cn, 0, 0, s)); }
+                { Span sp_(p, "time_inv", s); CK(qbvm::launch_bluestein(2, p->wk, y, tb.Nx, tb, 0.0, 0, n0_only, s)); }
+                launches += 2;
+            } else {
+                { Span sp_(p, "time_solve", s); CK(qbvm::launch_time_solve<double>(work, y, tb, tb.tau * cn, 0, n0_only, s)); }
+                ++launches;
+            }
         }
         // inverse DST (the (2/M) factors are in the time-solve constant)
         const long long lev = n0_only ? 1 : tb.nt;
@@ -470,11 +556,21 @@ int qbvm_plan(const qbvm_desc* desc, qbvm_plan_t** out) {
     if (!rc) rc = upload(p, &tb.gpowr32, to32(gpowr));
     if (!rc) rc = upload(p, &tb.gipr32, to32(gipr));
     if (!rc) rc = upload(p, &tb.ak32, to32(ak));
+    if (!rc && !is_pow2(nt)) rc = bluestein_tables(p, mag, scale1d);
     if (!rc && d.dim == 1) {
-        bk.resize(H);
         const double h2 = p->h[0] * p->h[0];
-        for (int m = 0; m < H; ++m)
-            bk[m] = make_double2(h2 * ak[m].x / p->tau + 2.0, h2 * ak[m].y / p->tau);
+        if (tb.gen) {                                     // every frequency k < nt
+            bk.resize(nt);
+            const double g1n = std::pow(mag, 1.0 / nt);
+            for (int k = 0; k < nt; ++k) {
+                const double a = M_PI * ((2.0 * k + 1.0) / nt);
+                bk[k] = make_double2(h2 * (1.0 - g1n * std::cos(a)) / p->tau + 2.0, -h2 * g1n * std::sin(a) / p->tau);
+            }
+        } else {
+            bk.resize(H);
+            for (int m = 0; m < H; ++m)
+                bk[m] = make_double2(h2 * ak[m].x / p->tau + 2.0, h2 * ak[m].y / p->tau);
+        }
         rc = upload(p, &tb.bk, bk);
     }
     if (!rc && d.dim > 1) {
@@ -523,7 +619,8 @@ int qbvm_plan(const qbvm_desc* desc, qbvm_plan_t** out) {
         if (!rc) rc = dalloc(p, &p->wcp, total);
     }
     if (!rc && d.dim > 1) rc = dalloc(p, &p->ghat, (size_t)tb.Nx);
-    if (!rc && d.dim > 1 && d.precision == QBVM_FP64) {
+    if (!rc && d.dim > 1 && tb.gen) rc = dalloc(p, &p->wk, total);      // Bluestein spectrum [nt][Nx]
+    if (!rc && d.dim > 1 && d.precision == QBVM_FP64 && !tb.gen) {
         // Step (b) reciprocals, once per plan
         rc = dalloc(p, &tb.qinv, (size_t)(nt / 2) * (size_t)tb.Nx);
         if (!rc && (qbvm::launch_make_qinv(tb, fp64_cnorm(p), tb.qinv, 0) != cudaSuccess ||

@@ -64,12 +64,15 @@ def test_bad_descriptors_are_rejected_without_a_gpu(lib, change):
     assert ei.value.code == -1
 
 
-@pytest.mark.parametrize("change", [dict(nt=24), dict(nt=2048), dict(m=(24, 16, 1)), dict(m=(2048, 16, 1))],
-                         ids=["nt24", "nt2048", "m24", "m2048"])
+@pytest.mark.parametrize("change", [dict(nt=24, precision=1), dict(nt=2048), dict(nt=2049), dict(m=(24, 16, 1)),
+                                    dict(m=(2048, 16, 1))],
+                         ids=["nt24-fp32", "nt2048", "nt2049", "m24", "m2048"])
 def test_unsupported_sizes(lib, change):
-    args = dict(dim=2, m=(16, 16, 1), nt=16)
+    """Power-of-two nt up to 1024; other nt (Bluestein time DFTs) up to 2048 and
+    FP64 only; DST lengths M = 2^k."""
+    args = dict(dim=2, m=(16, 16, 1), nt=16, precision=0)
     args.update(change)
-    desc = Q.make_desc(2, args["m"], 1.0, 0.1, args["nt"], 0, 1e-3)
+    desc = Q.make_desc(2, args["m"], 1.0, 0.1, args["nt"], 0, 1e-3, 0.0, args["precision"])
     with pytest.raises(Q.QbvmError) as ei:
         Q.qbvm_plan(desc)
     assert ei.value.code == -7

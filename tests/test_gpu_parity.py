@@ -95,6 +95,57 @@ def test_delta_rhs_matches_oracle(grid, form):
     assert O.rel_l2(got, want) <= TOL
 
 
+# nt not a power of two: Bluestein time DFTs (the paper's meshes have N_t = N + 1)
+GENERAL_NT = [
+    bi.Grid(1, (2,), 1.0, 0.1, 3),
+    bi.Grid(1, (64,), 1.0, 0.1, 17),
+    bi.Grid(1, (100,), math.pi, 1.0, 24),
+    bi.Grid(1, (256,), math.pi, 1.0, 257),       # Table 1 mesh (M, N) = (256, 256)
+    bi.Grid(2, (16, 16), math.pi, 1.0, 17),      # Table 2 mesh (16^2, 16)
+    bi.Grid(2, (32, 32), math.pi, 1.0, 33),
+    bi.Grid(2, (16, 8), 1.0, 0.1, 100),
+    bi.Grid(2, (8, 8), 1.0, 0.1, 1000),
+    bi.Grid(3, (8, 8, 8), 1.0, 0.05, 9),
+    bi.Grid(3, (8, 4, 16), 1.0, 0.05, 12),
+]
+
+
+@pytest.mark.parametrize("grid", GENERAL_NT, ids=lambda g: f"d{g.dim}-M{'x'.join(map(str, g.M))}-nt{g.nt}")
+@pytest.mark.parametrize("form", [Q.FORM_PQ, Q.FORM_PM])
+@pytest.mark.parametrize("rhs_kind", [Q.RHS_DELTA, Q.RHS_GENERAL])
+def test_general_nt_matches_oracle(grid, form, rhs_kind):
+    alpha = 1e-3 if form == Q.FORM_PQ else 1e-3 * grid.tau
+    F = bi.random_general_rhs(grid, seed=12)
+    if rhs_kind == Q.RHS_DELTA:
+        want = oracle_solve(grid, form, alpha, O.delta_rhs(grid, form, alpha, F[0]))
+        got = gpu_solve(grid, form, alpha, F[0], Q.RHS_DELTA)
+    else:
+        want = oracle_solve(grid, form, alpha, F)
+        got = gpu_solve(grid, form, alpha, F, Q.RHS_GENERAL)
+    assert O.rel_l2(got, want) <= TOL
+
+
+@pytest.mark.parametrize("grid", [bi.Grid(1, (64,), 1.0, 0.1, 33), bi.Grid(2, (16, 16), 1.0, 0.1, 65)],
+                         ids=["1d", "2d"])
+@pytest.mark.parametrize("rhs_kind", [Q.RHS_DELTA, Q.RHS_GENERAL])
+def test_general_nt_n0_only(grid, rhs_kind):
+    F = bi.random_general_rhs(grid, seed=13)
+    rhs = F[0] if rhs_kind == Q.RHS_DELTA else F
+    full = gpu_solve(grid, Q.FORM_PQ, 1e-3, rhs, rhs_kind)
+    y0 = gpu_solve(grid, Q.FORM_PQ, 1e-3, rhs, rhs_kind, n0_only=True)
+    np.testing.assert_allclose(y0[0], full[0], rtol=0, atol=1e-13 * np.abs(full).max())
+
+
+def test_general_nt_paper_table1_mesh():
+    """1D (0, pi), h = pi/1024, N_t = 1025 levels (the largest Table 1 mesh)."""
+    grid = bi.Grid(1, (1024,), math.pi, 1.0, 1025)
+    F = bi.random_general_rhs(grid, seed=14)
+    alpha = 1e-4
+    want = O.solve_spectral(grid, Q.FORM_PQ, alpha, O.delta_rhs(grid, Q.FORM_PQ, alpha, F[0]))
+    got = gpu_solve(grid, Q.FORM_PQ, alpha, F[0], Q.RHS_DELTA)
+    assert O.rel_l2(got, want) <= TOL
+
+
 @pytest.mark.parametrize("form", [Q.FORM_PQ, Q.FORM_PM])
 def test_c1_workload(form):
     """1D, 63 interior points x 64 levels, alpha by the Section 5 rule."""
