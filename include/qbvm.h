@@ -69,11 +69,14 @@ extern "C" {
 /* ------------------------------------------------------------ descriptor
  * dim     space dimension d = 1, 2 or 3.
  * m[3]    intervals per axis (x, y, z); m[d] >= 2; entries beyond dim ignored.
- *         Supported: 1D any m with m-1 <= 2^20; 2D/3D m a power of two in
- *         [4, 1024] (the DST-I length m-1 is then 2^k - 1).
+ *         Supported: m a power of two in [4, 1024] on every axis (the DST-I
+ *         length m-1 is then 2^k - 1); in 1D with the time-first order any m
+ *         with m-1 <= 2^20.
  * L       side length of the domain (0, L)^d; h = L/m[d].
  * T       final time, > 0.
- * nt      time levels N_t, a power of two in [2, 1024].
+ * nt      time levels N_t: a power of two in [2, 1024] (half-length time
+ *         transforms), or any other nt in [3, 2048] with FP64 (Bluestein time
+ *         DFTs; the paper's meshes have N_t = N + 1).
  * form    QBVM_FORM_PQ or QBVM_FORM_PM.
  * alpha   regularisation parameter > 0, or <= 0 for the a-priori rule of
  *         Section 5 from `delta`: alpha = delta (PQ), alpha = tau*delta (PM).
@@ -81,9 +84,22 @@ extern "C" {
  * precision  QBVM_FP64 or QBVM_FP32_REFINE.
  * rhs_kind   QBVM_RHS_DELTA or QBVM_RHS_GENERAL.
  * refine_tol       FP32_REFINE: stop when ||f - A y||/||f|| <= refine_tol
- *                  (<= 0 selects 1e-12).
+ *                  (<= 0 selects 1e-13).
  * refine_max_iters FP32_REFINE: iteration cap (<= 0 selects 10).
+ * order   QBVM_ORDER_*: how the factors of eq. 3.8 are applied.  Space-first
+ *         (DST-I along every axis, one scalar omega-circulant time solve per
+ *         spatial mode, inverse DST) is the only order in 2D/3D.  In 1D the
+ *         time-first order of Section 3.3 (omega-scaled time DFT, one complex
+ *         tridiagonal solve per frequency, inverse DFT) is also available;
+ *         it is the paper's order but loses accuracy when |omega| is large and
+ *         the data are smooth (the spatial systems of the low frequencies are
+ *         nearly singular): 2e-10 to 1e-9 against the exact solution on the
+ *         paper's 1D meshes at noise 1e-4, where space-first gives 1e-12.
+ *         AUTO takes space-first whenever m allows it.
  */
+#define QBVM_ORDER_AUTO        0
+#define QBVM_ORDER_TIME_FIRST  1
+#define QBVM_ORDER_SPACE_FIRST 2
 typedef struct qbvm_desc {
     int    dim;
     int    m[3];
@@ -97,6 +113,7 @@ typedef struct qbvm_desc {
     int    rhs_kind;
     double refine_tol;
     int    refine_max_iters;
+    int    order;
 } qbvm_desc;
 
 /* Read-only facts about a plan (qbvm_plan_info). */

@@ -26,6 +26,7 @@ __all__ = [
 FORM_PQ, FORM_PM = 0, 1
 FP64, FP32_REFINE = 0, 1
 RHS_DELTA, RHS_GENERAL = 0, 1
+ORDER_AUTO, ORDER_TIME_FIRST, ORDER_SPACE_FIRST = 0, 1, 2
 
 
 class QbvmDesc(ctypes.Structure):
@@ -34,7 +35,7 @@ class QbvmDesc(ctypes.Structure):
         ("T", ctypes.c_double), ("nt", ctypes.c_int), ("form", ctypes.c_int),
         ("alpha", ctypes.c_double), ("delta", ctypes.c_double),
         ("precision", ctypes.c_int), ("rhs_kind", ctypes.c_int),
-        ("refine_tol", ctypes.c_double), ("refine_max_iters", ctypes.c_int),
+        ("refine_tol", ctypes.c_double), ("refine_max_iters", ctypes.c_int), ("order", ctypes.c_int),
     ]
 
 
@@ -202,10 +203,11 @@ def qbvm_version() -> int:
 
 
 def make_desc(dim, m, L, T, nt, form=FORM_PQ, alpha=0.0, delta=0.0, precision=FP64,
-              rhs_kind=RHS_DELTA, refine_tol=0.0, refine_max_iters=0) -> QbvmDesc:
+              rhs_kind=RHS_DELTA, refine_tol=0.0, refine_max_iters=0, order=0) -> QbvmDesc:
     mm = list(m) + [1] * (3 - len(m))
     return QbvmDesc(dim, (ctypes.c_int * 3)(*mm), float(L), float(T), int(nt), int(form), float(alpha),
-                    float(delta), int(precision), int(rhs_kind), float(refine_tol), int(refine_max_iters))
+                    float(delta), int(precision), int(rhs_kind), float(refine_tol), int(refine_max_iters),
+                    int(order))
 
 
 def qbvm_plan(desc: QbvmDesc) -> int:
@@ -499,9 +501,9 @@ class Plan:
     """Owning wrapper around a qbvm plan handle."""
 
     def __init__(self, dim, m, L, T, nt, form=FORM_PQ, alpha=0.0, delta=0.0, precision=FP64,
-                 rhs_kind=RHS_DELTA, refine_tol=0.0, refine_max_iters=0):
+                 rhs_kind=RHS_DELTA, refine_tol=0.0, refine_max_iters=0, order=0):
         self.desc = make_desc(dim, m, L, T, nt, form, alpha, delta, precision, rhs_kind,
-                              refine_tol, refine_max_iters)
+                              refine_tol, refine_max_iters, order)
         self.handle = qbvm_plan(self.desc)
 
     def solve(self, g_or_F, y, n0_only=False, stream=None):

@@ -14,6 +14,7 @@ constexpr int TILE_THREADS = 256;
 struct Tables {
     int nt = 0, lnt = 0;             // time levels, log2
     int dim = 0;
+    int sf = 0;                      // space-first order (DST, per-mode time solve, inverse DST)
     int n[3] = {1, 1, 1};            // interior points per axis (x, y, z)
     int lpd[3] = {0, 0, 0};          // log2(M_d) = log2(n_d + 1), the DST FFT length
     long long Nx = 0;                // spatial unknowns per level

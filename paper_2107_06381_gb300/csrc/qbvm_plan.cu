@@ -55,6 +55,15 @@ namespace {
 bool is_pow2(long long v) { return v > 0 && (v & (v - 1)) == 0; }
 int ilog2(long long v) { int l = 0; while ((1LL << l) < v) ++l; return l; }
 
+bool dst_length_ok(int m) { return is_pow2(m) && m >= 4 && m <= 1024; }
+// Space-first always in 2D/3D; in 1D on request, or by default when m allows the DST.
+bool space_first(const qbvm_desc* d) {
+    if (d->dim > 1) return true;
+    if (d->order == QBVM_ORDER_TIME_FIRST) return false;
+    if (d->order == QBVM_ORDER_SPACE_FIRST) return true;
+    return dst_length_ok(d->m[0]);
+}
+
 int validate(const qbvm_desc* d) {
     if (!d) return QBVM_ERR_BAD_ARG;
     if (d->dim < 1 || d->dim > 3) return QBVM_ERR_BAD_ARG;
@@ -75,12 +84,15 @@ int validate(const qbvm_desc* d) {
         // other lengths: FP64, Bluestein time DFTs of power-of-two length L >= 2 nt - 1 <= 4096
         if (d->precision != QBVM_FP64 || d->nt > 2048) return QBVM_ERR_UNSUPPORTED;
     }
+    if (d->order < QBVM_ORDER_AUTO || d->order > QBVM_ORDER_SPACE_FIRST) return QBVM_ERR_BAD_ARG;
+    if (d->order == QBVM_ORDER_TIME_FIRST && d->dim != 1) return QBVM_ERR_BAD_ARG;
     if (d->precision == QBVM_FP32_REFINE && d->dim == 1) return QBVM_ERR_UNSUPPORTED;
-    if (d->dim == 1) {
-        if (d->m[0] - 1 > (1 << 20)) return QBVM_ERR_UNSUPPORTED;
-    } else {
+    const bool sf = space_first(d);
+    if (sf) {
         for (int i = 0; i < d->dim; ++i)
-            if (!is_pow2(d->m[i]) || d->m[i] < 4 || d->m[i] > 1024) return QBVM_ERR_UNSUPPORTED;
+            if (!dst_length_ok(d->m[i])) return QBVM_ERR_UNSUPPORTED;
+    } else if (d->m[0] - 1 > (1 << 20)) {
+        return QBVM_ERR_UNSUPPORTED;
     }
     return QBVM_OK;
 }
@@ -264,13 +276,13 @@ int solve_fp64_dev(qbvm_plan_t* p, const double* in, double* y, int n0_only, cud
     const Tables& tb = p->tb;
     const int delta = p->d.rhs_kind == QBVM_RHS_DELTA;
     int launches = 0;
-    if (tb.dim == 1 && tb.gen) {
+    if (!tb.sf && tb.gen) {
         // general nt: Bluestein time DFTs over every frequency, Thomas for each
         { Span sp_(p, "time_fwd_1d", s); CK(qbvm::launch_bluestein(1, in, p->wk, tb.Nx, tb, delta ? -tb.omega / tb.tau : 1.0, delta, 0, s)); }
         { Span sp_(p, "thomas_1d", s); CK(qbvm::launch_thomas_1d_n(p->wk, p->wcp, tb.nt, tb, s)); }
         { Span sp_(p, "time_inv_1d", s); CK(qbvm::launch_bluestein(2, p->wk, y, tb.Nx, tb, 0.0, 0, n0_only, s)); }
         launches = 3;
-    } else if (tb.dim == 1) {
+    } else if (!tb.sf) {
         // Step (a), Step (b) (Thomas per frequency), Step (c)
         { Span sp_(p, "time_fwd_1d", s); CK(qbvm::launch_time_fwd_1d(in, p->wk, tb, delta, delta ? -tb.omega / tb.tau : 1.0, s)); }
         { Span sp_(p, "thomas_1d", s); CK(qbvm::launch_thomas_1d(p->wk, p->wcp, tb, s)); }
@@ -283,8 +295,8 @@ int solve_fp64_dev(qbvm_plan_t* p, const double* in, double* y, int n0_only, cud
         if (delta) {
             // DST of g along x, y (, z) -> ghat, then the time solve reads level 0
             { Span sp_(p, "dst_x", s); CK(qbvm::launch_dst<double, double, 0, true>(in, p->ghat, tb.n[0], p->lp[0], ny * nz, 1, tb.tw_s[0], tb.sn_s[0], s)); }
-            { Span sp_(p, "dst_y", s); CK(qbvm::launch_dst<double, double, 0, true>(p->ghat, p->ghat, tb.n[1], p->lp[1], nz, nx, tb.tw_s[1], tb.sn_s[1], s)); }
-            launches += 2;
+            if (tb.dim >= 2) { Span sp_(p, "dst_y", s); CK(qbvm::launch_dst<double, double, 0, true>(p->ghat, p->ghat, tb.n[1], p->lp[1], nz, nx, tb.tw_s[1], tb.sn_s[1], s)); }
+            launches += tb.dim >= 2 ? 2 : 1;
             if (tb.dim == 3) {
                 { Span sp_(p, "dst_z", s); CK(qbvm::launch_dst<double, double, 0, true>(p->ghat, p->ghat, tb.n[2], p->lp[2], 1, nx * ny, tb.tw_s[2], tb.sn_s[2], s)); }
                 ++launches;
@@ -303,8 +315,8 @@ int solve_fp64_dev(qbvm_plan_t* p, const double* in, double* y, int n0_only, cud
             work = n0_only ? p->wreal : y;
             const long long nt = tb.nt;
             { Span sp_(p, "dst_x", s); CK(qbvm::launch_dst<double, double, 0, true>(in, work, tb.n[0], p->lp[0], nt * ny * nz, 1, tb.tw_s[0], tb.sn_s[0], s)); }
-            { Span sp_(p, "dst_y", s); CK(qbvm::launch_dst<double, double, 0, true>(work, work, tb.n[1], p->lp[1], nt * nz, nx, tb.tw_s[1], tb.sn_s[1], s)); }
-            launches += 2;
+            if (tb.dim >= 2) { Span sp_(p, "dst_y", s); CK(qbvm::launch_dst<double, double, 0, true>(work, work, tb.n[1], p->lp[1], nt * nz, nx, tb.tw_s[1], tb.sn_s[1], s)); }
+            launches += tb.dim >= 2 ? 2 : 1;
             if (tb.dim == 3) {
                 { Span sp_(p, "dst_z", s); CK(qbvm::launch_dst<double, double, 0, true>(work, work, tb.n[2], p->lp[2], nt, nx * ny, tb.tw_s[2], tb.sn_s[2], s)); }
                 ++launches;
@@ -321,8 +333,8 @@ int solve_fp64_dev(qbvm_plan_t* p, const double* in, double* y, int n0_only, cud
         // inverse DST (the (2/M) factors are in the time-solve constant)
         const long long lev = n0_only ? 1 : tb.nt;
         { Span sp_(p, "dst_x", s); CK(qbvm::launch_dst<double, double, 0, true>(y, y, tb.n[0], p->lp[0], lev * ny * nz, 1, tb.tw_s[0], tb.sn_s[0], s)); }
-        { Span sp_(p, "dst_y", s); CK(qbvm::launch_dst<double, double, 0, true>(y, y, tb.n[1], p->lp[1], lev * nz, nx, tb.tw_s[1], tb.sn_s[1], s)); }
-        launches += 2;
+        if (tb.dim >= 2) { Span sp_(p, "dst_y", s); CK(qbvm::launch_dst<double, double, 0, true>(y, y, tb.n[1], p->lp[1], lev * nz, nx, tb.tw_s[1], tb.sn_s[1], s)); }
+        launches += tb.dim >= 2 ? 2 : 1;
         if (tb.dim == 3) {
             { Span sp_(p, "dst_z", s); CK(qbvm::launch_dst<double, double, 0, true>(y, y, tb.n[2], p->lp[2], lev, nx * ny, tb.tw_s[2], tb.sn_s[2], s)); }
             ++launches;
@@ -489,6 +501,7 @@ int qbvm_plan(const qbvm_desc* desc, qbvm_plan_t** out) {
     const qbvm_desc& d = p->d;
     Tables& tb = p->tb;
     tb.dim = d.dim;
+    tb.sf = space_first(&d) ? 1 : 0;
     tb.nt = d.nt;
     tb.lnt = ilog2(d.nt);
     tb.Nx = 1;
@@ -520,7 +533,7 @@ int qbvm_plan(const qbvm_desc* desc, qbvm_plan_t** out) {
     std::vector<double2> tw64, gpow(H), gipw(H), gpowr(H), gipr(H), ak(H), bk;
     std::vector<float2> tw32;
     roots(H, tw64, tw32);
-    const double scale1d = d.dim == 1 ? p->h[0] * p->h[0] / nt : 1.0;
+    const double scale1d = !tb.sf ? p->h[0] * p->h[0] / nt : 1.0;   // time-first 1D: h^2 and 1/nt in gamma^t
     for (int t = 0; t < H; ++t) {
         double r = std::pow(mag, (double)t / nt);
         double a = M_PI * ((double)t / nt);
@@ -557,7 +570,7 @@ int qbvm_plan(const qbvm_desc* desc, qbvm_plan_t** out) {
     if (!rc) rc = upload(p, &tb.gipr32, to32(gipr));
     if (!rc) rc = upload(p, &tb.ak32, to32(ak));
     if (!rc && !is_pow2(nt)) rc = bluestein_tables(p, mag, scale1d);
-    if (!rc && d.dim == 1) {
+    if (!rc && !tb.sf) {
         const double h2 = p->h[0] * p->h[0];
         if (tb.gen) {                                     // every frequency k < nt
             bk.resize(nt);
@@ -573,7 +586,7 @@ int qbvm_plan(const qbvm_desc* desc, qbvm_plan_t** out) {
         }
         rc = upload(p, &tb.bk, bk);
     }
-    if (!rc && d.dim > 1) {
+    if (!rc && tb.sf) {
         // Dirichlet eigenvalues (4/h^2) sin^2(k pi/(2M)) per axis, summed per mode
         std::vector<std::vector<double>> lam(3);
         for (int i = 0; i < 3; ++i) {
@@ -614,13 +627,13 @@ int qbvm_plan(const qbvm_desc* desc, qbvm_plan_t** out) {
     }
     // ---- workspace ----
     const size_t total = (size_t)tb.Nx * nt;
-    if (!rc && d.dim == 1) {
+    if (!rc && !tb.sf) {
         rc = dalloc(p, &p->wk, total);
         if (!rc) rc = dalloc(p, &p->wcp, total);
     }
-    if (!rc && d.dim > 1) rc = dalloc(p, &p->ghat, (size_t)tb.Nx);
-    if (!rc && d.dim > 1 && tb.gen) rc = dalloc(p, &p->wk, total);      // Bluestein spectrum [nt][Nx]
-    if (!rc && d.dim > 1 && d.precision == QBVM_FP64 && !tb.gen) {
+    if (!rc && tb.sf) rc = dalloc(p, &p->ghat, (size_t)tb.Nx);
+    if (!rc && tb.sf && tb.gen) rc = dalloc(p, &p->wk, total);      // Bluestein spectrum [nt][Nx]
+    if (!rc && tb.sf && d.precision == QBVM_FP64 && !tb.gen) {
         // Step (b) reciprocals, once per plan
         rc = dalloc(p, &tb.qinv, (size_t)(nt / 2) * (size_t)tb.Nx);
         if (!rc && (qbvm::launch_make_qinv(tb, fp64_cnorm(p), tb.qinv, 0) != cudaSuccess ||
@@ -720,7 +733,7 @@ static int ensure_fp32(qbvm_plan_t* p) {
 
 static int solve_dev(qbvm_plan_t* p, const double* in, double* y, int n0_only, cudaStream_t s) {
     const bool refine = p->d.precision == QBVM_FP32_REFINE;
-    if (p->tb.dim > 1 && n0_only && (p->d.rhs_kind == QBVM_RHS_GENERAL || refine)) {
+    if (p->tb.sf && n0_only && (p->d.rhs_kind == QBVM_RHS_GENERAL || refine)) {
         int rc = ensure_wreal(p);
         if (rc) return rc;
     }

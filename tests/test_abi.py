@@ -50,15 +50,17 @@ BAD = [
     dict(dim=0), dict(dim=4), dict(m=(1, 8, 8)), dict(nt=1), dict(T=0.0), dict(T=float("nan")),
     dict(L=-1.0), dict(form=2), dict(precision=5), dict(rhs_kind=3),
     dict(alpha=0.0, delta=0.0), dict(alpha=-1.0, delta=-1.0), dict(alpha=float("inf")),
+    dict(order=3), dict(order=-1), dict(order=1),       # time-first exists in 1D only
 ]
 
 
 @pytest.mark.parametrize("change", BAD, ids=lambda c: ",".join(f"{k}={v}" for k, v in c.items()))
 def test_bad_descriptors_are_rejected_without_a_gpu(lib, change):
-    args = dict(dim=2, m=(16, 16, 1), L=1.0, T=0.1, nt=16, form=0, alpha=1e-3, delta=0.0, precision=0, rhs_kind=0)
+    args = dict(dim=2, m=(16, 16, 1), L=1.0, T=0.1, nt=16, form=0, alpha=1e-3, delta=0.0, precision=0, rhs_kind=0,
+                order=0)
     args.update(change)
     desc = Q.make_desc(args["dim"], args["m"], args["L"], args["T"], args["nt"], args["form"], args["alpha"],
-                       args["delta"], args["precision"], args["rhs_kind"])
+                       args["delta"], args["precision"], args["rhs_kind"], order=args["order"])
     with pytest.raises(Q.QbvmError) as ei:
         Q.qbvm_plan(desc)
     assert ei.value.code == -1
@@ -73,6 +75,13 @@ def test_unsupported_sizes(lib, change):
     args = dict(dim=2, m=(16, 16, 1), nt=16, precision=0)
     args.update(change)
     desc = Q.make_desc(2, args["m"], 1.0, 0.1, args["nt"], 0, 1e-3, 0.0, args["precision"])
+    with pytest.raises(Q.QbvmError) as ei:
+        Q.qbvm_plan(desc)
+    assert ei.value.code == -7
+
+
+def test_space_first_needs_a_dst_length(lib):
+    desc = Q.make_desc(1, (100,), 1.0, 0.1, 16, 0, 1e-3, order=Q.ORDER_SPACE_FIRST)
     with pytest.raises(Q.QbvmError) as ei:
         Q.qbvm_plan(desc)
     assert ei.value.code == -7

@@ -29,8 +29,9 @@ def _lib():
     Q.load_library()
 
 
-def gpu_solve(grid, form, alpha, rhs, rhs_kind, n0_only=False, precision=Q.FP64, host=False):
-    with Q.Plan(grid.dim, grid.M, grid.L, grid.T, grid.nt, form, alpha, 0.0, precision, rhs_kind) as plan:
+def gpu_solve(grid, form, alpha, rhs, rhs_kind, n0_only=False, precision=Q.FP64, host=False, order=Q.ORDER_AUTO):
+    with Q.Plan(grid.dim, grid.M, grid.L, grid.T, grid.nt, form, alpha, 0.0, precision, rhs_kind,
+                order=order) as plan:
         nout = grid.Nx * (1 if n0_only else grid.nt)
         if host:
             inp = np.ascontiguousarray(rhs, dtype=np.float64).ravel()
@@ -134,6 +135,25 @@ def test_general_nt_n0_only(grid, rhs_kind):
     full = gpu_solve(grid, Q.FORM_PQ, 1e-3, rhs, rhs_kind)
     y0 = gpu_solve(grid, Q.FORM_PQ, 1e-3, rhs, rhs_kind, n0_only=True)
     np.testing.assert_allclose(y0[0], full[0], rtol=0, atol=1e-13 * np.abs(full).max())
+
+
+@pytest.mark.parametrize("grid", [bi.Grid(1, (64,), 1.0, 0.1, 64), bi.Grid(1, (256,), math.pi, 1.0, 33),
+                                  bi.Grid(1, (1024,), math.pi, 1.0, 257), bi.Grid(1, (4,), 1.0, 0.1, 8)],
+                         ids=lambda g: f"M{g.M[0]}-nt{g.nt}")
+@pytest.mark.parametrize("order", [Q.ORDER_TIME_FIRST, Q.ORDER_SPACE_FIRST], ids=["time-first", "space-first"])
+@pytest.mark.parametrize("rhs_kind", [Q.RHS_DELTA, Q.RHS_GENERAL])
+def test_1d_both_orders_match_oracle(grid, order, rhs_kind):
+    """1D with m a power of two runs either order: the tridiagonal (Thomas)
+    solves of Section 3.3 after the time DFT, or the sine transform first."""
+    alpha = 1e-3
+    F = bi.random_general_rhs(grid, seed=15)
+    rhs = F[0] if rhs_kind == Q.RHS_DELTA else F
+    Ff = O.delta_rhs(grid, Q.FORM_PQ, alpha, F[0]) if rhs_kind == Q.RHS_DELTA else F
+    want = oracle_solve(grid, Q.FORM_PQ, alpha, Ff)
+    got = gpu_solve(grid, Q.FORM_PQ, alpha, rhs, rhs_kind, order=order)
+    assert O.rel_l2(got, want) <= TOL
+    y0 = gpu_solve(grid, Q.FORM_PQ, alpha, rhs, rhs_kind, n0_only=True, order=order)
+    np.testing.assert_allclose(y0[0], got[0], rtol=0, atol=1e-13 * np.abs(got).max())
 
 
 def test_general_nt_paper_table1_mesh():
