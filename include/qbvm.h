@@ -326,6 +326,46 @@ int qbvm_features_run(qbvm_features_t* feats_plan, const double* g, const double
                       float* feats, void* stream);
 int qbvm_features_destroy(qbvm_features_t* feats_plan);
 
+/* ------------------------------------------------------------------------
+ * The original QBVM / MQBVM systems (Section 2) by Krylov iteration with the
+ * PinT solve as preconditioner.  The paper solves them only by sparse direct
+ * LU and proposes the diagonalization-based PinT direct solver as a
+ * preconditioner for Krylov methods (Sections 2 and 6); this is that use.
+ *
+ * The systems (f = (g, 0, ..., 0), backward Euler rows for n >= 1 as in the
+ * PinT systems, first block row):
+ *   QBVM_ORIGINAL_QBVM  (A_h, eq. 2.3):  alpha y^0 + y^N = g;
+ *   QBVM_ORIGINAL_MQBVM (B_h, eq. 2.6):  (alpha/tau)(y^0 - y^1) + y^N = g.
+ * With the first block row of the PinT system scaled by tau*alpha (PQ) or
+ * alpha (PM) it reads alpha (I - tau Delta_h) y^0 + y^N = g or
+ * alpha (I/tau - Delta_h) y^0 + y^N = g, so the PinT operator differs from
+ * A_h / B_h in one block row only.  The iteration is flexible
+ * right-preconditioned GMRES(restart): each preconditioner application scales
+ * block 0 by 1/(tau alpha) (QBVM) or 1/alpha (MQBVM) and calls qbvm_solve;
+ * orthogonalisation is classical Gram-Schmidt applied twice.
+ *
+ * qbvm_gmres_create -- `plan` must be FP64, rhs_kind GENERAL and of the form
+ *   matching `method` (PQ for QBVM, PM for MQBVM); the handle borrows it (keep
+ *   it alive) and allocates (2 restart + 4) vectors of nt*N_x doubles.
+ *   restart in [1, 64].  Errors: BAD_ARG, UNSUPPORTED, OOM.
+ * qbvm_gmres_solve -- device pointers g (N_x values) and y (nt*N_x values,
+ *   output; the initial guess is zero).  Stops when ||f - A y||/||f|| <= tol
+ *   (the true residual, recomputed at the end) or after max_iters inner
+ *   iterations, or when a whole restart cycle lowers the true residual by less
+ *   than 10 % (its FP64 floor lies above tol: the original systems are far
+ *   worse conditioned than the PinT ones); *iters and *rel_residual report
+ *   (either may be NULL).
+ *   Synchronises `stream` once per iteration (the Hessenberg update runs on
+ *   the host).  Errors: BAD_ARG, DIVERGED (max_iters reached above tol; y holds
+ *   the last iterate), NONFINITE, CUDA. */
+#define QBVM_ORIGINAL_QBVM  0
+#define QBVM_ORIGINAL_MQBVM 1
+typedef struct qbvm_gmres qbvm_gmres_t;
+int qbvm_gmres_create(qbvm_plan_t* plan, int method, int restart, qbvm_gmres_t** out);
+int qbvm_gmres_solve(qbvm_gmres_t* gm, const double* g, double* y, double tol, int max_iters, int* iters,
+                     double* rel_residual, void* stream);
+int qbvm_gmres_destroy(qbvm_gmres_t* gm);
+
 /* qbvm_destroy -- free the plan and everything it owns (NULL is accepted). */
 int qbvm_destroy(qbvm_plan_t* plan);
 

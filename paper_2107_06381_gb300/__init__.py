@@ -27,6 +27,7 @@ FORM_PQ, FORM_PM = 0, 1
 FP64, FP32_REFINE = 0, 1
 RHS_DELTA, RHS_GENERAL = 0, 1
 ORDER_AUTO, ORDER_TIME_FIRST, ORDER_SPACE_FIRST = 0, 1, 2
+ORIGINAL_QBVM, ORIGINAL_MQBVM = 0, 1
 
 
 class QbvmDesc(ctypes.Structure):
@@ -111,6 +112,12 @@ def load_library(path: str | None = None) -> ctypes.CDLL:
     lib.qbvm_profile_read.restype = ip
     lib.qbvm_residual_noalloc.argtypes = [ctypes.POINTER(QbvmDesc), vp, vp, ctypes.POINTER(dp), vp]
     lib.qbvm_residual_noalloc.restype = ip
+    lib.qbvm_gmres_create.argtypes = [vp, ip, ip, ctypes.POINTER(vp)]
+    lib.qbvm_gmres_create.restype = ip
+    lib.qbvm_gmres_solve.argtypes = [vp, vp, vp, dp, ip, ctypes.POINTER(ip), ctypes.POINTER(dp), vp]
+    lib.qbvm_gmres_solve.restype = ip
+    lib.qbvm_gmres_destroy.argtypes = [vp]
+    lib.qbvm_gmres_destroy.restype = ip
     lib.qbvm_sweep_plan.argtypes = [ctypes.POINTER(QbvmSweepDesc), ctypes.POINTER(vp)]
     lib.qbvm_sweep_plan.restype = ip
     lib.qbvm_sweep_run.argtypes = [vp, vp]
@@ -489,6 +496,49 @@ class Features:
         if self.handle:
             load_library().qbvm_features_destroy(self.handle)
             self.handle = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+
+class GMRES:
+    """The original QBVM (method ORIGINAL_QBVM, A_h of eq. 2.3) or MQBVM
+    (ORIGINAL_MQBVM, B_h of eq. 2.6) system with f = (g, 0, ..., 0), solved by
+    flexible right-preconditioned GMRES(restart) with `plan`'s PinT solve as the
+    preconditioner.  `plan`: FP64, RHS_GENERAL, form PQ for QBVM / PM for MQBVM;
+    it must outlive this object."""
+
+    def __init__(self, plan: "Plan", method: int, restart: int = 20):
+        h = ctypes.c_void_p()
+        _check(load_library().qbvm_gmres_create(plan.handle, int(method), int(restart), ctypes.byref(h)),
+               "qbvm_gmres_create")
+        self.handle = h.value
+        self.plan = plan
+
+    def solve(self, g, y, tol=1e-12, max_iters=200, stream=None, raise_on_diverged=True):
+        """Returns (iterations, relative residual); raises QbvmError on DIVERGED
+        unless raise_on_diverged is False (y then holds the last iterate)."""
+        it = ctypes.c_int()
+        rel = ctypes.c_double()
+        code = load_library().qbvm_gmres_solve(self.handle, _ptr(g), _ptr(y), float(tol), int(max_iters),
+                                               ctypes.byref(it), ctypes.byref(rel), _stream(stream, g, y))
+        if not (code == -4 and not raise_on_diverged):
+            _check(code, "qbvm_gmres_solve")
+        return it.value, rel.value
+
+    def close(self):
+        if self.handle:
+            load_library().qbvm_gmres_destroy(self.handle)
+            self.handle = None
+
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *exc):
+        self.close()
 
     def __del__(self):
         try:

@@ -115,7 +115,17 @@ int dst_tile_lw(int lm);
 }  // namespace qbvm
 
 struct qbvm_desc;
+struct qbvm_plan;
 namespace qbvm {
 // The descriptor checks of qbvm_plan (status code; needs no GPU).
 int validate_desc(const qbvm_desc* d);
+// Read access to a plan's descriptor and tables for the other translation
+// units (the plan type itself is private to qbvm_plan.cu).
+struct PlanView {
+    const Tables* tb;
+    int form, precision, rhs_kind, dim;
+    double alpha, tau, h2inv[3];
+};
+int plan_view(const struct ::qbvm_plan* p, PlanView* out);
+
 }  // namespace qbvm

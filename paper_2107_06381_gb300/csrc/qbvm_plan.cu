@@ -470,6 +470,19 @@ int solve_fp32r_dev(qbvm_plan_t* p, const double* in, double* y, int n0_only, cu
 
 int qbvm::validate_desc(const qbvm_desc* d) { return validate(d); }
 
+int qbvm::plan_view(const struct ::qbvm_plan* p, PlanView* out) {
+    if (!p || !out) return QBVM_ERR_BAD_ARG;
+    out->tb = &p->tb;
+    out->form = p->d.form;
+    out->precision = p->d.precision;
+    out->rhs_kind = p->d.rhs_kind;
+    out->dim = p->d.dim;
+    out->alpha = p->alpha;
+    out->tau = p->tau;
+    for (int i = 0; i < 3; ++i) out->h2inv[i] = p->h2inv[i];
+    return QBVM_OK;
+}
+
 // ------------------------------------------------------------------ C ABI
 
 extern "C" {
@@ -482,7 +495,7 @@ const char* qbvm_strerror(int code) {
         case QBVM_ERR_BAD_ARG: return "invalid argument or descriptor";
         case QBVM_ERR_OOM: return "out of memory";
         case QBVM_ERR_NONFINITE: return "non-finite value in input or result";
-        case QBVM_ERR_DIVERGED: return "FP32 iterative refinement did not contract";
+        case QBVM_ERR_DIVERGED: return "iteration stopped above its tolerance (FP32 refinement or GMRES)";
         case QBVM_ERR_TIMEOUT: return "a bounded device wait gave up";
         case QBVM_ERR_CUDA: return "CUDA runtime error";
         case QBVM_ERR_UNSUPPORTED: return "size not implemented by the kernels";
