@@ -344,6 +344,43 @@ def our_arm(args, rank, world, device):
         for plan in rplans:
             plan.close()
 
+    # ---- y^0 only from the delta right-hand side (a separate metric: the
+    # forward time transform of f^0 e_0 is constant, so Step (c) at t = 0 is one
+    # factor per spatial mode; DSTs of one level around it)
+    y0m = None
+    if not args.refine_only:
+        y0plans = []
+        for form in forms:
+            alpha = prob.delta if form == Q.FORM_PQ else grid.tau * prob.delta
+            y0plans.append(Q.Plan(grid.dim, grid.M, grid.L, grid.T, grid.nt, form, alpha, 0.0, Q.FP64, Q.RHS_DELTA))
+        gdev = torch.as_tensor(np.ascontiguousarray(prob.g_delta).ravel(), dtype=torch.float64, device=device)
+        y0s = [torch.empty(grid.Nx, dtype=torch.float64, device=device) for _ in forms]
+        with torch.cuda.stream(stream):
+            for plan, yo in zip(y0plans, y0s):
+                plan.solve(gdev, yo, n0_only=True, stream=stream)
+        torch.cuda.synchronize(device)
+        nrep = 20
+        ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        with torch.cuda.stream(stream):
+            ev0.record(stream)
+            for _ in range(nrep):
+                for plan, yo in zip(y0plans, y0s):
+                    plan.solve(gdev, yo, n0_only=True, stream=stream)
+            ev1.record(stream)
+        torch.cuda.synchronize(device)
+        ms = ev0.elapsed_time(ev1) / (nrep * len(forms))
+        # against level 0 of the full delta-RHS solve
+        yfull = torch.empty(grid.unknowns, dtype=torch.float64, device=device)
+        y0plans[0].solve(gdev, yfull, stream=stream)
+        torch.cuda.synchronize(device)
+        diff = float((y0s[0] - yfull[:grid.Nx]).norm() / yfull[:grid.Nx].norm())
+        y0m = {"metric": "y0-only solves/sec, delta right-hand side (a separate metric, not the headline)",
+               "value": 1e3 / ms, "unit": "solves/s", "ms_per_solve": round(ms, 4),
+               "outputs_per_solve": grid.Nx, "rel_diff_vs_full_solve_level0": diff,
+               "kernels_per_solve": y0plans[0].info.kernels_per_solve}
+        for plan in y0plans:
+            plan.close()
+
     # ---- end to end through the C ABI with pinned host buffers
     host_in = [torch.empty(x.numel(), dtype=torch.float64, pin_memory=True) for x in inputs]
     host_out = [torch.empty(y.numel(), dtype=torch.float64, pin_memory=True) for y in outputs]
@@ -414,6 +451,7 @@ def our_arm(args, rank, world, device):
         "cpu_baseline": cpu,
         "rel_err_vs_oracle": rel_err,
         "fp32_refine": refine,
+        "y0_delta_rhs": y0m,
         **extra,
     }
     for plan in plans:

@@ -40,6 +40,7 @@ struct Tables {
     float*   lamtau32 = nullptr;
     double2* bk = nullptr;           // 1D Thomas diagonal for frequency 2m: h^2 d_{2m} / tau + 2
     double2* qinv = nullptr;         // FP64 2D/3D: cnorm / (d_{2m} + tau Lambda_l), [H][Nx]
+    double*  y0fac = nullptr;        // FP64 delta rhs: y^0_l = y0fac[l] * (DST g)_l (Step (c) at t = 0)
     // general nt (not a power of two): Bluestein tables, every frequency k < nt
     int gen = 0;                     // 1: the time DFTs use k_bluestein
     int lL = 0;                      // log2 L, L >= 2 nt - 1
@@ -68,6 +69,15 @@ cudaError_t launch_dst(const TIN* in, void* out, int n, int lm, long long outer,
 template <typename R>
 cudaError_t launch_time_solve(const R* in, R* out, const Tables& tb, double cnorm, int delta_rhs,
                               int n0_only, cudaStream_t s);
+
+// y0fac[l] = Re sum over the formed frequencies of cnorm / (d_k + tau Lambda_l)
+// (x2 for the half spectrum of a power-of-two nt): with the delta right-hand
+// side the forward time transform is the constant f^0, so Step (c) at t = 0
+// is this factor times the mode's coefficient.  Power-of-two nt: from tb.qinv;
+// other nt: direct FP64 divisions over every frequency.
+cudaError_t launch_make_y0fac(const Tables& tb, double cnorm, double* out, cudaStream_t s);
+// y[l] = fac[l] * x[l], l < n
+cudaError_t launch_mul_modes(const double* x, const double* fac, double* y, long long n, cudaStream_t s);
 
 // Time DFTs of length nt for a general nt (tb.gen): mode 0 = Step (a) + the
 // divide of Step (b) (real [nt][N] in, complex out), 1 = Step (a) only (1D),

@@ -427,6 +427,48 @@ cudaError_t launch_make_qinv(const Tables& tb, double cnorm, double2* q, cudaStr
     return cudaGetLastError();
 }
 
+__global__ void k_y0fac_pow2(const double2* __restrict__ q, int H, long long Nx, double* __restrict__ out) {
+    for (long long l = (long long)blockIdx.x * blockDim.x + threadIdx.x; l < Nx; l += (long long)gridDim.x * blockDim.x) {
+        double a = 0.0;
+        for (int m = 0; m < H; ++m) a += q[(long long)m * Nx + l].x;
+        out[l] = 2.0 * a;                                // the odd frequencies are the conjugates
+    }
+}
+
+__global__ void k_y0fac_gen(const double2* __restrict__ dk, const double* __restrict__ lamtau, double cnorm, int P,
+                            long long Nx, double* __restrict__ out) {
+    for (long long l = (long long)blockIdx.x * blockDim.x + threadIdx.x; l < Nx; l += (long long)gridDim.x * blockDim.x) {
+        double a = 0.0;
+        const double lt = lamtau[l];
+        for (int k = 0; k < P; ++k) {
+            const double zr = dk[k].x + lt, zi = dk[k].y;
+            a += cnorm * zr / (zr * zr + zi * zi);
+        }
+        out[l] = a;
+    }
+}
+
+__global__ void k_mul_modes(const double* __restrict__ x, const double* __restrict__ fac, double* __restrict__ y,
+                            long long n) {
+    for (long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (long long)gridDim.x * blockDim.x)
+        y[i] = fac[i] * x[i];
+}
+
+cudaError_t launch_make_y0fac(const Tables& tb, double cnorm, double* out, cudaStream_t s) {
+    long long blocks = (tb.Nx + 255) / 256;
+    if (blocks > 152 * 32) blocks = 152 * 32;
+    if (tb.gen) k_y0fac_gen<<<(unsigned)blocks, 256, 0, s>>>(tb.dk_full, tb.lamtau, cnorm, tb.nt, tb.Nx, out);
+    else k_y0fac_pow2<<<(unsigned)blocks, 256, 0, s>>>(tb.qinv, tb.nt / 2, tb.Nx, out);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_mul_modes(const double* x, const double* fac, double* y, long long n, cudaStream_t s) {
+    long long blocks = (n + 255) / 256;
+    if (blocks > 152 * 32) blocks = 152 * 32;
+    k_mul_modes<<<(unsigned)blocks, 256, 0, s>>>(x, fac, y, n);
+    return cudaGetLastError();
+}
+
 static int tile_lw(int lp, int tile = TILE_ELEMS) {
     int lw = 0;
     while (((1 << lp) << (lw + 1)) <= tile) ++lw;

@@ -302,7 +302,11 @@ int solve_fp64_dev(qbvm_plan_t* p, const double* in, double* y, int n0_only, cud
                 ++launches;
             }
             // f^0 = -omega g / tau: fold -omega/tau into the time-solve constant
-            if (tb.gen) {
+            if (n0_only && tb.y0fac) {
+                // y^0 only: Step (c) at t = 0 of a constant spectrum is one factor per mode
+                { Span sp_(p, "y0_modes", s); CK(qbvm::launch_mul_modes(p->ghat, tb.y0fac, y, tb.Nx, s)); }
+                launches += 1;
+            } else if (tb.gen) {
                 { Span sp_(p, "time_fwd", s); CK(qbvm::launch_bluestein(0, p->ghat, p->wk, tb.Nx, tb, -tb.omega * cn, 1, 0, s)); }
                 { Span sp_(p, "time_inv", s); CK(qbvm::launch_bluestein(2, p->wk, y, tb.Nx, tb, 0.0, 0, n0_only, s)); }
                 launches += 2;
@@ -650,6 +654,13 @@ int qbvm_plan(const qbvm_desc* desc, qbvm_plan_t** out) {
         // Step (b) reciprocals, once per plan
         rc = dalloc(p, &tb.qinv, (size_t)(nt / 2) * (size_t)tb.Nx);
         if (!rc && (qbvm::launch_make_qinv(tb, fp64_cnorm(p), tb.qinv, 0) != cudaSuccess ||
+                    cudaStreamSynchronize(0) != cudaSuccess))
+            rc = QBVM_ERR_CUDA;
+    }
+    if (!rc && tb.sf && d.precision == QBVM_FP64 && d.rhs_kind == QBVM_RHS_DELTA) {
+        // y^0-only fast mode of the delta right-hand side
+        rc = dalloc(p, &tb.y0fac, (size_t)tb.Nx);
+        if (!rc && (qbvm::launch_make_y0fac(tb, fp64_cnorm(p), tb.y0fac, 0) != cudaSuccess ||
                     cudaStreamSynchronize(0) != cudaSuccess))
             rc = QBVM_ERR_CUDA;
     }
