@@ -269,19 +269,24 @@ k_time_solve_ct(const R* in, R* out, long long Nx, const cplx<R>* __restrict__ t
 // owns, and the length-N2 DFTs give it the frequencies k1 + N1 k2.  After the
 // divide the inverse runs in mirror order (length-N2 DFTs over k2, twiddle,
 // transpose back, length-N1 DFTs over k1), which leaves each thread holding
-// exactly the time indices it loaded.  Loads and stores go straight between
-// global memory and registers (a warp reads 32/T consecutive modes of T rows).
-// With the delta right-hand side the forward transform of f^0 e_0 is the
-// constant f^0 and is not computed.
+// exactly the time indices it loaded.  A CTA takes TS_MODES consecutive modes:
+// the [nt][TS_MODES] tile is staged through shared memory with coalesced row
+// accesses (row stride RS chosen so that the threads' strided time reads are
+// bank-conflict free), and each mode's column is read and rewritten only by
+// its own threads.  With the delta right-hand side the forward transform of
+// f^0 e_0 is the constant f^0 and is not computed.
 template <int LH> struct TsCfg;
-template <> struct TsCfg<8> { static constexpr int N1 = 16, N2 = 16, BS = 17, FB = 272; };
-template <> struct TsCfg<7> { static constexpr int N1 = 16, N2 = 8, BS = 9, FB = 152; };
-template <> struct TsCfg<6> { static constexpr int N1 = 8, N2 = 8, BS = 9, FB = 72; };
-template <> struct TsCfg<5> { static constexpr int N1 = 8, N2 = 4, BS = 5, FB = 52; };
-constexpr int TS_MODES = 32;     // spatial modes per CTA
+template <> struct TsCfg<8> { static constexpr int N1 = 16, N2 = 16, BS = 17, FB = 272, RS = 18; };
+template <> struct TsCfg<7> { static constexpr int N1 = 16, N2 = 8, BS = 9, FB = 152, RS = 20; };
+template <> struct TsCfg<6> { static constexpr int N1 = 8, N2 = 8, BS = 9, FB = 72, RS = 20; };
+template <> struct TsCfg<5> { static constexpr int N1 = 8, N2 = 4, BS = 5, FB = 52, RS = 24; };
+constexpr int TS_MODES = 16;     // spatial modes per CTA
 
 template <int LH>
-constexpr size_t ts_reg_smem() { return (size_t)(4 * (1 << LH) + TS_MODES * TsCfg<LH>::FB) * sizeof(float2); }
+constexpr size_t ts_reg_smem() {
+    return (size_t)(4 * (1 << LH) + TS_MODES * TsCfg<LH>::FB) * sizeof(float2) +
+           (size_t)(2 << LH) * TsCfg<LH>::RS * sizeof(float);
+}
 
 template <int LH>
 __global__ void __launch_bounds__(TS_MODES * TsCfg<LH>::N2)
@@ -290,13 +295,15 @@ k_time_solve_reg(const float* in, float* out, long long Nx, const float2* __rest
                  const float* __restrict__ lamtau, float cnorm, float rho_h, float rho_hinv, int delta_rhs,
                  int n0_only) {
     using G = TsCfg<LH>;
-    constexpr int H = 1 << LH, N1 = G::N1, N2 = G::N2, T = N2, NTH = TS_MODES * T, Q = N1 / T;
+    constexpr int H = 1 << LH, NT = 2 * H, N1 = G::N1, N2 = G::N2, T = N2, NTH = TS_MODES * T, Q = N1 / T;
+    constexpr int RS = G::RS, RSTEP = NTH / TS_MODES;
     extern __shared__ __align__(16) unsigned char smem_raw[];
     float2* stw = reinterpret_cast<float2*>(smem_raw);
     float2* sgp = stw + H;
     float2* sgi = sgp + H;
     float2* sak = sgi + H;
     float2* fbuf = sak + H;
+    float* st = reinterpret_cast<float*>(fbuf + TS_MODES * G::FB);     // [NT][RS]
     const int tid = threadIdx.x;
     for (int i = tid; i < H; i += NTH) {
         stw[i] = tw[i];
@@ -304,33 +311,47 @@ k_time_solve_reg(const float* in, float* out, long long Nx, const float2* __rest
         sgi[i] = gipw[i];
         sak[i] = ak[i];
     }
+    const long long l0 = (long long)blockIdx.x * TS_MODES;
+    {   // load phase: rows of TS_MODES consecutive modes, a batch of loads in flight per thread
+        const int cc = tid % TS_MODES, r0 = tid / TS_MODES;
+        const bool ok = l0 + cc < Nx;
+        const float* src = in + l0 + cc;
+        const int rows = delta_rhs ? 1 : NT;
+        constexpr int BATCH = 16;
+        for (int rb = r0; rb < rows; rb += RSTEP * BATCH) {
+            float v[BATCH];
+#pragma unroll
+            for (int q = 0; q < BATCH; ++q) {
+                const int r = rb + q * RSTEP;
+                v[q] = (ok && r < rows) ? src[(long long)r * Nx] : 0.f;
+            }
+#pragma unroll
+            for (int q = 0; q < BATCH; ++q) {
+                const int r = rb + q * RSTEP;
+                if (r < rows) st[r * RS + cc] = v[q];
+            }
+        }
+    }
+    __syncthreads();
     const int c = tid / T, n2 = tid % T;
-    const long long l = (long long)blockIdx.x * TS_MODES + c;
+    const long long l = l0 + c;
     const bool ok = l < Nx;
     float2* buf = fbuf + c * G::FB;
     float2 X[Q][N2];
     if (delta_rhs) {
-        const float f0 = ok ? in[l] : 0.f;
+        const float f0 = st[c];
 #pragma unroll
         for (int q = 0; q < Q; ++q)
 #pragma unroll
             for (int k2 = 0; k2 < N2; ++k2) X[q][k2] = make_float2(f0, 0.f);
-        __syncthreads();
     } else {
-        float fa[N1], fh[N1];
-#pragma unroll
-        for (int n1 = 0; n1 < N1; ++n1) {
-            const long long n = N2 * n1 + n2;
-            fa[n1] = ok ? in[n * Nx + l] : 0.f;
-            fh[n1] = ok ? in[(n + H) * Nx + l] : 0.f;
-        }
-        __syncthreads();                                   // tables
         float2 v[N1];
 #pragma unroll
         for (int n1 = 0; n1 < N1; ++n1) {                  // gamma^t (f_t + i rho^H f_{t+H})
-            const float2 g = sgp[N2 * n1 + n2];
-            const float f1 = rho_h * fh[n1];
-            v[n1] = make_float2(fmaf(g.x, fa[n1], -g.y * f1), fmaf(g.y, fa[n1], g.x * f1));
+            const int n = N2 * n1 + n2;
+            const float2 g = sgp[n];
+            const float fa = st[n * RS + c], f1 = rho_h * st[(n + H) * RS + c];
+            v[n1] = make_float2(fmaf(g.x, fa, -g.y * f1), fmaf(g.y, fa, g.x * f1));
         }
         rd::rdft<N1, +1>(v);
 #pragma unroll
@@ -382,14 +403,21 @@ k_time_solve_reg(const float* in, float* out, long long Nx, const float2* __rest
 #pragma unroll
     for (int k1 = 0; k1 < N1; ++k1) w[k1] = buf[k1 * G::BS + n2];
     rd::rdft<N1, -1>(w);
-    if (!ok) return;
 #pragma unroll
-    for (int n1 = 0; n1 < N1; ++n1) {
+    for (int n1 = 0; n1 < N1; ++n1) {                      // outputs into this mode's own column
         const int n = N2 * n1 + n2;
-        if (n0_only && n != 0) continue;
         const float2 gi = sgi[n], qv = w[n1];
-        out[(long long)n * Nx + l] = fmaf(gi.x, qv.x, -gi.y * qv.y);
-        if (!n0_only) out[(long long)(n + H) * Nx + l] = rho_hinv * fmaf(gi.x, qv.y, gi.y * qv.x);
+        st[n * RS + c] = fmaf(gi.x, qv.x, -gi.y * qv.y);
+        st[(n + H) * RS + c] = rho_hinv * fmaf(gi.x, qv.y, gi.y * qv.x);
+    }
+    __syncthreads();
+    {   // store phase
+        const int cc = tid % TS_MODES, r0 = tid / TS_MODES;
+        if (l0 + cc < Nx) {
+            float* dst = out + l0 + cc;
+            const int rows = n0_only ? 1 : NT;
+            for (int r = r0; r < rows; r += RSTEP) dst[(long long)r * Nx] = st[r * RS + cc];
+        }
     }
 }
 
