@@ -282,11 +282,16 @@ template <> struct TsCfg<6> { static constexpr int N1 = 8, N2 = 8, BS = 9, FB = 
 template <> struct TsCfg<5> { static constexpr int N1 = 8, N2 = 4, BS = 5, FB = 52, RS = 24; };
 constexpr int TS_MODES = 16;     // spatial modes per CTA
 
+// The staging tile [nt][RS] and the per-mode transpose buffers share one
+// region: the tile is free between the first reads and the final writes.
 template <int LH>
-constexpr size_t ts_reg_smem() {
-    return (size_t)(4 * (1 << LH) + TS_MODES * TsCfg<LH>::FB) * sizeof(float2) +
-           (size_t)(2 << LH) * TsCfg<LH>::RS * sizeof(float);
+constexpr size_t ts_region_bytes() {
+    return (size_t)(2 << LH) * TsCfg<LH>::RS * sizeof(float) > (size_t)TS_MODES * TsCfg<LH>::FB * sizeof(float2)
+               ? (size_t)(2 << LH) * TsCfg<LH>::RS * sizeof(float)
+               : (size_t)TS_MODES * TsCfg<LH>::FB * sizeof(float2);
 }
+template <int LH>
+constexpr size_t ts_reg_smem() { return (size_t)4 * (1 << LH) * sizeof(float2) + ts_region_bytes<LH>(); }
 
 template <int LH>
 __global__ void __launch_bounds__(TS_MODES * TsCfg<LH>::N2)
@@ -302,8 +307,8 @@ k_time_solve_reg(const float* in, float* out, long long Nx, const float2* __rest
     float2* sgp = stw + H;
     float2* sgi = sgp + H;
     float2* sak = sgi + H;
-    float2* fbuf = sak + H;
-    float* st = reinterpret_cast<float*>(fbuf + TS_MODES * G::FB);     // [NT][RS]
+    float2* fbuf = sak + H;                                            // transpose buffers ...
+    float* st = reinterpret_cast<float*>(fbuf);                        // ... aliasing the tile [NT][RS]
     const int tid = threadIdx.x;
     for (int i = tid; i < H; i += NTH) {
         stw[i] = tw[i];
@@ -338,6 +343,7 @@ k_time_solve_reg(const float* in, float* out, long long Nx, const float2* __rest
     const bool ok = l < Nx;
     float2* buf = fbuf + c * G::FB;
     float2 X[Q][N2];
+    float2 v[N1];
     if (delta_rhs) {
         const float f0 = st[c];
 #pragma unroll
@@ -345,7 +351,6 @@ k_time_solve_reg(const float* in, float* out, long long Nx, const float2* __rest
 #pragma unroll
             for (int k2 = 0; k2 < N2; ++k2) X[q][k2] = make_float2(f0, 0.f);
     } else {
-        float2 v[N1];
 #pragma unroll
         for (int n1 = 0; n1 < N1; ++n1) {                  // gamma^t (f_t + i rho^H f_{t+H})
             const int n = N2 * n1 + n2;
@@ -353,6 +358,9 @@ k_time_solve_reg(const float* in, float* out, long long Nx, const float2* __rest
             const float fa = st[n * RS + c], f1 = rho_h * st[(n + H) * RS + c];
             v[n1] = make_float2(fmaf(g.x, fa, -g.y * f1), fmaf(g.y, fa, g.x * f1));
         }
+    }
+    __syncthreads();                                       // every column read: the tile becomes the buffers
+    if (!delta_rhs) {
         rd::rdft<N1, +1>(v);
 #pragma unroll
         for (int k1 = 1; k1 < N1; ++k1)
@@ -377,7 +385,9 @@ k_time_solve_reg(const float* in, float* out, long long Nx, const float2* __rest
         for (int k2 = 0; k2 < N2; ++k2) {
             const float2 a = sak[k1 + N1 * k2];
             const float zr = a.x + lt, zi = a.y;
-            const float inv = cnorm / fmaf(zr, zr, zi * zi);
+            // |d + tau Lambda|^2 lies far inside the fast division's range (2 ulp):
+            // this FP32 solve is the refinement's correction step
+            const float inv = __fdividef(cnorm, fmaf(zr, zr, zi * zi));
             const float2 u = X[q][k2];
             X[q][k2] = make_float2(fmaf(u.x, zr, u.y * zi) * inv, fmaf(u.y, zr, -u.x * zi) * inv);
         }
@@ -402,6 +412,7 @@ k_time_solve_reg(const float* in, float* out, long long Nx, const float2* __rest
     float2 w[N1];
 #pragma unroll
     for (int k1 = 0; k1 < N1; ++k1) w[k1] = buf[k1 * G::BS + n2];
+    __syncthreads();                                       // every buffer read: the region is the tile again
     rd::rdft<N1, -1>(w);
 #pragma unroll
     for (int n1 = 0; n1 < N1; ++n1) {                      // outputs into this mode's own column

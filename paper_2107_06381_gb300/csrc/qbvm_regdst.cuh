@@ -104,11 +104,18 @@ __host__ __device__ constexpr int staging_floats() {
     return XAX ? NCOL * Cfg<LM>::CS
                : ((1 << LM) - 1 + (((1 << LM) - 2) >> Cfg<LM>::LPAD) + 1) * Cfg<LM>::RS;
 }
-// Dynamic shared memory of one CTA: staging, per-DFT buffers, twiddles, sines.
+// The staging tile and the per-DFT buffers share one region: the tile is free
+// between the first reads and the output writes (CTA barriers at both ends).
+template <int LM, bool XAX>
+__host__ __device__ constexpr size_t region_bytes() {
+    return (size_t)staging_floats<LM, XAX>() * 4 > (size_t)NFFT * Cfg<LM>::FB * 8
+               ? (size_t)staging_floats<LM, XAX>() * 4
+               : (size_t)NFFT * Cfg<LM>::FB * 8;
+}
+// Dynamic shared memory of one CTA: the region, twiddles, sines.
 template <int LM, bool XAX>
 __host__ __device__ constexpr size_t smem_bytes() {
-    return (size_t)staging_floats<LM, XAX>() * 4 + (size_t)NFFT * Cfg<LM>::FB * 8 + (size_t)(1 << LM) * 8 +
-           (size_t)(((1 << (LM - 1)) + 1 + 3) & ~3) * 4;
+    return region_bytes<LM, XAX>() + (size_t)(1 << LM) * 8 + (size_t)(((1 << (LM - 1)) + 1 + 3) & ~3) * 4;
 }
 
 // Staging offset of element (column c, j' = j - 1) and of the pair (c, c+1) in YAX.
@@ -130,8 +137,8 @@ __device__ __forceinline__ void tile(const TIN* in, void* out, long long outer, 
     constexpr int N1 = G::N1, N2 = G::N2, T = N2, NTH = threads<LM>();
     constexpr int KP = H / T;                        // spectrum entries per thread in the blocked phase
     float* st = reinterpret_cast<float*>(smem_raw);
-    float2* fb = reinterpret_cast<float2*>(st + staging_floats<LM, XAX>());
-    float2* stw = fb + NFFT * G::FB;
+    float2* fb = reinterpret_cast<float2*>(smem_raw);                  // aliases the staging tile
+    float2* stw = reinterpret_cast<float2*>(smem_raw + region_bytes<LM, XAX>());
     float* ssn = reinterpret_cast<float*>(stw + M);
     const int tid = threadIdx.x;
 
@@ -236,6 +243,7 @@ __device__ __forceinline__ void tile(const TIN* in, void* out, long long outer, 
             v[n1] = make_float2(fmaf(s, x.x + m.x, 0.5f * (x.x - m.x)), fmaf(s, x.y + m.y, 0.5f * (x.y - m.y)));
         }
     }
+    __syncthreads();                              // every column read: the tile becomes the buffers
     rdft<N1, -1>(v);
 #pragma unroll
     for (int k1 = 1; k1 < N1; ++k1) {
@@ -294,6 +302,7 @@ __device__ __forceinline__ void tile(const TIN* in, void* out, long long outer, 
         }
     }
     const float oa = sa - pa, ob = sb - pb;
+    __syncthreads();                              // every spectrum read: the region is the tile again
     auto st2 = [&](int jp, float a, float b) {
         const int p = spos<LM, XAX>(ca, jp);
         if (XAX) {
