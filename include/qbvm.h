@@ -60,8 +60,10 @@ extern "C" {
 #define QBVM_FORM_PM 1            /* PinT-MQBVM, Section 3.2                    */
 
 #define QBVM_FP64        0        /* every stage in FP64                        */
-#define QBVM_FP32_REFINE 1        /* FP32 transforms, FP64 scaling tables, FP64
-                                     residual and update: iterative refinement */
+#define QBVM_FP32_REFINE 1        /* FP32 transforms (tables computed in FP64 and
+                                     rounded once), double-float residual and
+                                     iterate: iterative refinement.  Needs the
+                                     space-first order and a power-of-two nt. */
 
 #define QBVM_RHS_DELTA   0        /* input is g (one level): f^0 = -omega g/tau */
 #define QBVM_RHS_GENERAL 1        /* input is a full right-hand side F [nt][..] */

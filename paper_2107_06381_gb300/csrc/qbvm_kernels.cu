@@ -1210,14 +1210,16 @@ cudaError_t launch_residual_df(const void* y_df, const double* f, int delta_rhs,
     const bool eq = (tb.dim < 2 || h2inv[1] == h2inv[0]) && (tb.dim < 3 || h2inv[2] == h2inv[0]);
     const bool aligned = ((reinterpret_cast<uintptr_t>(y_df) | reinterpret_cast<uintptr_t>(f) |
                            reinterpret_cast<uintptr_t>(r_out)) & 15) == 0;
-    if (aligned && (tb.dim == 2 || tb.dim == 3)) {
+    if (aligned) {
         const long long groups = ((long long)tb.nt * tb.Nx + 3) / 4;
         long long nb = (groups + RES_THREADS - 1) / RES_THREADS;
         if (nb > nblocks) nb = nblocks;
         const float2* yy = reinterpret_cast<const float2*>(y_df);
         const double fs = -tb.omega * it;
         const int nx = tb.n[0], ny = tb.n[1], nz = tb.n[2];
-        if (tb.dim == 2) {
+        if (tb.dim == 1) {
+            k_residual_df4<true, 1><<<(unsigned)nb, RES_THREADS, 0, s>>>(yy, f, delta_rhs, tb.nt, nx, ny, nz, k, fs, r_out, partials);
+        } else if (tb.dim == 2) {
             if (eq) k_residual_df4<true, 2><<<(unsigned)nb, RES_THREADS, 0, s>>>(yy, f, delta_rhs, tb.nt, nx, ny, nz, k, fs, r_out, partials);
             else k_residual_df4<false, 2><<<(unsigned)nb, RES_THREADS, 0, s>>>(yy, f, delta_rhs, tb.nt, nx, ny, nz, k, fs, r_out, partials);
         } else {

@@ -86,8 +86,8 @@ int validate(const qbvm_desc* d) {
     }
     if (d->order < QBVM_ORDER_AUTO || d->order > QBVM_ORDER_SPACE_FIRST) return QBVM_ERR_BAD_ARG;
     if (d->order == QBVM_ORDER_TIME_FIRST && d->dim != 1) return QBVM_ERR_BAD_ARG;
-    if (d->precision == QBVM_FP32_REFINE && d->dim == 1) return QBVM_ERR_UNSUPPORTED;
     const bool sf = space_first(d);
+    if (d->precision == QBVM_FP32_REFINE && !sf) return QBVM_ERR_UNSUPPORTED;   // refinement runs space-first
     if (sf) {
         for (int i = 0; i < d->dim; ++i)
             if (!dst_length_ok(d->m[i])) return QBVM_ERR_UNSUPPORTED;
@@ -368,18 +368,18 @@ int fp32_solve(qbvm_plan_t* p, const void* rhs, int rhs_fp64, int delta, void* y
     float* w = p->f32;
     if (delta) {
         { Span sp_(p, "dst_x", s); CK(qbvm::launch_dst<float, double, 0>((const double*)rhs, p->g32, tb.n[0], p->lp[0], ny * nz, 1, tb.tw_s32[0], tb.sn_s32[0], s)); }
-        { Span sp_(p, "dst_y", s); CK(qbvm::launch_dst<float, float, 0>(p->g32, p->g32, tb.n[1], p->lp[1], nz, nx, tb.tw_s32[1], tb.sn_s32[1], s)); }
+        if (tb.dim >= 2) { Span sp_(p, "dst_y", s); CK(qbvm::launch_dst<float, float, 0>(p->g32, p->g32, tb.n[1], p->lp[1], nz, nx, tb.tw_s32[1], tb.sn_s32[1], s)); }
         if (tb.dim == 3) { Span sp_(p, "dst_z", s); CK(qbvm::launch_dst<float, float, 0>(p->g32, p->g32, tb.n[2], p->lp[2], 1, nx * ny, tb.tw_s32[2], tb.sn_s32[2], s)); }
         { Span sp_(p, "time_solve", s); CK(qbvm::launch_time_solve<float>(p->g32, w, tb, -tb.omega * cn, 1, 0, s)); }
     } else {
         if (rhs_fp64) { Span sp_(p, "dst_x", s); CK(qbvm::launch_dst<float, double, 0>((const double*)rhs, w, tb.n[0], p->lp[0], nt * ny * nz, 1, tb.tw_s32[0], tb.sn_s32[0], s)); }
         else { Span sp_(p, "dst_x", s); CK(qbvm::launch_dst<float, float, 0>((const float*)rhs, w, tb.n[0], p->lp[0], nt * ny * nz, 1, tb.tw_s32[0], tb.sn_s32[0], s)); }
-        { Span sp_(p, "dst_y", s); CK(qbvm::launch_dst<float, float, 0>(w, w, tb.n[1], p->lp[1], nt * nz, nx, tb.tw_s32[1], tb.sn_s32[1], s)); }
+        if (tb.dim >= 2) { Span sp_(p, "dst_y", s); CK(qbvm::launch_dst<float, float, 0>(w, w, tb.n[1], p->lp[1], nt * nz, nx, tb.tw_s32[1], tb.sn_s32[1], s)); }
         if (tb.dim == 3) { Span sp_(p, "dst_z", s); CK(qbvm::launch_dst<float, float, 0>(w, w, tb.n[2], p->lp[2], nt, nx * ny, tb.tw_s32[2], tb.sn_s32[2], s)); }
         { Span sp_(p, "time_solve", s); CK(qbvm::launch_time_solve<float>(w, w, tb, tb.tau * cn, 0, 0, s)); }
     }
     if (tb.dim == 3) { Span sp_(p, "dst_z", s); CK(qbvm::launch_dst<float, float, 0>(w, w, tb.n[2], p->lp[2], nt, nx * ny, tb.tw_s32[2], tb.sn_s32[2], s)); }
-    { Span sp_(p, "dst_y", s); CK(qbvm::launch_dst<float, float, 0>(w, w, tb.n[1], p->lp[1], nt * nz, nx, tb.tw_s32[1], tb.sn_s32[1], s)); }
+    if (tb.dim >= 2) { Span sp_(p, "dst_y", s); CK(qbvm::launch_dst<float, float, 0>(w, w, tb.n[1], p->lp[1], nt * nz, nx, tb.tw_s32[1], tb.sn_s32[1], s)); }
     if (accumulate) {
         Span sp_(p, "dst_x", s);
         CK(qbvm::launch_dst<float, float, 1>(w, ydf, tb.n[0], p->lp[0], nt * ny * nz, 1, tb.tw_s32[0], tb.sn_s32[0], s));
@@ -415,7 +415,7 @@ int solve_fp32r_dev(qbvm_plan_t* p, const double* in, double* y, int n0_only, cu
     const int maxit = p->d.refine_max_iters > 0 ? p->d.refine_max_iters : 10;
     int rc = fp32_solve(p, in, 1, delta, yfull, 0, s);
     if (rc) return rc;
-    const int launches_solve = tb.dim == 3 ? 7 : 5;
+    const int launches_solve = 2 * tb.dim + 1;
     int launches = launches_solve;
     double rel = 0.0, prev = INFINITY;
     int it = 0;
@@ -762,7 +762,7 @@ static int solve_dev(qbvm_plan_t* p, const double* in, double* y, int n0_only, c
         if (rc) return rc;
     }
     if (!refine) return solve_fp64_dev(p, in, y, n0_only, s);
-    if (p->tb.dim == 1) return QBVM_ERR_UNSUPPORTED;
+    if (!p->tb.sf) return QBVM_ERR_UNSUPPORTED;
     int rc = ensure_fp32(p);
     if (rc) return rc;
     if (p->d.rhs_kind == QBVM_RHS_GENERAL) {

@@ -80,6 +80,14 @@ def test_unsupported_sizes(lib, change):
     assert ei.value.code == -7
 
 
+def test_fp32_refinement_needs_the_space_first_order(lib):
+    for m, order in (((100,), Q.ORDER_AUTO), ((64,), Q.ORDER_TIME_FIRST)):
+        desc = Q.make_desc(1, m, 1.0, 0.1, 16, 0, 1e-3, 0.0, Q.FP32_REFINE, order=order)
+        with pytest.raises(Q.QbvmError) as ei:
+            Q.qbvm_plan(desc)
+        assert ei.value.code == -7
+
+
 def test_space_first_needs_a_dst_length(lib):
     desc = Q.make_desc(1, (100,), 1.0, 0.1, 16, 0, 1e-3, order=Q.ORDER_SPACE_FIRST)
     with pytest.raises(Q.QbvmError) as ei:

