@@ -166,6 +166,28 @@ def test_general_nt_paper_table1_mesh():
     assert O.rel_l2(got, want) <= TOL
 
 
+# the largest size along each axis that the plan accepts
+MAX_SIZES = [
+    bi.Grid(2, (1024, 1024), 1.0, 0.1, 8),       # largest DST length
+    bi.Grid(2, (16, 16), 1.0, 0.1, 1024),        # largest power-of-two nt
+    bi.Grid(2, (8, 8), 1.0, 0.1, 2047),          # largest Bluestein nt (2048 is a power of two: 1024 is that limit)
+    bi.Grid(3, (256, 256, 16), 1.0, 0.05, 4),
+    bi.Grid(1, (16385,), 1.0, 0.1, 4),           # long 1D, time-first (m not a power of two)
+]
+
+
+@pytest.mark.parametrize("grid", MAX_SIZES, ids=lambda g: f"d{g.dim}-M{'x'.join(map(str, g.M))}-nt{g.nt}")
+def test_maximum_sizes_match_oracle(grid):
+    alpha = 1e-3
+    F = bi.random_general_rhs(grid, seed=16)
+    want = O.solve_sparse_lu(grid, Q.FORM_PQ, alpha, F) if grid.dim == 1 else O.solve_spectral(grid, Q.FORM_PQ, alpha, F)
+    got = gpu_solve(grid, Q.FORM_PQ, alpha, F, Q.RHS_GENERAL)
+    assert O.rel_l2(got, want) <= TOL
+    if grid.dim > 1 and grid.nt <= 1024 and (grid.nt & (grid.nt - 1)) == 0:
+        got32 = gpu_solve(grid, Q.FORM_PQ, alpha, F, Q.RHS_GENERAL, precision=Q.FP32_REFINE)
+        assert O.rel_l2(got32, want) <= TOL
+
+
 @pytest.mark.parametrize("form", [Q.FORM_PQ, Q.FORM_PM])
 def test_c1_workload(form):
     """1D, 63 interior points x 64 levels, alpha by the Section 5 rule."""
