@@ -233,7 +233,8 @@ int qbvm_residual_noalloc(const qbvm_desc* desc, const double* y, const double* 
  * thread, CTAs per SM) is picked by qbvm_sweep_autotune.
  * Supported: dim 1 or 2; m a power of two in [4, 2048]; nt a power of two in
  * [2, 1024]; n_alpha in [1, 64].  precision: QBVM_FP64 (every stage in FP64)
- * or QBVM_FP32_REFINE (the alpha scan in FP32, the picked alpha's y^0 in FP64).
+ * or QBVM_FP32_REFINE (the alpha scan in FP32; the picked alpha's y^0 summed in
+ * double-float, about 2^-44 per term, and the DSTs in FP64).
  * The sweep holds device copies of its tables; g, z0 and y0 are caller-owned
  * device arrays that must stay valid while the sweep is used. */
 typedef struct qbvm_sweep_instance {

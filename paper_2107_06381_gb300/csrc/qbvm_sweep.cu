@@ -59,6 +59,7 @@ struct SwInst {
     const double* lamy;          // tau * lambda_y (ny), 2D
     const double2* dtab;         // n_alpha x H: d_{2m}(alpha)
     const float2* dtab32;
+    const float4* dtabdf;        // the same as double-float pairs (re.hi, re.lo, im.hi, im.lo)
     const double* cn;            // n_alpha: 2 * cnorm(alpha)
     const double* coef;          // n_alpha: alpha (PQ) or alpha / tau (PM)
     const double* alphas;        // n_alpha
@@ -145,7 +146,10 @@ __device__ void spectral_tile(const SwInst& I, int tile, unsigned char* smem) {
 #pragma unroll
             for (int q = 0; q < MPT; ++q) {
                 R zr = d.x + lam[q];
-                s[q] += zr / (zr * zr + d.y * d.y);
+                if (std::is_same<R, float>::value)      // the FP32 scan: the 2-ulp fast division
+                    s[q] += __fdividef((float)zr, fmaf((float)zr, (float)zr, (float)(d.y * d.y)));
+                else
+                    s[q] += zr / (zr * zr + d.y * d.y);
             }
         }
         const R cna = R(I.cn[a]);
@@ -199,6 +203,12 @@ __device__ void pick_alpha(const SwInst& I) {
 }
 
 // Stage D: FP64 spectral y^0 at the picked alpha for one tile of modes.
+// Stage D: y^0 in the sine basis at the picked alpha, Step (c) at t = 0:
+// sum over the even frequencies of Re 1/(d_{2m} + tau Lambda_l).  FP64 for the
+// FP64 sweep; for the FP32 sweep in double-float on the FP32 pipes (each term
+// to about 2^-44: |z|^2 in double-float, one fast division and one correction
+// step), since FP64 sums cost the FP64 pipe ~16 operations per term.
+template <typename R>
 __device__ void final_tile(const SwInst& I, int tile) {
     const int a = __ldcg(I.pick);
     const long long l = (long long)tile * SW_THREADS + threadIdx.x;
@@ -206,13 +216,47 @@ __device__ void final_tile(const SwInst& I, int tile) {
     const int lx = (int)(l % I.nx), ly = (int)(l / I.nx);
     const double lt = I.lamx[lx] + (I.dim == 2 ? I.lamy[ly] : 0.0);
     double s = 0.0;
-    const double2* dt = I.dtab + (long long)a * I.H;
-    for (int m = 0; m < I.H; ++m) {
-        double2 d = dt[m];
-        double zr = d.x + lt;
-        s += zr / fma(zr, zr, d.y * d.y);
+    if (std::is_same<R, double>::value) {
+        const double2* dt = I.dtab + (long long)a * I.H;
+        for (int m = 0; m < I.H; ++m) {
+            double2 d = dt[m];
+            double zr = d.x + lt;
+            s += zr / fma(zr, zr, d.y * d.y);
+        }
+    } else {
+        const float4* dt = I.dtabdf + (long long)a * I.H;
+        const qbvm::dfloat ltd = qbvm::df_from_double(lt);
+        qbvm::dfloat acc = {0.f, 0.f};
+        for (int m = 0; m < I.H; ++m) {
+            const float4 d = dt[m];
+            const qbvm::dfloat zr = qbvm::df_add_sloppy(qbvm::dfloat{d.x, d.y}, ltd), zi = {d.z, d.w};
+            const qbvm::dfloat den = qbvm::df_add_sloppy(qbvm::df_mul(zr, zr), qbvm::df_mul(zi, zi));
+            const float q1 = __fdividef(zr.hi, den.hi);
+            const qbvm::dfloat r = qbvm::df_add_sloppy(zr, qbvm::df_neg(qbvm::df_mul(den, qbvm::dfloat{q1, 0.f})));
+            const float q2 = __fdividef(r.hi, den.hi);
+            acc = qbvm::df_add_sloppy(acc, qbvm::df_fast_two_sum(q1, q2));
+        }
+        s = qbvm::df_to_double(acc);
     }
     I.yhat[l] = I.cn[a] * __ldcg(I.ghat + l) * s;
+}
+
+// Each stage out of line: the persistent kernel's register budget is then set
+// per stage rather than by the union of all of them inlined into one body.
+template <bool LDCG>
+__device__ __noinline__ void dst_stage(const double* in, double* out, int n, int lm, long long outer,
+                                       long long inner, long long tile, const double2* tw, const double* sn,
+                                       unsigned char* smem) {
+    qbvm::dst_tile<double, double, 0, qbvm::DST_TILE / 4 / SW_THREADS, LDCG>(in, out, n, lm, qbvm::dst_lw(lm), outer,
+                                                                            inner, tile, tw, sn, smem);
+}
+template <typename R, int MPT>
+__device__ __noinline__ void spectral_stage(const SwInst& I, int tile, unsigned char* smem) {
+    spectral_tile<R, MPT>(I, tile, smem);
+}
+template <typename R>
+__device__ __noinline__ void final_stage(const SwInst& I, int tile) {
+    final_tile<R>(I, tile);
 }
 
 struct SwRun {
@@ -225,7 +269,7 @@ struct SwRun {
 };
 
 template <typename R, int MPT>
-__global__ void __launch_bounds__(SW_THREADS) k_sweep(SwRun run) {
+__global__ void __launch_bounds__(SW_THREADS, 2) k_sweep(SwRun run) {
     extern __shared__ __align__(16) unsigned char smem[];
     __shared__ int s_item;
     __shared__ SwInst I;
@@ -259,31 +303,25 @@ __global__ void __launch_bounds__(SW_THREADS) k_sweep(SwRun run) {
         if (!ok) return;
         switch (w.x) {
             case ST_GX:       // x-DST of g, one level: rows = ny
-                qbvm::dst_tile<double, double, 0, qbvm::DST_TILE / 4 / SW_THREADS, false>(
-                    I.g, I.ghat, I.nx, I.lmx, qbvm::dst_lw(I.lmx), I.ny, 1, w.z, I.twx, I.snx, smem);
+                dst_stage<false>(I.g, I.ghat, I.nx, I.lmx, I.ny, 1, w.z, I.twx, I.snx, smem);
                 break;
             case ST_GY:
-                qbvm::dst_tile<double, double, 0, qbvm::DST_TILE / 4 / SW_THREADS, true>(
-                    I.ghat, I.ghat, I.ny, I.lmy, qbvm::dst_lw(I.lmy), 1, I.nx, w.z, I.twy, I.sny, smem);
+                dst_stage<true>(I.ghat, I.ghat, I.ny, I.lmy, 1, I.nx, w.z, I.twy, I.sny, smem);
                 break;
             case ST_ZX:
-                qbvm::dst_tile<double, double, 0, qbvm::DST_TILE / 4 / SW_THREADS, false>(
-                    I.z0, I.zhat, I.nx, I.lmx, qbvm::dst_lw(I.lmx), I.ny, 1, w.z, I.twx, I.snx, smem);
+                dst_stage<false>(I.z0, I.zhat, I.nx, I.lmx, I.ny, 1, w.z, I.twx, I.snx, smem);
                 break;
             case ST_ZY:
-                qbvm::dst_tile<double, double, 0, qbvm::DST_TILE / 4 / SW_THREADS, true>(
-                    I.zhat, I.zhat, I.ny, I.lmy, qbvm::dst_lw(I.lmy), 1, I.nx, w.z, I.twy, I.sny, smem);
+                dst_stage<true>(I.zhat, I.zhat, I.ny, I.lmy, 1, I.nx, w.z, I.twy, I.sny, smem);
                 break;
-            case ST_SPEC: spectral_tile<R, MPT>(I, w.z, smem); break;
+            case ST_SPEC: spectral_stage<R, MPT>(I, w.z, smem); break;
             case ST_PICK: pick_alpha(I); break;
-            case ST_FIN: final_tile(I, w.z); break;
+            case ST_FIN: final_stage<R>(I, w.z); break;
             case ST_IY:
-                qbvm::dst_tile<double, double, 0, qbvm::DST_TILE / 4 / SW_THREADS, true>(
-                    I.yhat, I.yhat, I.ny, I.lmy, qbvm::dst_lw(I.lmy), 1, I.nx, w.z, I.twy, I.sny, smem);
+                dst_stage<true>(I.yhat, I.yhat, I.ny, I.lmy, 1, I.nx, w.z, I.twy, I.sny, smem);
                 break;
             case ST_IX:
-                qbvm::dst_tile<double, double, 0, qbvm::DST_TILE / 4 / SW_THREADS, true>(
-                    I.yhat, I.y0, I.nx, I.lmx, qbvm::dst_lw(I.lmx), I.ny, 1, w.z, I.twx, I.snx, smem);
+                dst_stage<true>(I.yhat, I.y0, I.nx, I.lmx, I.ny, 1, w.z, I.twx, I.snx, smem);
                 break;
             default: break;
         }
@@ -552,7 +590,7 @@ int qbvm_sweep_plan(const qbvm_sweep_desc* d, qbvm_sweep_t** out) {
         std::memcpy(arena.data() + off, src, bytes);
         return off;
     };
-    struct Offs { size_t lamx, lamy, dtab, dtab32, cn, coef, al, twx, twy, snx, sny, gh, zh, yh; };
+    struct Offs { size_t lamx, lamy, dtab, dtab32, dtabdf, cn, coef, al, twx, twy, snx, sny, gh, zh, yh; };
     std::vector<Offs> offs(d->count);
     std::vector<std::pair<int, std::pair<size_t, size_t>>> dst_cache;   // M -> (tw, sn) offsets
     auto dst_tables = [&](int M) {
@@ -620,6 +658,7 @@ int qbvm_sweep_plan(const qbvm_sweep_desc* d, qbvm_sweep_t** out) {
             }
         std::vector<double2> dtab((size_t)na * I.H);
         std::vector<float2> dtab32((size_t)na * I.H);
+        std::vector<float4> dtabdf((size_t)na * I.H);
         std::vector<double> cn(na), coef(na), al(na);
         const double rule = in.alpha_base > 0 ? in.alpha_base
                                               : (in.form == QBVM_FORM_PQ ? in.delta : I.tau * in.delta);   // Section 5
@@ -635,6 +674,10 @@ int qbvm_sweep_plan(const qbvm_sweep_desc* d, qbvm_sweep_t** out) {
                 double2 v = make_double2(1.0 - g1 * std::cos(ang), -g1 * std::sin(ang));
                 dtab[(size_t)a * I.H + m] = v;
                 dtab32[(size_t)a * I.H + m] = make_float2((float)v.x, (float)v.y);
+                float rh, rl, ih, il;
+                qbvm::qbvm_split_d(v.x, &rh, &rl);
+                qbvm::qbvm_split_d(v.y, &ih, &il);
+                dtabdf[(size_t)a * I.H + m] = make_float4(rh, rl, ih, il);
             }
             // 2 cnorm with cnorm = -omega * prod(2/M) / nt (the delta right-hand side)
             cn[a] = 2.0 * (-omega) * I.zscale / in.nt;
@@ -645,6 +688,7 @@ int qbvm_sweep_plan(const qbvm_sweep_desc* d, qbvm_sweep_t** out) {
         o.lamy = put(ly.data(), ly.size() * sizeof(double));
         o.dtab = put(dtab.data(), dtab.size() * sizeof(double2));
         o.dtab32 = put(dtab32.data(), dtab32.size() * sizeof(float2));
+        o.dtabdf = put(dtabdf.data(), dtabdf.size() * sizeof(float4));
         o.cn = put(cn.data(), cn.size() * sizeof(double));
         o.coef = put(coef.data(), coef.size() * sizeof(double));
         o.al = put(al.data(), al.size() * sizeof(double));
@@ -668,6 +712,7 @@ int qbvm_sweep_plan(const qbvm_sweep_desc* d, qbvm_sweep_t** out) {
         I.lamy = reinterpret_cast<const double*>(tab + o.lamy);
         I.dtab = reinterpret_cast<const double2*>(tab + o.dtab);
         I.dtab32 = reinterpret_cast<const float2*>(tab + o.dtab32);
+        I.dtabdf = reinterpret_cast<const float4*>(tab + o.dtabdf);
         I.cn = reinterpret_cast<const double*>(tab + o.cn);
         I.coef = reinterpret_cast<const double*>(tab + o.coef);
         I.alphas = reinterpret_cast<const double*>(tab + o.al);
