@@ -674,10 +674,9 @@ int qbvm_sweep_plan(const qbvm_sweep_desc* d, qbvm_sweep_t** out) {
                 double2 v = make_double2(1.0 - g1 * std::cos(ang), -g1 * std::sin(ang));
                 dtab[(size_t)a * I.H + m] = v;
                 dtab32[(size_t)a * I.H + m] = make_float2((float)v.x, (float)v.y);
-                float rh, rl, ih, il;
-                qbvm::qbvm_split_d(v.x, &rh, &rl);
-                qbvm::qbvm_split_d(v.y, &ih, &il);
-                dtabdf[(size_t)a * I.H + m] = make_float4(rh, rl, ih, il);
+                // on the host the plain casts (the device uses an integer split of the same value)
+                const float rh = (float)v.x, ih = (float)v.y;
+                dtabdf[(size_t)a * I.H + m] = make_float4(rh, (float)(v.x - (double)rh), ih, (float)(v.y - (double)ih));
             }
             // 2 cnorm with cnorm = -omega * prod(2/M) / nt (the delta right-hand side)
             cn[a] = 2.0 * (-omega) * I.zscale / in.nt;
