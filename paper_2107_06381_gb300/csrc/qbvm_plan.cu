@@ -4,6 +4,7 @@
 // Section 5), builds the FP64 tables of the diagonalisation of Section 3.3
 // on the host, uploads them, and owns the device workspace.  qbvm_solve
 // enqueues the three steps of eq. 3.8 on the caller's stream.
+#include <algorithm>
 #include <cmath>
 #include <cstdio>
 #include <cstdlib>
@@ -37,6 +38,9 @@ struct qbvm_plan {
     // FP32 refinement workspace
     float* f32 = nullptr;         // [nt][Nx] FP32 work array (and the residual's r.hi)
     double* fcopy = nullptr;      // FP32_REFINE: copy of an F that aliases y
+    // host-pointer solves: a copy stream and events that pipeline the staging
+    cudaStream_t copy_stream = nullptr;
+    std::vector<cudaEvent_t> copy_events;
     float* g32 = nullptr;         // Nx FP32 (delta rhs)
     long long ws_bytes = 0;
     int last_iters = 0;
@@ -198,6 +202,8 @@ int bluestein_tables(qbvm_plan_t* p, double mag, double scale1d) {
 
 void destroy_plan(qbvm_plan_t* p) {
     if (!p) return;
+    for (cudaEvent_t e : p->copy_events) cudaEventDestroy(e);
+    if (p->copy_stream) cudaStreamDestroy(p->copy_stream);
     for (void* v : p->allocs) cudaFree(v);
     for (auto& m : p->marks) {
         cudaEventDestroy(m.a);
@@ -272,6 +278,43 @@ double fp64_cnorm(const qbvm_plan_t* p) {
     return p->d.rhs_kind == QBVM_RHS_DELTA ? -p->tb.omega * cn : p->tb.tau * cn;
 }
 
+// FP64 space-first solve in three phases, so that the host-pointer path can
+// overlap its copies with the per-level DSTs.
+// DST-I along every axis of the levels [l0, l1) of [nt][Nx] arrays, in -> out.
+int fp64_dst_levels(qbvm_plan_t* p, const double* in, double* out, long long l0, long long l1, cudaStream_t s,
+                    int* launches) {
+    const Tables& tb = p->tb;
+    const long long nx = tb.n[0], ny = tb.n[1], nz = tb.n[2], lev = l1 - l0, off = l0 * tb.Nx;
+    { Span sp_(p, "dst_x", s); CK(qbvm::launch_dst<double, double, 0, true>(in + off, out + off, tb.n[0], p->lp[0], lev * ny * nz, 1, tb.tw_s[0], tb.sn_s[0], s)); }
+    if (tb.dim >= 2) { Span sp_(p, "dst_y", s); CK(qbvm::launch_dst<double, double, 0, true>(out + off, out + off, tb.n[1], p->lp[1], lev * nz, nx, tb.tw_s[1], tb.sn_s[1], s)); }
+    if (tb.dim == 3) { Span sp_(p, "dst_z", s); CK(qbvm::launch_dst<double, double, 0, true>(out + off, out + off, tb.n[2], p->lp[2], lev, nx * ny, tb.tw_s[2], tb.sn_s[2], s)); }
+    *launches += tb.dim;
+    return QBVM_OK;
+}
+
+// Steps (a)-(c) in time for every spatial mode: the sine-basis spectrum `spec`
+// (one level for the delta right-hand side, [nt][Nx] otherwise) -> y.
+int fp64_time_part(qbvm_plan_t* p, const double* spec, double* y, int delta, int n0_only, cudaStream_t s,
+                   int* launches) {
+    const Tables& tb = p->tb;
+    const double cn = fp64_cn(tb);
+    // f^0 = -omega g / tau: fold -omega/tau into the time-solve constant
+    const double cnorm = delta ? -tb.omega * cn : tb.tau * cn;
+    if (delta && n0_only && tb.y0fac) {
+        // y^0 only: Step (c) at t = 0 of a constant spectrum is one factor per mode
+        { Span sp_(p, "y0_modes", s); CK(qbvm::launch_mul_modes(spec, tb.y0fac, y, tb.Nx, s)); }
+        *launches += 1;
+    } else if (tb.gen) {
+        { Span sp_(p, "time_fwd", s); CK(qbvm::launch_bluestein(0, spec, p->wk, tb.Nx, tb, cnorm, delta, 0, s)); }
+        { Span sp_(p, "time_inv", s); CK(qbvm::launch_bluestein(2, p->wk, y, tb.Nx, tb, 0.0, 0, n0_only, s)); }
+        *launches += 2;
+    } else {
+        { Span sp_(p, "time_solve", s); CK(qbvm::launch_time_solve<double>(spec, y, tb, cnorm, delta, n0_only, s)); }
+        *launches += 1;
+    }
+    return QBVM_OK;
+}
+
 int solve_fp64_dev(qbvm_plan_t* p, const double* in, double* y, int n0_only, cudaStream_t s) {
     const Tables& tb = p->tb;
     const int delta = p->d.rhs_kind == QBVM_RHS_DELTA;
@@ -289,60 +332,20 @@ int solve_fp64_dev(qbvm_plan_t* p, const double* in, double* y, int n0_only, cud
         { Span sp_(p, "time_inv_1d", s); CK(qbvm::launch_time_inv_1d(p->wk, y, tb, n0_only, s)); }
         launches = 3;
     } else {
-        const long long nx = tb.n[0], ny = tb.n[1], nz = tb.n[2];
-        const double cn = fp64_cn(tb);
-        double* work;
         if (delta) {
-            // DST of g along x, y (, z) -> ghat, then the time solve reads level 0
-            { Span sp_(p, "dst_x", s); CK(qbvm::launch_dst<double, double, 0, true>(in, p->ghat, tb.n[0], p->lp[0], ny * nz, 1, tb.tw_s[0], tb.sn_s[0], s)); }
-            if (tb.dim >= 2) { Span sp_(p, "dst_y", s); CK(qbvm::launch_dst<double, double, 0, true>(p->ghat, p->ghat, tb.n[1], p->lp[1], nz, nx, tb.tw_s[1], tb.sn_s[1], s)); }
-            launches += tb.dim >= 2 ? 2 : 1;
-            if (tb.dim == 3) {
-                { Span sp_(p, "dst_z", s); CK(qbvm::launch_dst<double, double, 0, true>(p->ghat, p->ghat, tb.n[2], p->lp[2], 1, nx * ny, tb.tw_s[2], tb.sn_s[2], s)); }
-                ++launches;
-            }
-            // f^0 = -omega g / tau: fold -omega/tau into the time-solve constant
-            if (n0_only && tb.y0fac) {
-                // y^0 only: Step (c) at t = 0 of a constant spectrum is one factor per mode
-                { Span sp_(p, "y0_modes", s); CK(qbvm::launch_mul_modes(p->ghat, tb.y0fac, y, tb.Nx, s)); }
-                launches += 1;
-            } else if (tb.gen) {
-                { Span sp_(p, "time_fwd", s); CK(qbvm::launch_bluestein(0, p->ghat, p->wk, tb.Nx, tb, -tb.omega * cn, 1, 0, s)); }
-                { Span sp_(p, "time_inv", s); CK(qbvm::launch_bluestein(2, p->wk, y, tb.Nx, tb, 0.0, 0, n0_only, s)); }
-                launches += 2;
-            } else {
-                { Span sp_(p, "time_solve", s); CK(qbvm::launch_time_solve<double>(p->ghat, y, tb, -tb.omega * cn, 1, n0_only, s)); }
-                ++launches;
-            }
-            work = y;
+            // DST of g along every axis -> ghat, then the time part reads level 0
+            int rc = fp64_dst_levels(p, in, p->ghat, 0, 1, s, &launches);
+            if (!rc) rc = fp64_time_part(p, p->ghat, y, 1, n0_only, s, &launches);
+            if (rc) return rc;
         } else {
-            work = n0_only ? p->wreal : y;
-            const long long nt = tb.nt;
-            { Span sp_(p, "dst_x", s); CK(qbvm::launch_dst<double, double, 0, true>(in, work, tb.n[0], p->lp[0], nt * ny * nz, 1, tb.tw_s[0], tb.sn_s[0], s)); }
-            if (tb.dim >= 2) { Span sp_(p, "dst_y", s); CK(qbvm::launch_dst<double, double, 0, true>(work, work, tb.n[1], p->lp[1], nt * nz, nx, tb.tw_s[1], tb.sn_s[1], s)); }
-            launches += tb.dim >= 2 ? 2 : 1;
-            if (tb.dim == 3) {
-                { Span sp_(p, "dst_z", s); CK(qbvm::launch_dst<double, double, 0, true>(work, work, tb.n[2], p->lp[2], nt, nx * ny, tb.tw_s[2], tb.sn_s[2], s)); }
-                ++launches;
-            }
-            if (tb.gen) {
-                { Span sp_(p, "time_fwd", s); CK(qbvm::launch_bluestein(0, work, p->wk, tb.Nx, tb, tb.tau * cn, 0, 0, s)); }
-                { Span sp_(p, "time_inv", s); CK(qbvm::launch_bluestein(2, p->wk, y, tb.Nx, tb, 0.0, 0, n0_only, s)); }
-                launches += 2;
-            } else {
-                { Span sp_(p, "time_solve", s); CK(qbvm::launch_time_solve<double>(work, y, tb, tb.tau * cn, 0, n0_only, s)); }
-                ++launches;
-            }
+            double* work = n0_only ? p->wreal : y;
+            int rc = fp64_dst_levels(p, in, work, 0, tb.nt, s, &launches);
+            if (!rc) rc = fp64_time_part(p, work, y, 0, n0_only, s, &launches);
+            if (rc) return rc;
         }
         // inverse DST (the (2/M) factors are in the time-solve constant)
-        const long long lev = n0_only ? 1 : tb.nt;
-        { Span sp_(p, "dst_x", s); CK(qbvm::launch_dst<double, double, 0, true>(y, y, tb.n[0], p->lp[0], lev * ny * nz, 1, tb.tw_s[0], tb.sn_s[0], s)); }
-        if (tb.dim >= 2) { Span sp_(p, "dst_y", s); CK(qbvm::launch_dst<double, double, 0, true>(y, y, tb.n[1], p->lp[1], lev * nz, nx, tb.tw_s[1], tb.sn_s[1], s)); }
-        launches += tb.dim >= 2 ? 2 : 1;
-        if (tb.dim == 3) {
-            { Span sp_(p, "dst_z", s); CK(qbvm::launch_dst<double, double, 0, true>(y, y, tb.n[2], p->lp[2], lev, nx * ny, tb.tw_s[2], tb.sn_s[2], s)); }
-            ++launches;
-        }
+        int rc = fp64_dst_levels(p, y, y, 0, n0_only ? 1 : tb.nt, s, &launches);
+        if (rc) return rc;
     }
     p->kernels_per_solve = launches;
     return QBVM_OK;
@@ -781,6 +784,67 @@ static int solve_dev(qbvm_plan_t* p, const double* in, double* y, int n0_only, c
     return solve_fp32r_dev(p, in, y, n0_only, s);
 }
 
+// Host-pointer FP64 space-first solve with the copies overlapped: chunks of
+// time levels go host -> device on the copy stream while the DSTs of the
+// chunks already there run on the caller's stream; after the time part each
+// chunk's inverse DSTs are followed by its device -> host copy, again on the
+// copy stream.  Events order the two streams; the caller's stream ends after
+// the last copy.  (Overlap needs pinned host memory; pageable memory still
+// gives the right answer.)
+constexpr int HOST_CHUNKS = 8;
+
+static int solve_fp64_host(qbvm_plan_t* p, const double* hin, double* hout, int n0_only, cudaStream_t s) {
+    const Tables& tb = p->tb;
+    const long long Nx = tb.Nx, nt = tb.nt;
+    const int delta = p->d.rhs_kind == QBVM_RHS_DELTA;
+    if (!p->copy_stream) {
+        CK(cudaStreamCreateWithFlags(&p->copy_stream, cudaStreamNonBlocking));
+        p->copy_events.resize(2 * HOST_CHUNKS + 2);
+        for (auto& e : p->copy_events) CK(cudaEventCreateWithFlags(&e, cudaEventDisableTiming));
+    }
+    cudaStream_t cs = p->copy_stream;
+    cudaEvent_t* ev = p->copy_events.data();
+    // chunks start at even levels: the x-DST packs rows in pairs from its first
+    // row, so the pairs (and the rounding) are those of the whole-array pass
+    const int nch = nt >= 2 * HOST_CHUNKS ? HOST_CHUNKS : 1;
+    auto lev0 = [&](int c) { return c == nch ? nt : ((nt * c / nch) & ~1LL); };
+    double *din = p->stage_in, *dy = p->stage_out;
+    int launches = 0, rc = QBVM_OK;
+    CK(cudaEventRecord(ev[2 * HOST_CHUNKS], s));            // the copies start after the caller's work
+    CK(cudaStreamWaitEvent(cs, ev[2 * HOST_CHUNKS], 0));
+    if (delta) {
+        CK(cudaMemcpyAsync(din, hin, sizeof(double) * Nx, cudaMemcpyHostToDevice, s));
+        rc = fp64_dst_levels(p, din, p->ghat, 0, 1, s, &launches);
+        if (!rc) rc = fp64_time_part(p, p->ghat, dy, 1, n0_only, s, &launches);
+    } else {
+        double* work = n0_only ? p->wreal : dy;
+        for (int c = 0; c < nch && !rc; ++c) {
+            const long long a = lev0(c), b = lev0(c + 1);
+            CK(cudaMemcpyAsync(din + a * Nx, hin + a * Nx, sizeof(double) * (b - a) * Nx, cudaMemcpyHostToDevice, cs));
+            CK(cudaEventRecord(ev[c], cs));
+            CK(cudaStreamWaitEvent(s, ev[c], 0));
+            rc = fp64_dst_levels(p, din, work, a, b, s, &launches);
+        }
+        if (!rc) rc = fp64_time_part(p, work, dy, 0, n0_only, s, &launches);
+    }
+    if (rc) return rc;
+    const int nco = n0_only ? 1 : nch;
+    for (int c = 0; c < nco && !rc; ++c) {
+        const long long a = n0_only ? 0 : lev0(c), b = n0_only ? 1 : lev0(c + 1);
+        rc = fp64_dst_levels(p, dy, dy, a, b, s, &launches);
+        if (rc) break;
+        CK(cudaEventRecord(ev[HOST_CHUNKS + c], s));
+        CK(cudaStreamWaitEvent(cs, ev[HOST_CHUNKS + c], 0));
+        CK(cudaMemcpyAsync(hout + a * Nx, dy + a * Nx, sizeof(double) * (b - a) * Nx, cudaMemcpyDeviceToHost, cs));
+    }
+    if (rc) return rc;
+    CK(cudaEventRecord(ev[2 * HOST_CHUNKS + 1], cs));
+    CK(cudaStreamWaitEvent(s, ev[2 * HOST_CHUNKS + 1], 0));
+    CK(cudaStreamSynchronize(s));
+    p->kernels_per_solve = launches;
+    return QBVM_OK;
+}
+
 int qbvm_solve(qbvm_plan_t* p, const double* g_or_F, double* y, int n0_only, void* stream) {
     if (!p || !g_or_F || !y) return QBVM_ERR_BAD_ARG;
     cudaStream_t s = static_cast<cudaStream_t>(stream);
@@ -790,6 +854,11 @@ int qbvm_solve(qbvm_plan_t* p, const double* g_or_F, double* y, int n0_only, voi
     // host pointers: stage through plan buffers
     int rc = ensure_stage(p);
     if (rc) return rc;
+    if (p->d.precision == QBVM_FP64 && p->tb.sf) {
+        if (n0_only && p->d.rhs_kind == QBVM_RHS_GENERAL) rc = ensure_wreal(p);
+        if (rc) return rc;
+        return solve_fp64_host(p, g_or_F, y, n0_only, s);
+    }
     const size_t nin = (size_t)p->tb.Nx * (p->d.rhs_kind == QBVM_RHS_DELTA ? 1 : p->tb.nt);
     const size_t nout = (size_t)p->tb.Nx * (n0_only ? 1 : p->tb.nt);
     CK(cudaMemcpyAsync(p->stage_in, g_or_F, nin * sizeof(double), cudaMemcpyHostToDevice, s));
