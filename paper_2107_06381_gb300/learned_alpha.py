@@ -27,7 +27,7 @@ from dataclasses import dataclass
 
 import numpy as np
 
-from . import FORM_PQ, FP32_REFINE, FP64, MLP, Features, Sweep
+from . import FORM_PQ, FP32_REFINE, MLP, Features, Sweep
 
 N_ALPHA = 32
 LOG_LO, LOG_HI = -2.0, 2.0
@@ -153,10 +153,11 @@ def evaluate(mlp: MLP, count: int, seed: int, chunk: int = 4096, M: int = 128, n
         t_pred = predict(mlp, feats)
         alpha_rule = delta                      # PinT-QBVM, Section 5
         t0 = time.perf_counter()
+        # one-alpha y^0 solves: the sweep's FP32 mode sums y^0 in double-float (~1e-13)
         _, _, _, err_l, _ = _sweep_chunk(torch, grid, z0, gd, delta, 1, 0.0, 0.0,
-                                         alpha_base=alpha_rule * 10.0 ** t_pred, precision=FP64)
+                                         alpha_base=alpha_rule * 10.0 ** t_pred, precision=FP32_REFINE)
         times["one_alpha_s"] += time.perf_counter() - t0
-        _, _, _, err_r, _ = _sweep_chunk(torch, grid, z0, gd, delta, 1, 0.0, 0.0, precision=FP64)
+        _, _, _, err_r, _ = _sweep_chunk(torch, grid, z0, gd, delta, 1, 0.0, 0.0, precision=FP32_REFINE)
         res["learned"].append(err_l[:, 0])
         res["rule"].append(err_r[:, 0])
         res["morozov"].append(err[np.arange(b), pick[:, 0]])
