@@ -433,6 +433,7 @@ def our_arm(args, rank, world, device):
     if not args.no_extra and not args.refine_only:
         extra["c3_3d"] = c3_leg(args, device, stream, flush, rank == 0 and world == 1 and not args.no_cpu_baseline)
         extra["c4_sweep"] = c4_leg(args, device, stream)
+        extra["c1_batched"] = c1_batched_leg(args, device, stream, flush)
 
     out = {
         "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
@@ -551,6 +552,55 @@ def c4_leg(args, device, stream):
                          "config": {"modes_per_thread": cfg.modes_per_thread, "ctas_per_sm": cfg.ctas_per_sm,
                                     "grid": cfg.grid},
                          "graph_launches_per_run": 1, "kernel_launches_per_run": 1}
+    return out
+
+
+def c1_batched_leg(args, device, stream, flush, count=10_000):
+    """The 1D problem (63 interior points x 64 levels, T = 0.1, z0 = sin(pi x) +
+    0.5 sin(3 pi x), multiplicative uniform noise eps = 1e-3) as a batch of
+    `count` instances with their own noise draw and alpha = their own delta
+    (PinT-QBVM, Section 5), full y of every instance: one qbvm_solve_batched
+    call = 3 kernel launches for the whole batch."""
+    import numpy as np
+    import torch
+    import bhcp_inputs as bi
+    import paper_2107_06381_gb300 as Q
+    base = bi.make_c1()
+    grid = base.grid
+    rng = np.random.default_rng(101)
+    g = base.g[None, :] * (1.0 + 1e-3 * rng.uniform(-1.0, 1.0, size=(count, grid.Nx)))
+    alphas = np.sqrt(grid.h[0]) * np.linalg.norm(g - base.g[None, :], axis=1)      # grid-weighted delta
+    gd = torch.as_tensor(g.ravel(), dtype=torch.float64, device=device)
+    y = torch.empty(count * grid.unknowns, dtype=torch.float64, device=device)
+    out = {"workload": f"c1_1d_63x64_batch{count}_delta_rhs", "instances": count,
+           "unknowns_per_batch": count * grid.unknowns}
+    with Q.Batch(1, grid.M, grid.L, grid.T, grid.nt, Q.FORM_PQ, alphas=list(alphas), rhs_kind=Q.RHS_DELTA) as bt:
+        steps = max(3, args.steps // 2)
+        evs = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(steps)]
+        with torch.cuda.stream(stream):
+            for _ in range(3):
+                bt.solve(gd, y, stream=stream)
+            for i in range(steps):
+                evs[i][0].record(stream)
+                bt.solve(gd, y, stream=stream)
+                evs[i][1].record(stream)
+                flush.zero_()
+        torch.cuda.synchronize()
+        ms = sum(a.elapsed_time(b) for a, b in evs) / steps
+        # two instances against single-instance plans (the same kernels, one instance each)
+        diffs = []
+        for b in (0, count - 1):
+            with Q.Plan(1, grid.M, grid.L, grid.T, grid.nt, Q.FORM_PQ, float(alphas[b]), 0.0, Q.FP64,
+                        Q.RHS_DELTA) as plan:
+                one = torch.empty(grid.unknowns, dtype=torch.float64, device=device)
+                plan.solve(gd[b * grid.Nx:(b + 1) * grid.Nx].contiguous(), one)
+                torch.cuda.synchronize()
+                mine = y[b * grid.unknowns:(b + 1) * grid.unknowns]
+                diffs.append(float((mine - one).norm() / one.norm()))
+    out.update({"ms_per_batch": ms, "value": count * grid.unknowns / (ms / 1e3), "unit": UNIT,
+                "solves_per_s": count / (ms / 1e3), "kernel_launches_per_batch": 3,
+                "rel_diff_vs_single_instance_plans": max(diffs),
+                "l2": "flushed between batches; output 322 MB"})
     return out
 
 

@@ -214,6 +214,31 @@ int qbvm_residual_noalloc(const qbvm_desc* desc, const double* y, const double* 
                           double* rel_norm_out, void* stream);
 
 /* ------------------------------------------------------------------------
+ * Batched solve: `count` instances of ONE shape, each with its own alpha.
+ * `desc` fixes everything but alpha (dim, m, L, T, nt, form, rhs_kind,
+ * order; precision must be QBVM_FP64); `alphas` is a host array of `count`
+ * values (NULL: desc's alpha, or its a-priori rule, for every instance), and
+ * each alpha gives its instance's omega (-1/alpha for PinT-QBVM, -tau/alpha
+ * for PinT-MQBVM, eqs. 3.3 / 3.6).  The instances are stored back to back in
+ * device memory: g_or_F is [count][Nx] (delta right-hand side) or
+ * [count][nt][Nx]; y is [count][nt][Nx], or [count][Nx] with n0_only.  Every
+ * stage of Section 3.3 runs once over the whole batch -- the DST-I passes
+ * over count*nt levels, the time solve over every (instance, mode tile) with
+ * the instance's own omega tables -- so a batch costs the launches of one
+ * solve, whatever `count` is.  Asynchronous on `stream`.
+ * Supported: space-first order (2D/3D; 1D with m a power of two), nt a power
+ * of two <= 1024, device pointers.  The batch owns its tables ([count][nt/2]
+ * omega factors and [count][nt/2][Nx] Step (b) reciprocals) and a base plan.
+ * Errors: BAD_ARG (count < 1, an alpha not finite and positive, host
+ * pointers), UNSUPPORTED, OOM, CUDA. */
+typedef struct qbvm_batch qbvm_batch_t;
+int qbvm_batch_plan(const qbvm_desc* desc, int count, const double* alphas, qbvm_batch_t** out);
+int qbvm_solve_batched(qbvm_batch_t* batch, const double* g_or_F, double* y, int n0_only, void* stream);
+/* alphas: host [count] (may be NULL); unknowns_per_instance = nt * Nx (may be NULL). */
+int qbvm_batch_info(const qbvm_batch_t* batch, double* alphas, long long* unknowns_per_instance);
+int qbvm_batch_destroy(qbvm_batch_t* batch);
+
+/* ------------------------------------------------------------------------
  * Batched regularisation-parameter sweep.  Many PinT-QBVM / PinT-MQBVM
  * instances of uneven size (1D or 2D, delta right-hand side f^0 = -omega g/tau),
  * each solved for n_alpha values of alpha log-spaced around the a-priori rule

@@ -19,7 +19,7 @@ __all__ = [
     "qbvm_profile_enable", "qbvm_profile_read", "qbvm_residual_noalloc",
     "qbvm_strerror", "qbvm_version", "Plan", "Sweep", "QbvmSweepInstance", "QbvmSweepDesc", "QbvmSweepConfig",
     "qbvm_sweep_plan", "qbvm_sweep_run", "qbvm_sweep_read", "qbvm_sweep_autotune", "qbvm_sweep_set_config",
-    "qbvm_sweep_get_config", "qbvm_sweep_destroy", "MLP", "Features",
+    "qbvm_sweep_get_config", "qbvm_sweep_destroy", "MLP", "Features", "Batch", "GMRES",
     "FORM_PQ", "FORM_PM", "FP64", "FP32_REFINE", "RHS_DELTA", "RHS_GENERAL",
 ]
 
@@ -118,6 +118,14 @@ def load_library(path: str | None = None) -> ctypes.CDLL:
     lib.qbvm_gmres_solve.restype = ip
     lib.qbvm_gmres_destroy.argtypes = [vp]
     lib.qbvm_gmres_destroy.restype = ip
+    lib.qbvm_batch_plan.argtypes = [ctypes.POINTER(QbvmDesc), ip, ctypes.POINTER(dp), ctypes.POINTER(vp)]
+    lib.qbvm_batch_plan.restype = ip
+    lib.qbvm_solve_batched.argtypes = [vp, vp, vp, ip, vp]
+    lib.qbvm_solve_batched.restype = ip
+    lib.qbvm_batch_info.argtypes = [vp, ctypes.POINTER(dp), ctypes.POINTER(ctypes.c_longlong)]
+    lib.qbvm_batch_info.restype = ip
+    lib.qbvm_batch_destroy.argtypes = [vp]
+    lib.qbvm_batch_destroy.restype = ip
     lib.qbvm_sweep_plan.argtypes = [ctypes.POINTER(QbvmSweepDesc), ctypes.POINTER(vp)]
     lib.qbvm_sweep_plan.restype = ip
     lib.qbvm_sweep_run.argtypes = [vp, vp]
@@ -532,6 +540,56 @@ class GMRES:
     def close(self):
         if self.handle:
             load_library().qbvm_gmres_destroy(self.handle)
+            self.handle = None
+
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *exc):
+        self.close()
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+
+class Batch:
+    """`len(alphas)` same-shape instances solved together (qbvm_solve_batched):
+    inputs and outputs stored back to back, [count][Nx] or [count][nt][Nx]
+    (device arrays).  alphas=None with count=B uses the descriptor's alpha
+    (or its a-priori rule from delta) for all B instances."""
+
+    def __init__(self, dim, m, L, T, nt, form=FORM_PQ, alphas=None, count=None, alpha=0.0, delta=0.0,
+                 rhs_kind=RHS_DELTA, order=0):
+        self.desc = make_desc(dim, m, L, T, nt, form, alpha, delta, FP64, rhs_kind, 0.0, 0, order)
+        if alphas is not None:
+            arr = (ctypes.c_double * len(alphas))(*[float(a) for a in alphas])
+            n = len(alphas)
+        else:
+            if count is None:
+                raise ValueError("give alphas or count")
+            arr, n = None, int(count)
+        h = ctypes.c_void_p()
+        _check(load_library().qbvm_batch_plan(ctypes.byref(self.desc), n, arr, ctypes.byref(h)), "qbvm_batch_plan")
+        self.handle = h.value
+        self.count = n
+
+    def solve(self, g_or_F, y, n0_only=False, stream=None):
+        _check(load_library().qbvm_solve_batched(self.handle, _ptr(g_or_F), _ptr(y), int(bool(n0_only)),
+                                                 _stream(stream, g_or_F, y)), "qbvm_solve_batched")
+        return y
+
+    @property
+    def alphas(self):
+        out = (ctypes.c_double * self.count)()
+        _check(load_library().qbvm_batch_info(self.handle, out, None), "qbvm_batch_info")
+        return list(out)
+
+    def close(self):
+        if self.handle:
+            load_library().qbvm_batch_destroy(self.handle)
             self.handle = None
 
     def __enter__(self):

@@ -70,6 +70,16 @@ template <typename R>
 cudaError_t launch_time_solve(const R* in, R* out, const Tables& tb, double cnorm, int delta_rhs,
                               int n0_only, cudaStream_t s);
 
+// The FP64 time solve of `count` same-shape instances stored back to back
+// (instance b: in + b in_stride -> out + b out_stride), each with its own
+// omega tables gpow, gipw, gpowr, gipr ([count][nt/2]) and Step (b)
+// reciprocals qinv ([count][nt/2][Nx], the constant cnorm folded in); the
+// shape tables (time roots, Nx, nt) are tb's.  Power-of-two nt.
+cudaError_t launch_time_solve_batched(const double* in, double* out, const Tables& tb, long long count,
+                                      long long in_stride, long long out_stride, const double2* gpow,
+                                      const double2* gipw, const double2* gpowr, const double2* gipr,
+                                      const double2* qinv, int delta_rhs, int n0_only, cudaStream_t s);
+
 // y0fac[l] = Re sum over the formed frequencies of cnorm / (d_k + tau Lambda_l)
 // (x2 for the half spectrum of a power-of-two nt): with the delta right-hand
 // side the forward time transform is the constant f^0, so Step (c) at t = 0
@@ -129,6 +139,10 @@ struct qbvm_plan;
 namespace qbvm {
 // The descriptor checks of qbvm_plan (status code; needs no GPU).
 int validate_desc(const qbvm_desc* d);
+// The FP64 space-first time-solve constant without its right-hand-side
+// factor: prod_d 2/(n_d + 1) (inverse DST-I) / nt (inverse DFT) / 4^dim per
+// forward-inverse DST pair (the 4x transform).
+double time_cn(const Tables& tb);
 // Read access to a plan's descriptor and tables for the other translation
 // units (the plan type itself is private to qbvm_plan.cu).
 struct PlanView {

@@ -171,13 +171,13 @@ __device__ __forceinline__ void time_solve_tile(const R* in, R* out, long long N
                                                 const R* __restrict__ lamtau, R cnorm,
                                                 const cplx<R>* __restrict__ gpowr, const cplx<R>* __restrict__ gipr,
                                                 const cplx<R>* __restrict__ qinv, int delta_rhs, int n0_only,
-                                                unsigned char* smem_raw) {
+                                                long long tile, unsigned char* smem_raw) {
     using C = cplx<R>;
     const int H = 1 << lh, W = 1 << lw;
     C* buf = reinterpret_cast<C*>(smem_raw);
     C* stw = buf + (H << lw);
     const int tid = threadIdx.x, nth = blockDim.x;
-    const long long l0 = (long long)blockIdx.x * W;
+    const long long l0 = tile * W;
 
     for (int i = tid; i < H; i += nth) stw[i] = tw[i];
     for (int e = tid; e < (H << lw); e += nth) {
@@ -244,7 +244,7 @@ k_time_solve(const R* in, R* out, long long Nx, int lh, int lw, const cplx<R>* _
              int delta_rhs, int n0_only) {
     extern __shared__ __align__(16) unsigned char smem_raw[];
     time_solve_tile<R, MAXB4>(in, out, Nx, lh, lw, tw, gpow, gipw, ak, lamtau, cnorm, gpowr, gipr, qinv, delta_rhs,
-                              n0_only, smem_raw);
+                              n0_only, (long long)blockIdx.x, smem_raw);
 }
 
 // Compile-time half length LH and tile width LW (H * W = 4 * MAXB4 * TILE_THREADS).
@@ -258,7 +258,29 @@ k_time_solve_ct(const R* in, R* out, long long Nx, const cplx<R>* __restrict__ t
     extern __shared__ __align__(16) unsigned char smem_raw[];
     constexpr int LT = (MAXB4 == 4 ? 12 : MAXB4 == 2 ? 11 : 10);     // log2 of the tile size
     time_solve_tile<R, MAXB4>(in, out, Nx, LH, LT - LH, tw, gpow, gipw, ak, lamtau, cnorm, gpowr, gipr, qinv,
-                              delta_rhs, n0_only, smem_raw);
+                              delta_rhs, n0_only, (long long)blockIdx.x, smem_raw);
+}
+
+// The FP64 time solve of `count` instances of one shape stored back to back
+// (instance b reads in + b in_stride and writes out + b out_stride), each with
+// its own omega: gpow, gipw, gpowr, gipr are [count][H] and qinv [count][H][Nx].
+// Block = b * tiles + mode tile.  The tile is W = 2^lw modes wide (at most
+// the single-instance width, fewer when Nx is small); LH < 0: lh is taken at
+// run time.
+template <int MAXB4, int LH>
+__global__ void __launch_bounds__(TILE_THREADS)
+k_time_solve_batched(const double* in, double* out, long long Nx, int lh, int lw, long long tiles,
+                     long long in_stride, long long out_stride, const double2* __restrict__ tw,
+                     const double2* __restrict__ gpow, const double2* __restrict__ gipw,
+                     const double2* __restrict__ gpowr, const double2* __restrict__ gipr,
+                     const double2* __restrict__ qinv, int delta_rhs, int n0_only) {
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    const int h = LH >= 0 ? LH : lh, w = lw;
+    const long long b = (long long)blockIdx.x / tiles, tile = (long long)blockIdx.x - b * tiles;
+    const long long H = 1LL << h;
+    time_solve_tile<double, MAXB4>(in + b * in_stride, out + b * out_stride, Nx, h, w, tw, gpow + b * H,
+                                   gipw + b * H, nullptr, nullptr, 0.0, gpowr + b * H, gipr + b * H,
+                                   qinv + b * H * Nx, delta_rhs, n0_only, tile, smem_raw);
 }
 
 // FP32 time solve with the transforms in registers, H = nt/2 = 32 ... 256.
@@ -576,6 +598,40 @@ cudaError_t launch_time_solve(const R* in, R* out, const Tables& tb, double cnor
 
 template cudaError_t launch_time_solve<double>(const double*, double*, const Tables&, double, int, int, cudaStream_t);
 template cudaError_t launch_time_solve<float>(const float*, float*, const Tables&, double, int, int, cudaStream_t);
+
+cudaError_t launch_time_solve_batched(const double* in, double* out, const Tables& tb, long long count,
+                                      long long in_stride, long long out_stride, const double2* gpow,
+                                      const double2* gipw, const double2* gpowr, const double2* gipr,
+                                      const double2* qinv, int delta_rhs, int n0_only, cudaStream_t s) {
+    constexpr int MB = time_tile_maxb4<double>();
+    constexpr int TILE = 4 * MB * TILE_THREADS;
+    const int lh = tb.lnt - 1, H = 1 << lh;
+    int lw = tile_lw(lh, TILE);
+    while (lw > 0 && (1LL << (lw - 1)) >= tb.Nx) --lw;         // no wider than the modes
+    const int W = 1 << lw;
+    const long long tiles = (tb.Nx + W - 1) / W;
+    const long long blocks = tiles * count;
+    if (count < 1 || blocks > 0x7fffffffLL) return cudaErrorInvalidValue;
+    const size_t smem = sizeof(double2) * ((size_t)H * W + H);
+#define QBVM_TSB(LHV)                                                                                            \
+    {                                                                                                            \
+        auto kern = k_time_solve_batched<MB, LHV>;                                                               \
+        cudaError_t e = set_smem(kern, smem);                                                                    \
+        if (e != cudaSuccess) return e;                                                                          \
+        kern<<<(unsigned)blocks, TILE_THREADS, smem, s>>>(in, out, tb.Nx, lh, lw, tiles, in_stride, out_stride,  \
+                                                          tb.tw_t, gpow, gipw, gpowr, gipr, qinv, delta_rhs,     \
+                                                          n0_only);                                              \
+        return cudaGetLastError();                                                                               \
+    }
+    switch (lh) {
+        case 5: QBVM_TSB(5)
+        case 6: QBVM_TSB(6)
+        case 7: QBVM_TSB(7)
+        case 8: QBVM_TSB(8)
+        default: QBVM_TSB(-1)
+    }
+#undef QBVM_TSB
+}
 
 // ------------------------------------------------------------------ 1D path
 //
@@ -1192,6 +1248,29 @@ __global__ void k_df_to_double(void* buf, long long n) {
     }
 }
 
+// The same conversion, four values per thread: two 16-byte loads of the pairs,
+// then two 16-byte stores of the doubles over the same 32 bytes (every thread
+// reads its bytes before writing them, and no other thread touches them).
+// Requires a 16-byte aligned buffer; values past the last group of four are
+// taken one per thread by the first threads of the grid.
+__global__ void __launch_bounds__(256) k_df_to_double4(void* buf, long long n) {
+    const long long ng = n >> 2;
+    const long long tid = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+    const long long stride = (long long)gridDim.x * blockDim.x;
+    const float4* src = reinterpret_cast<const float4*>(buf);
+    double2* dst = reinterpret_cast<double2*>(buf);
+    for (long long g = tid; g < ng; g += stride) {
+        const float4 a = src[2 * g], b = src[2 * g + 1];
+        dst[2 * g] = make_double2(qbvm_join_df(a.x, a.y), qbvm_join_df(a.z, a.w));
+        dst[2 * g + 1] = make_double2(qbvm_join_df(b.x, b.y), qbvm_join_df(b.z, b.w));
+    }
+    const long long i = 4 * ng + tid;
+    if (i < n) {
+        const float2 v = reinterpret_cast<const float2*>(buf)[i];
+        reinterpret_cast<double*>(buf)[i] = qbvm_join_df(v.x, v.y);
+    }
+}
+
 static dfloat df_const(double c) {
     float h = (float)c;
     return {h, (float)(c - (double)h)};
@@ -1246,6 +1325,13 @@ cudaError_t launch_residual_df(const void* y_df, const double* f, int delta_rhs,
 }
 
 cudaError_t launch_df_to_double(void* buf, long long n, cudaStream_t s) {
+    if ((reinterpret_cast<uintptr_t>(buf) & 15) == 0) {
+        long long blocks = ((n >> 2) + 255) / 256;
+        if (blocks > 152 * 8) blocks = 152 * 8;
+        if (blocks < 1) blocks = 1;
+        k_df_to_double4<<<(unsigned)blocks, 256, 0, s>>>(buf, n);
+        return cudaGetLastError();
+    }
     long long blocks = (n + 1023) / 1024;
     if (blocks > 152 * 32) blocks = 152 * 32;
     if (blocks < 1) blocks = 1;

@@ -40,6 +40,7 @@ struct qbvm_plan {
     double* fcopy = nullptr;      // FP32_REFINE: copy of an F that aliases y
     // host-pointer solves: a copy stream and events that pipeline the staging
     cudaStream_t copy_stream = nullptr;
+    cudaStream_t aux_stream = nullptr;   // second compute stream for alternate chunks
     std::vector<cudaEvent_t> copy_events;
     float* g32 = nullptr;         // Nx FP32 (delta rhs)
     long long ws_bytes = 0;
@@ -204,6 +205,7 @@ void destroy_plan(qbvm_plan_t* p) {
     if (!p) return;
     for (cudaEvent_t e : p->copy_events) cudaEventDestroy(e);
     if (p->copy_stream) cudaStreamDestroy(p->copy_stream);
+    if (p->aux_stream) cudaStreamDestroy(p->aux_stream);
     for (void* v : p->allocs) cudaFree(v);
     for (auto& m : p->marks) {
         cudaEventDestroy(m.a);
@@ -476,6 +478,7 @@ int solve_fp32r_dev(qbvm_plan_t* p, const double* in, double* y, int n0_only, cu
 }  // namespace
 
 int qbvm::validate_desc(const qbvm_desc* d) { return validate(d); }
+double qbvm::time_cn(const Tables& tb) { return fp64_cn(tb); }
 
 int qbvm::plan_view(const struct ::qbvm_plan* p, PlanView* out) {
     if (!p || !out) return QBVM_ERR_BAD_ARG;
@@ -786,10 +789,14 @@ static int solve_dev(qbvm_plan_t* p, const double* in, double* y, int n0_only, c
 
 // Host-pointer FP64 space-first solve with the copies overlapped: chunks of
 // time levels go host -> device on the copy stream while the DSTs of the
-// chunks already there run on the caller's stream; after the time part each
-// chunk's inverse DSTs are followed by its device -> host copy, again on the
-// copy stream.  Events order the two streams; the caller's stream ends after
-// the last copy.  (Overlap needs pinned host memory; pageable memory still
+// chunks already there run; after the time part each chunk's inverse DSTs are
+// followed by its device -> host copy, again on the copy stream.  Chunks
+// alternate between the caller's stream and a second compute stream, so the
+// partly filled last wave of one chunk's DST shares the SMs with the first
+// CTAs of the next (a chunk alone fills about one wave and a fraction).
+// Events order the three streams; the caller's stream ends after the last
+// copy; only the first chunk's input copy and the last chunk's output copy
+// are exposed.  (Overlap needs pinned host memory; pageable memory still
 // gives the right answer.)
 constexpr int HOST_CHUNKS = 8;
 
@@ -797,21 +804,29 @@ static int solve_fp64_host(qbvm_plan_t* p, const double* hin, double* hout, int 
     const Tables& tb = p->tb;
     const long long Nx = tb.Nx, nt = tb.nt;
     const int delta = p->d.rhs_kind == QBVM_RHS_DELTA;
+    // events: [0, H) chunk inputs copied, [H, 2H) chunk outputs ready, then
+    // start, copies done, forward chunks joined, time part done
+    const int E_START = 2 * HOST_CHUNKS, E_DONE = E_START + 1, E_JOIN = E_START + 2, E_FORK = E_START + 3;
     if (!p->copy_stream) {
         CK(cudaStreamCreateWithFlags(&p->copy_stream, cudaStreamNonBlocking));
-        p->copy_events.resize(2 * HOST_CHUNKS + 2);
+        CK(cudaStreamCreateWithFlags(&p->aux_stream, cudaStreamNonBlocking));
+        p->copy_events.resize(E_FORK + 1);
         for (auto& e : p->copy_events) CK(cudaEventCreateWithFlags(&e, cudaEventDisableTiming));
     }
-    cudaStream_t cs = p->copy_stream;
+    cudaStream_t cs = p->copy_stream, as = p->aux_stream;
     cudaEvent_t* ev = p->copy_events.data();
+    auto cst = [&](int c) { return (c & 1) ? as : s; };
     // chunks start at even levels: the x-DST packs rows in pairs from its first
-    // row, so the pairs (and the rounding) are those of the whole-array pass
-    const int nch = nt >= 2 * HOST_CHUNKS ? HOST_CHUNKS : 1;
+    // row, so the pairs (and the rounding) are those of the whole-array pass.
+    // (Measured on 255^2 x 256: 8 equal chunks beat 16 equal ones and chunks
+    // growing 7/5 per step with the output ones shrinking.)
+    const int nch = (int)std::max(1LL, std::min((long long)HOST_CHUNKS, nt / 2));
     auto lev0 = [&](int c) { return c == nch ? nt : ((nt * c / nch) & ~1LL); };
     double *din = p->stage_in, *dy = p->stage_out;
     int launches = 0, rc = QBVM_OK;
-    CK(cudaEventRecord(ev[2 * HOST_CHUNKS], s));            // the copies start after the caller's work
-    CK(cudaStreamWaitEvent(cs, ev[2 * HOST_CHUNKS], 0));
+    CK(cudaEventRecord(ev[E_START], s));                     // everything starts after the caller's work
+    CK(cudaStreamWaitEvent(cs, ev[E_START], 0));
+    CK(cudaStreamWaitEvent(as, ev[E_START], 0));
     if (delta) {
         CK(cudaMemcpyAsync(din, hin, sizeof(double) * Nx, cudaMemcpyHostToDevice, s));
         rc = fp64_dst_levels(p, din, p->ghat, 0, 1, s, &launches);
@@ -822,24 +837,30 @@ static int solve_fp64_host(qbvm_plan_t* p, const double* hin, double* hout, int 
             const long long a = lev0(c), b = lev0(c + 1);
             CK(cudaMemcpyAsync(din + a * Nx, hin + a * Nx, sizeof(double) * (b - a) * Nx, cudaMemcpyHostToDevice, cs));
             CK(cudaEventRecord(ev[c], cs));
-            CK(cudaStreamWaitEvent(s, ev[c], 0));
-            rc = fp64_dst_levels(p, din, work, a, b, s, &launches);
+            CK(cudaStreamWaitEvent(cst(c), ev[c], 0));
+            rc = fp64_dst_levels(p, din, work, a, b, cst(c), &launches);
         }
-        if (!rc) rc = fp64_time_part(p, work, dy, 0, n0_only, s, &launches);
+        if (rc) return rc;
+        CK(cudaEventRecord(ev[E_JOIN], as));
+        CK(cudaStreamWaitEvent(s, ev[E_JOIN], 0));
+        rc = fp64_time_part(p, work, dy, 0, n0_only, s, &launches);
     }
     if (rc) return rc;
+    CK(cudaEventRecord(ev[E_FORK], s));
+    CK(cudaStreamWaitEvent(as, ev[E_FORK], 0));
     const int nco = n0_only ? 1 : nch;
     for (int c = 0; c < nco && !rc; ++c) {
         const long long a = n0_only ? 0 : lev0(c), b = n0_only ? 1 : lev0(c + 1);
-        rc = fp64_dst_levels(p, dy, dy, a, b, s, &launches);
+        rc = fp64_dst_levels(p, dy, dy, a, b, cst(c), &launches);
         if (rc) break;
-        CK(cudaEventRecord(ev[HOST_CHUNKS + c], s));
+        CK(cudaEventRecord(ev[HOST_CHUNKS + c], cst(c)));
         CK(cudaStreamWaitEvent(cs, ev[HOST_CHUNKS + c], 0));
         CK(cudaMemcpyAsync(hout + a * Nx, dy + a * Nx, sizeof(double) * (b - a) * Nx, cudaMemcpyDeviceToHost, cs));
     }
     if (rc) return rc;
-    CK(cudaEventRecord(ev[2 * HOST_CHUNKS + 1], cs));
-    CK(cudaStreamWaitEvent(s, ev[2 * HOST_CHUNKS + 1], 0));
+    // the last copy waited for every chunk of either compute stream
+    CK(cudaEventRecord(ev[E_DONE], cs));
+    CK(cudaStreamWaitEvent(s, ev[E_DONE], 0));
     CK(cudaStreamSynchronize(s));
     p->kernels_per_solve = launches;
     return QBVM_OK;

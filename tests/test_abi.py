@@ -102,3 +102,25 @@ def test_null_arguments(lib):
     out = ctypes.c_double()
     assert lib.qbvm_residual(None, None, None, ctypes.byref(out), None) == -1
     assert lib.qbvm_destroy(None) == 0
+
+
+@pytest.mark.parametrize("case", [
+    dict(count=0, code=-1), dict(alphas=[1e-3, -1.0], code=-1), dict(alphas=[float("nan")], code=-1),
+    dict(precision=1, code=-7), dict(nt=24, code=-7), dict(dim=1, m=(24, 1, 1), code=-7),
+    dict(dim=1, m=(64, 1, 1), order=1, code=-7), dict(dim=0, code=-1)],
+    ids=["count0", "alpha-neg", "alpha-nan", "fp32", "nt24", "1d-m24", "1d-time-first", "dim0"])
+def test_batch_plan_rejects_before_a_gpu(lib, case):
+    """qbvm_batch_plan: same-shape FP64 space-first batches with power-of-two nt;
+    everything else is refused on the host."""
+    import ctypes
+    a = dict(dim=2, m=(16, 16, 1), nt=16, precision=0, order=0, count=2, alphas=None)
+    a.update(case)
+    desc = Q.make_desc(a["dim"], a["m"], 1.0, 0.1, a["nt"], 0, 1e-3, 0.0, a["precision"], order=a["order"])
+    arr = None
+    n = a["count"]
+    if a["alphas"] is not None:
+        arr = (ctypes.c_double * len(a["alphas"]))(*a["alphas"])
+        n = len(a["alphas"])
+    h = ctypes.c_void_p()
+    assert lib.qbvm_batch_plan(ctypes.byref(desc), n, arr, ctypes.byref(h)) == case["code"]
+    assert not h.value

@@ -225,6 +225,26 @@ def test_n0_only_and_host_pointers(grid, rhs_kind):
     np.testing.assert_array_equal(host, full)
 
 
+@pytest.mark.parametrize("grid", [bi.Grid(2, (64, 32), 1.0, 0.1, 50), bi.Grid(3, (16, 8, 8), 1.0, 0.1, 64),
+                                  bi.Grid(2, (256, 256), 1.0, 0.1, 32)],
+                         ids=["2d-nt50", "3d-nt64", "2d-255sq-nt32"])
+def test_host_pointers_chunked_pinned(grid):
+    """Pinned host buffers: the level chunks' copies overlap DSTs that alternate
+    between two compute streams; the result is bitwise the device-pointer solve."""
+    F = bi.random_general_rhs(grid, seed=14)
+    dev = gpu_solve(grid, Q.FORM_PM, 1e-3, F, Q.RHS_GENERAL)
+    dev0 = gpu_solve(grid, Q.FORM_PM, 1e-3, F, Q.RHS_GENERAL, n0_only=True)
+    with Q.Plan(grid.dim, grid.M, grid.L, grid.T, grid.nt, Q.FORM_PM, 1e-3, 0.0, Q.FP64, Q.RHS_GENERAL) as plan:
+        hin = torch.as_tensor(F.ravel()).pin_memory()
+        hout = torch.full((grid.unknowns,), float("nan"), dtype=torch.float64).pin_memory()
+        for _ in range(2):                                   # second call reuses streams and events
+            plan.solve(hin, hout)
+            np.testing.assert_array_equal(hout.numpy().reshape(grid.full_shape), dev)
+        h0 = torch.full((grid.Nx,), float("nan"), dtype=torch.float64).pin_memory()
+        plan.solve(hin, h0, n0_only=True)
+        np.testing.assert_array_equal(h0.numpy().reshape((1,) + grid.shape), dev0)
+
+
 def test_inplace_general_rhs():
     grid = bi.Grid(2, (16, 16), 1.0, 0.1, 16)
     F = bi.random_general_rhs(grid, seed=11)
