@@ -312,6 +312,15 @@ int qbvm_sweep_autotune(qbvm_sweep_t* sweep, int repeats, qbvm_sweep_config* bes
 int qbvm_sweep_set_config(qbvm_sweep_t* sweep, const qbvm_sweep_config* cfg);
 int qbvm_sweep_get_config(const qbvm_sweep_t* sweep, qbvm_sweep_config* cfg);
 int qbvm_sweep_destroy(qbvm_sweep_t* sweep);
+/* Diagnostic of the failure path above: `ctas` CTAs (1..64) of one kernel run
+ * the sweep's bounded wait on a counter that nothing advances.  The wait gives
+ * up after its spin limit (about half a second), raises the error flag, the
+ * other CTAs see the flag and leave, and the kernel returns.  Returns
+ * QBVM_ERR_TIMEOUT (what qbvm_sweep_read reports in that case) when every CTA
+ * gave up and the flag was raised, QBVM_OK if a wait wrongly succeeded;
+ * *seconds (may be NULL) receives the kernel's duration.  The context stays
+ * usable afterwards. */
+int qbvm_selftest_bounded_wait(int ctas, double* seconds, void* stream);
 
 /* ------------------------------------------------------------------------
  * Learned regularisation parameter.  The paper picks alpha a priori

@@ -126,6 +126,8 @@ def load_library(path: str | None = None) -> ctypes.CDLL:
     lib.qbvm_batch_info.restype = ip
     lib.qbvm_batch_destroy.argtypes = [vp]
     lib.qbvm_batch_destroy.restype = ip
+    lib.qbvm_selftest_bounded_wait.argtypes = [ip, ctypes.POINTER(dp), vp]
+    lib.qbvm_selftest_bounded_wait.restype = ip
     lib.qbvm_sweep_plan.argtypes = [ctypes.POINTER(QbvmSweepDesc), ctypes.POINTER(vp)]
     lib.qbvm_sweep_plan.restype = ip
     lib.qbvm_sweep_run.argtypes = [vp, vp]

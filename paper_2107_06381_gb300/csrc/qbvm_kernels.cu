@@ -67,8 +67,11 @@ static cudaError_t launch_dst_ct(const TIN* in, void* out, long long outer, long
 }
 
 // FP32 DST with the transform in registers (rd::tile), M = 64, 128, 256.
+// Minimum CTAs per SM: shared memory admits 5 (M = 256) / 10 (M = 128) CTAs;
+// the y/z passes fit that in 48 registers without spills, the x passes keep
+// 64 (measured: the x pass slows down when squeezed to 48).
 template <typename TIN, int OMODE, int LM, bool XAX>
-__global__ void __launch_bounds__(rd::threads<LM>())
+__global__ void __launch_bounds__(rd::threads<LM>(), LM == 8 ? (XAX ? 4 : 5) : LM == 7 ? (XAX ? 8 : 10) : (XAX ? 9 : 12))
 k_dst_reg(const TIN* in, void* out, long long outer, long long inner, const float2* __restrict__ tw,
           const float* __restrict__ sn) {
     extern __shared__ __align__(16) unsigned char smem_raw[];
@@ -315,8 +318,10 @@ constexpr size_t ts_region_bytes() {
 template <int LH>
 constexpr size_t ts_reg_smem() { return (size_t)4 * (1 << LH) * sizeof(float2) + ts_region_bytes<LH>(); }
 
+// Minimum CTAs per SM: 64 registers for H = 256 / 128 (from 80: 24 -> 32
+// resident warps, 4 % faster at H = 128), 48 below.
 template <int LH>
-__global__ void __launch_bounds__(TS_MODES * TsCfg<LH>::N2)
+__global__ void __launch_bounds__(TS_MODES * TsCfg<LH>::N2, LH == 8 ? 4 : LH == 7 ? 8 : LH == 6 ? 10 : 20)
 k_time_solve_reg(const float* in, float* out, long long Nx, const float2* __restrict__ tw,
                  const float2* __restrict__ gpow, const float2* __restrict__ gipw, const float2* __restrict__ ak,
                  const float* __restrict__ lamtau, float cnorm, float rho_h, float rho_hinv, int delta_rhs,

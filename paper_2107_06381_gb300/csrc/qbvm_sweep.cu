@@ -542,6 +542,15 @@ int run_graph(qbvm_sweep_t* p, cudaStream_t s) {
 
 }  // namespace
 
+// Diagnostic: every CTA runs the persistent kernel's bounded wait on a
+// counter that nothing advances.  The first CTA to exhaust SPIN_LIMIT raises
+// the error flag; the others see it and leave.  out[b] = 1 if CTA b's wait
+// succeeded (it never should).
+__global__ void k_wait_selftest(const int* counter, int* errflag, int* out) {
+    const bool ok = wait_for(counter, 1, errflag);
+    if (threadIdx.x == 0) out[blockIdx.x] = ok ? 1 : 0;
+}
+
 extern "C" {
 
 int qbvm_sweep_plan(const qbvm_sweep_desc* d, qbvm_sweep_t** out) {
@@ -827,6 +836,45 @@ int qbvm_sweep_get_config(const qbvm_sweep_t* p, qbvm_sweep_config* cfg) {
 int qbvm_sweep_destroy(qbvm_sweep_t* p) {
     sw_destroy(p);
     return QBVM_OK;
+}
+
+int qbvm_selftest_bounded_wait(int ctas, double* seconds, void* stream) {
+    if (ctas < 1 || ctas > 64) return QBVM_ERR_BAD_ARG;
+    cudaStream_t s = static_cast<cudaStream_t>(stream);
+    int* buf = nullptr;                       // [0] counter, [1] error flag, [2..] per-CTA outcome
+    if (cudaMalloc(&buf, sizeof(int) * (size_t)(2 + ctas)) != cudaSuccess) {
+        cudaGetLastError();
+        return QBVM_ERR_OOM;
+    }
+    std::vector<int> h((size_t)(2 + ctas), -1);
+    cudaEvent_t e0 = nullptr, e1 = nullptr;
+    int rc = QBVM_OK;
+    if (cudaEventCreate(&e0) != cudaSuccess || cudaEventCreate(&e1) != cudaSuccess ||
+        cudaMemsetAsync(buf, 0, sizeof(int) * (size_t)(2 + ctas), s) != cudaSuccess ||
+        cudaEventRecord(e0, s) != cudaSuccess) {
+        rc = QBVM_ERR_CUDA;
+    } else {
+        k_wait_selftest<<<ctas, 32, 0, s>>>(buf, buf + 1, buf + 2);
+        if (cudaGetLastError() != cudaSuccess || cudaEventRecord(e1, s) != cudaSuccess ||
+            cudaMemcpyAsync(h.data(), buf, sizeof(int) * h.size(), cudaMemcpyDeviceToHost, s) != cudaSuccess ||
+            cudaStreamSynchronize(s) != cudaSuccess)
+            rc = QBVM_ERR_CUDA;
+    }
+    if (!rc && seconds) {
+        float ms = 0.f;
+        cudaEventElapsedTime(&ms, e0, e1);
+        *seconds = ms * 1e-3;
+    }
+    if (e0) cudaEventDestroy(e0);
+    if (e1) cudaEventDestroy(e1);
+    cudaFree(buf);
+    if (rc) {
+        cudaGetLastError();
+        return rc;
+    }
+    bool any_ok = false;
+    for (int b = 0; b < ctas; ++b) any_ok = any_ok || h[(size_t)(2 + b)] != 0;
+    return (h[1] != 0 && !any_ok) ? QBVM_ERR_TIMEOUT : QBVM_OK;
 }
 
 }  // extern "C"

@@ -124,3 +124,8 @@ def test_batch_plan_rejects_before_a_gpu(lib, case):
     h = ctypes.c_void_p()
     assert lib.qbvm_batch_plan(ctypes.byref(desc), n, arr, ctypes.byref(h)) == case["code"]
     assert not h.value
+
+
+def test_selftest_rejects_bad_cta_counts(lib):
+    assert lib.qbvm_selftest_bounded_wait(0, None, None) == -1
+    assert lib.qbvm_selftest_bounded_wait(65, None, None) == -1

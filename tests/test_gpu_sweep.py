@@ -144,3 +144,23 @@ def test_c4_style_batch_sampled():
             assert O.rel_l2(y0s[i], oys[int(pick[i, 0])].ravel()) <= 1e-10
     finally:
         sw.close()
+
+
+@pytest.mark.parametrize("ctas", [1, 8])
+def test_bounded_wait_gives_up_and_the_context_survives(ctas):
+    """The persistent kernel's wait on a counter that nothing advances gives up
+    after its spin limit, raises the error flag (the other CTAs leave on it) and
+    reports QBVM_ERR_TIMEOUT; a solve on the same context still works."""
+    import ctypes
+    lib = Q.load_library()
+    secs = ctypes.c_double(-1.0)
+    assert lib.qbvm_selftest_bounded_wait(ctas, ctypes.byref(secs), None) == -5
+    assert 1e-3 < secs.value < 5.0
+    grid = bi.Grid(2, (16, 16), 1.0, 0.1, 8)
+    g = bi.random_general_rhs(grid, seed=5)[0]
+    with Q.Plan(2, grid.M, grid.L, grid.T, grid.nt, Q.FORM_PQ, 1e-3, 0.0, Q.FP64, Q.RHS_DELTA) as plan:
+        y = torch.empty(grid.unknowns, dtype=torch.float64, device="cuda")
+        plan.solve(torch.as_tensor(g.ravel()).cuda(), y)
+        torch.cuda.synchronize()
+    want = O.solve_spectral(grid, O.PQ, 1e-3, O.delta_rhs(grid, O.PQ, 1e-3, g))
+    assert O.rel_l2(y.cpu().numpy(), want) <= 1e-10
