@@ -183,23 +183,31 @@ __device__ __forceinline__ void time_solve_tile(const R* in, R* out, long long N
     const long long l0 = tile * W;
 
     for (int i = tid; i < H; i += nth) stw[i] = tw[i];
-    for (int e = tid; e < (H << lw); e += nth) {
-        int t = e >> lw, c = e & (W - 1);
-        long long l = l0 + c;
-        R f0 = R(0), f1 = R(0);
-        if (l < Nx) {
-            if (delta_rhs) {
-                if (t == 0) f0 = in[l];
-            } else {
+    if (delta_rhs) {
+        // f = f^0 e_0: Step (a) of a single level-0 value is that value (times
+        // gamma^0) at every frequency, so the forward transform is not computed
+        const C g = gpow[0];
+        for (int e = tid; e < (H << lw); e += nth) {
+            const long long l = l0 + (e & (W - 1));
+            const R f0 = l < Nx ? in[l] : R(0);
+            buf[e] = mkc(g.x * f0, g.y * f0);
+        }
+        __syncthreads();
+    } else {
+        for (int e = tid; e < (H << lw); e += nth) {
+            int t = e >> lw, c = e & (W - 1);
+            long long l = l0 + c;
+            R f0 = R(0), f1 = R(0);
+            if (l < Nx) {
                 f0 = in[(long long)t * Nx + l];
                 f1 = in[(long long)(t + H) * Nx + l];
             }
+            const C g = gpow[t], gr = gpowr[t];      // gamma^t f0 + i rho^H gamma^t f1
+            buf[e] = mkc(rfma(g.x, f0, gr.x * f1), rfma(g.y, f0, gr.y * f1));
         }
-        const C g = gpow[t], gr = gpowr[t];          // gamma^t f0 + i rho^H gamma^t f1
-        buf[e] = mkc(rfma(g.x, f0, gr.x * f1), rfma(g.y, f0, gr.y * f1));
+        __syncthreads();
+        fft_tile<+1, MAXB4>(buf, stw, lh, lw);
     }
-    __syncthreads();
-    fft_tile<+1, MAXB4>(buf, stw, lh, lw);
 
     if (qinv) {                                          // the plan's table of cnorm / (d_{2m} + tau Lambda_l)
         for (int e = tid; e < (H << lw); e += nth) {
