@@ -337,7 +337,7 @@ def our_arm(args, rank, world, device):
                 a, b = rk.get(name, (0, 0.0))
                 rk[name] = (a + launches, b + ms)
         refine = {"value": world * unknowns_step * args.steps / (r_ms / 1e3), "unit": UNIT,
-                  "ms_per_step": r_ms / args.steps, "dtype": "f32 transforms + f64 residual/update",
+                  "ms_per_step": r_ms / args.steps, "dtype": "f32 transforms + double-float residual/update",
                   "refine_steps": [plan.info.last_refine_iters for plan in rplans],
                   "rel_residual": [plan.info.last_rel_residual for plan in rplans],
                   "kernels": {k: {"launches": v[0], "avg_ms": round(v[1] / v[0], 4)} for k, v in rk.items()},

@@ -663,24 +663,31 @@ k_time_fwd_1d(const double* in, double2* wk, long long Nx, int lh, int lw, const
     double2* stw = buf + (H << lw);
     const int tid = threadIdx.x, nth = blockDim.x;
     const long long x0 = (long long)blockIdx.x * W;
-    for (int i = tid; i < H; i += nth) stw[i] = tw[i];
-    for (int e = tid; e < (H << lw); e += nth) {
-        int t = e >> lw, c = e & (W - 1);
-        long long x = x0 + c;
-        double f0 = 0.0, f1 = 0.0;
-        if (x < Nx) {
-            if (delta_rhs) {
-                if (t == 0) f0 = in_scale * in[x];
-            } else {
+    if (delta_rhs) {
+        // f = f^0 e_0: the transform is gamma^0 f^0 at every frequency
+        const double2 g = gpow[0];
+        for (int e = tid; e < (H << lw); e += nth) {
+            const long long x = x0 + (e & (W - 1));
+            const double f0 = x < Nx ? in_scale * in[x] : 0.0;
+            buf[e] = make_double2(g.x * f0, g.y * f0);
+        }
+        __syncthreads();
+    } else {
+        for (int i = tid; i < H; i += nth) stw[i] = tw[i];
+        for (int e = tid; e < (H << lw); e += nth) {
+            int t = e >> lw, c = e & (W - 1);
+            long long x = x0 + c;
+            double f0 = 0.0, f1 = 0.0;
+            if (x < Nx) {
                 f0 = in[(long long)t * Nx + x];
                 f1 = rho_h * in[(long long)(t + H) * Nx + x];
             }
+            double2 g = gpow[t];
+            buf[e] = make_double2(g.x * f0 - g.y * f1, g.y * f0 + g.x * f1);
         }
-        double2 g = gpow[t];
-        buf[e] = make_double2(g.x * f0 - g.y * f1, g.y * f0 + g.x * f1);
+        __syncthreads();
+        fft_tile<+1, TILE_ELEMS / 4 / TILE_THREADS>(buf, stw, lh, lw);
     }
-    __syncthreads();
-    fft_tile<+1, TILE_ELEMS / 4 / TILE_THREADS>(buf, stw, lh, lw);
     for (int e = tid; e < (H << lw); e += nth) {
         int k = e >> lw, c = e & (W - 1);
         long long x = x0 + c;
