@@ -57,6 +57,8 @@ __device__ __forceinline__ T ldin(const T* p) {
     return *p;
 }
 
+constexpr int DST_TILE = 2048;     // complex elements per (full-width) DST tile
+
 // One DST tile (`tile` selects 2W real columns) on a CTA of TILE_THREADS
 // threads with dynamic shared memory `smem_raw` of dst_smem bytes.
 // X4: produce 4 times the DST.  The factors 1/2 of the pre-processing and of
@@ -156,7 +158,10 @@ __device__ __forceinline__ void dst_tile(const TIN* in, void* out, int n, int lm
     }
     __syncthreads();
     // y_{2k+1} = sum_{kappa <= k} (odd increments): segmented prefix sum per real column
-    const int segs = nth >= ncol ? nth / ncol : 1;
+    // the segment count of the full-width tile whatever this tile's width, so
+    // that the prefix sums (and their rounding) do not depend on the width
+    const int wfull = (DST_TILE >> lm) > 0 ? (DST_TILE >> lm) : 1;
+    const int segs = nth >= 2 * wfull ? nth / (2 * wfull) : 1;
     const int L = (H + segs - 1) / segs;
     for (int task = tid; task < ncol * segs; task += nth) {
         int c = task % ncol, sg = task / ncol;
@@ -202,8 +207,6 @@ __device__ __forceinline__ void dst_tile(const TIN* in, void* out, int n, int lm
     }
 }
 
-constexpr int DST_TILE = 2048;     // complex elements per DST tile
-
 __host__ __device__ inline int dst_lw(int lm) {
     int lw = 0;
     while (((1 << lm) << (lw + 1)) <= DST_TILE) ++lw;
@@ -211,11 +214,13 @@ __host__ __device__ inline int dst_lw(int lm) {
 }
 
 template <typename R>
-inline size_t dst_smem(int lm) {
-    const int M = 1 << lm, lw = dst_lw(lm), W = 1 << lw, H = M >> 1;
+inline size_t dst_smem(int lm, int lw) {
+    const int M = 1 << lm, W = 1 << lw, H = M >> 1;
     const int ncol = 2 * W;
     size_t seg = (size_t)(TILE_THREADS >= ncol ? TILE_THREADS : ncol);
     return sizeof(cplx<R>) * ((size_t)M * W + M) + sizeof(R) * ((size_t)M * 2 * W + H + 2 + seg);
 }
+template <typename R>
+inline size_t dst_smem(int lm) { return dst_smem<R>(lm, dst_lw(lm)); }
 
 }  // namespace qbvm

@@ -115,14 +115,29 @@ int dst_tile_lw(int lm) { return dst_lw(lm); }
 template <typename R, typename TIN, int OMODE, bool X4>
 cudaError_t launch_dst(const TIN* in, void* out, int n, int lm, long long outer, long long inner,
                        const void* tw, const void* sn, cudaStream_t s) {
-    const int lw = dst_lw(lm), W = 1 << lw;
-    long long blocks;
-    if (inner == 1) blocks = (outer + 2 * W - 1) / (2 * W);
-    else blocks = outer * ((inner + 2 * W - 1) / (2 * W));
-    size_t smem = dst_smem<R>(lm);
+    const int lw0 = dst_lw(lm);
+    auto nblocks = [&](int l) {
+        const long long W2 = 2LL << l;               // real columns per tile
+        return inner == 1 ? (outer + W2 - 1) / W2 : outer * ((inner + W2 - 1) / W2);
+    };
+    int lw = lw0;
+    if (std::is_same<R, double>::value) {
+        // Few tiles (one or a few levels, e.g. the y^0-only solve): an FP64 tile
+        // is ~15 us of FP64-pipe work on its SM, so narrower tiles spread the
+        // pass over at least two per SM.  Column pairs and prefix-sum segments
+        // are those of the full-width tiles, so the results are bitwise the same.
+        int dev = 0, sms = 0;
+        if (cudaGetDevice(&dev) == cudaSuccess &&
+            cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev) == cudaSuccess && sms > 0)
+            while (lw > 0 && nblocks(lw) < 2LL * sms) --lw;
+        else
+            cudaGetLastError();
+    }
+    const long long blocks = nblocks(lw);
+    size_t smem = dst_smem<R>(lm, lw);
     if (std::is_same<R, float>::value && !X4 && n == (1 << lm) - 1 && lm >= 6 && lm <= 8)
         return launch_dst_reg_any<TIN, OMODE>(in, out, lm, outer, inner, tw, sn, s);
-    if (n == (1 << lm) - 1) {
+    if (n == (1 << lm) - 1 && lw == lw0) {
         switch (lm) {
             case 6: return launch_dst_ct<R, TIN, OMODE, 6, X4>(in, out, outer, inner, tw, sn, blocks, smem, s);
             case 7: return launch_dst_ct<R, TIN, OMODE, 7, X4>(in, out, outer, inner, tw, sn, blocks, smem, s);

@@ -311,3 +311,15 @@ def test_c3_full_size_sampled_levels():
                             levels=levels)
     got = gpu_solve(grid, Q.FORM_PQ, alpha, p.g_delta, Q.RHS_DELTA)[levels]
     assert O.rel_l2(got, want) <= TOL
+
+
+@pytest.mark.parametrize("form", [Q.FORM_PQ, Q.FORM_PM], ids=["pq", "pm"])
+def test_y0_only_full_size_delta(form):
+    """y^0 alone from the delta right-hand side on 255^2 x 256 (one level of DSTs
+    in narrow tiles around the per-mode factor) against the oracle."""
+    p = bi.make_c2()
+    grid = p.grid
+    alpha = O.alpha_apriori(form, p.delta, grid.tau)
+    y0 = gpu_solve(grid, form, alpha, p.g_delta, Q.RHS_DELTA, n0_only=True)
+    want = O.solve_spectral(grid, form, alpha, O.delta_rhs(grid, form, alpha, p.g_delta), levels=[0])
+    assert O.rel_l2(y0, want) <= TOL
