@@ -18,18 +18,65 @@
 #include "qbvm_regdst.cuh"
 #include "qbvm_internal.h"
 
+#include <algorithm>
 #include <cstdint>
+#include <mutex>
+#include <vector>
 #include <type_traits>
 
 namespace qbvm {
 
 // Raise a kernel's dynamic shared-memory limit and prefer the largest
-// shared-memory carve-out (cheap host calls, made before every launch).
+// shared-memory carve-out.  The attribute calls are driver calls, so they are
+// made once per (device, kernel) and whenever a launch needs more than the
+// limit set so far; launches of small problems are otherwise host-bound.
+struct SmemSet {
+    int dev;
+    const void* fn;
+    size_t bytes;
+};
+static std::mutex g_smem_mu;
+static std::vector<SmemSet> g_smem_set;
+
 template <typename K>
 static cudaError_t set_smem(K kern, size_t smem) {
+    int dev = 0;
+    if (cudaGetDevice(&dev) != cudaSuccess) return cudaGetLastError();
+    const void* fn = reinterpret_cast<const void*>(kern);
+    {
+        std::lock_guard<std::mutex> lk(g_smem_mu);
+        for (const SmemSet& r : g_smem_set)
+            if (r.dev == dev && r.fn == fn && r.bytes >= smem) return cudaSuccess;
+    }
     cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     if (e != cudaSuccess) return e;
-    return cudaFuncSetAttribute(kern, cudaFuncAttributePreferredSharedMemoryCarveout, 100);
+    e = cudaFuncSetAttribute(kern, cudaFuncAttributePreferredSharedMemoryCarveout, 100);
+    if (e != cudaSuccess) return e;
+    std::lock_guard<std::mutex> lk(g_smem_mu);
+    for (SmemSet& r : g_smem_set)
+        if (r.dev == dev && r.fn == fn) {
+            r.bytes = std::max(r.bytes, smem);
+            return cudaSuccess;
+        }
+    g_smem_set.push_back({dev, fn, smem});
+    return cudaSuccess;
+}
+
+// SMs of the current device, queried once per device.
+static int device_sms() {
+    static std::mutex mu;
+    static int sms[64] = {0};
+    int dev = 0;
+    if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= 64) {
+        cudaGetLastError();
+        return 0;
+    }
+    std::lock_guard<std::mutex> lk(mu);
+    if (sms[dev] == 0 && cudaDeviceGetAttribute(&sms[dev], cudaDevAttrMultiProcessorCount, dev) != cudaSuccess) {
+        cudaGetLastError();
+        sms[dev] = 0;
+    }
+    return sms[dev];
 }
 
 template <typename R, typename TIN, int OMODE, int MAXB4, bool X4>
@@ -126,12 +173,8 @@ cudaError_t launch_dst(const TIN* in, void* out, int n, int lm, long long outer,
         // is ~15 us of FP64-pipe work on its SM, so narrower tiles spread the
         // pass over at least two per SM.  Column pairs and prefix-sum segments
         // are those of the full-width tiles, so the results are bitwise the same.
-        int dev = 0, sms = 0;
-        if (cudaGetDevice(&dev) == cudaSuccess &&
-            cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev) == cudaSuccess && sms > 0)
-            while (lw > 0 && nblocks(lw) < 2LL * sms) --lw;
-        else
-            cudaGetLastError();
+        const int sms = device_sms();
+        while (sms > 0 && lw > 0 && nblocks(lw) < 2LL * sms) --lw;
     }
     const long long blocks = nblocks(lw);
     size_t smem = dst_smem<R>(lm, lw);
@@ -576,7 +619,15 @@ cudaError_t launch_time_solve(const R* in, R* out, const Tables& tb, double cnor
     constexpr int MB = time_tile_maxb4<R>();
     constexpr int TILE = 4 * MB * TILE_THREADS;
     const int lh = tb.lnt - 1, H = 1 << lh;
-    const int lw = tile_lw(lh, TILE), W = 1 << lw;
+    const int lw0 = tile_lw(lh, TILE);
+    int lw = lw0;
+    {
+        // few modes (small grids): narrower tiles spread the FP64 work over more
+        // SMs; every mode's transforms are the same arithmetic at any width
+        const int sms = device_sms();
+        while (sms > 0 && lw > 0 && (tb.Nx + (1LL << lw) - 1) >> lw < 2LL * sms) --lw;
+    }
+    const int W = 1 << lw;
     long long blocks = (tb.Nx + W - 1) / W;
     size_t smem = sizeof(cplx<R>) * ((size_t)H * W + H);
     const bool f64 = std::is_same<R, double>::value;
@@ -606,12 +657,14 @@ cudaError_t launch_time_solve(const R* in, R* out, const Tables& tb, double cnor
                                                           qv, delta_rhs, n0_only);                             \
         return cudaGetLastError();                                                                             \
     }
-    switch (lh) {
-        QBVM_TS_CT(5)
-        QBVM_TS_CT(6)
-        QBVM_TS_CT(7)
-        QBVM_TS_CT(8)
-        default: break;
+    if (lw == lw0) {
+        switch (lh) {
+            QBVM_TS_CT(5)
+            QBVM_TS_CT(6)
+            QBVM_TS_CT(7)
+            QBVM_TS_CT(8)
+            default: break;
+        }
     }
 #undef QBVM_TS_CT
     auto kern = k_time_solve<R, MB>;
@@ -636,6 +689,8 @@ cudaError_t launch_time_solve_batched(const double* in, double* out, const Table
     const int lh = tb.lnt - 1, H = 1 << lh;
     int lw = tile_lw(lh, TILE);
     while (lw > 0 && (1LL << (lw - 1)) >= tb.Nx) --lw;         // no wider than the modes
+    const int sms = device_sms();                               // and at least two tiles per SM
+    while (sms > 0 && lw > 0 && count * ((tb.Nx + (1LL << lw) - 1) >> lw) < 2LL * sms) --lw;
     const int W = 1 << lw;
     const long long tiles = (tb.Nx + W - 1) / W;
     const long long blocks = tiles * count;
