@@ -391,6 +391,8 @@ QBVM_HD double qbvm_join_df(float hi, float lo) {
                           ((unsigned long long)(lb & 0x7FFFFFu) << 29));
     if (e1 == 0 || e1 == 255 || e2 == 255 || (e2 == 0 && (lb & 0x7FFFFFu)) || e2 > e1)
         return qbvm_join_hw(hi, lo);                      // zero/denormal/Inf/NaN/unnormalised: hardware
+    if (((hb ^ lb) & 0x80000000u) && e2 != 0 && e1 - e2 <= 1)
+        return qbvm_join_hw(hi, lo);                      // opposite signs within a binade: the sum may cancel
     const unsigned long long sign = (unsigned long long)(hb & 0x80000000u) << 32;
     long long S = (long long)((unsigned long long)((hb & 0x7FFFFFu) | 0x800000u) << 39);   // < 2^63
     if (e2 != 0) {
@@ -429,6 +431,26 @@ __device__ __forceinline__ dfloat df_from_double(double x) {
     return r;
 }
 __device__ __forceinline__ double df_to_double(dfloat a) { return qbvm_join_df(a.hi, a.lo); }
+
+// The same join where the integer pipes are the bottleneck: for normal hi and
+// lo (or lo = +-0) the exact widenings to FP64 are built from the bits (sign,
+// exponent rebased by 1023 - 127, significand shifted by 29) and summed by one
+// FP64 add, which rounds to nearest even exactly as qbvm_join_df does; any
+// other operand takes qbvm_join_df.  One FP64-pipe operation per value.
+__device__ __forceinline__ double qbvm_widen_normal(unsigned int b) {
+    const unsigned int w = (b & 0x80000000u) | ((((b >> 23) & 0xFFu) + 896u) << 20) | ((b & 0x7FFFFFu) >> 3);
+    return __hiloint2double((int)w, (int)(b << 29));
+}
+__device__ __forceinline__ double qbvm_join_df_dadd(float hi, float lo) {
+    const unsigned int hb = __float_as_uint(hi), lb = __float_as_uint(lo);
+    const unsigned int e1 = (hb >> 23) & 0xFFu, e2 = (lb >> 23) & 0xFFu;
+    if (e1 - 1u < 254u) {                                 // hi normal
+        const double dh = qbvm_widen_normal(hb);
+        if ((lb << 1) == 0) return dh;                    // lo = +-0
+        if (e2 - 1u < 254u) return __dadd_rn(dh, qbvm_widen_normal(lb));
+    }
+    return qbvm_join_df(hi, lo);
+}
 __device__ __forceinline__ float d2f_int(double x) {
     float h, l;
     qbvm_split_d(x, &h, &l);

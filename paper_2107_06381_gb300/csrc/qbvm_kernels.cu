@@ -1338,7 +1338,9 @@ __global__ void k_df_to_double(void* buf, long long n) {
     }
 }
 
-// The same conversion, four values per thread: two 16-byte loads of the pairs,
+// The same conversion, four values per thread (the join with one FP64 add per
+// value, qbvm_join_df_dadd: the integer join made this kernel instruction-bound
+// at 3.8 TB/s): two 16-byte loads of the pairs,
 // then two 16-byte stores of the doubles over the same 32 bytes (every thread
 // reads its bytes before writing them, and no other thread touches them).
 // Requires a 16-byte aligned buffer; values past the last group of four are
@@ -1351,8 +1353,8 @@ __global__ void __launch_bounds__(256) k_df_to_double4(void* buf, long long n) {
     double2* dst = reinterpret_cast<double2*>(buf);
     for (long long g = tid; g < ng; g += stride) {
         const float4 a = src[2 * g], b = src[2 * g + 1];
-        dst[2 * g] = make_double2(qbvm_join_df(a.x, a.y), qbvm_join_df(a.z, a.w));
-        dst[2 * g + 1] = make_double2(qbvm_join_df(b.x, b.y), qbvm_join_df(b.z, b.w));
+        dst[2 * g] = make_double2(qbvm_join_df_dadd(a.x, a.y), qbvm_join_df_dadd(a.z, a.w));
+        dst[2 * g + 1] = make_double2(qbvm_join_df_dadd(b.x, b.y), qbvm_join_df_dadd(b.z, b.w));
     }
     const long long i = 4 * ng + tid;
     if (i < n) {

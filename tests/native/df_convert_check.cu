@@ -69,6 +69,20 @@ int main() {
         }
         ++n;
     }
+    // opposite signs within a binade: exact and heavy cancellation
+    for (int i = 0; i < 200000; ++i) {
+        float h = (float)std::ldexp(u(rng), (int)(rng() % 120) - 60);
+        float l = -(float)std::ldexp(u(rng), std::ilogb(h) - (int)(rng() % 2));
+        if (i % 7 == 0) l = -h;
+        if (i % 11 == 0) l = -std::nextafter(h, 0.0f);
+        if (std::fabs(l) > std::fabs(h)) std::swap(h, l);
+        double j = qbvm::qbvm_join_df(h, l), j0 = (double)h + (double)l;
+        if (std::memcmp(&j, &j0, 8) != 0) {
+            if (bad_join < 5) printf("cancelling join mismatch %.9g %.9g: %.17g vs %.17g\n", h, l, j, j0);
+            ++bad_join;
+        }
+        ++n;
+    }
     printf("checked %lld values: split mismatches %lld, join mismatches %lld\n", n, bad_split, bad_join);
     return (bad_split || bad_join) ? 1 : 0;
 }
