@@ -109,12 +109,19 @@ def test_refined_inplace_general_rhs():
         np.testing.assert_array_equal(buf.cpu().numpy().reshape(grid.full_shape), want)
 
 
+# one size on the generic shared-memory FP32 transforms and one on the
+# register-resident ones (M = 64 ... 256, nt/2 = 32 ... 256)
+HOST_LOOP = "generic-kernels"
+DEVICE_LOOP = "register-kernels"
+
+
+@pytest.mark.parametrize("driver", [HOST_LOOP, DEVICE_LOOP])
 @pytest.mark.parametrize("scale", [1e-30, 1e-12, 1e12, 1e30])
-def test_refinement_at_extreme_data_scales(scale):
+def test_refinement_at_extreme_data_scales(scale, driver):
     """The solve is linear: data scaled by 1e+-12 stay on the FP32 path and
     give the scaled answer; at 1e+-30 FP32 cannot hold the residuals and the
     plan solves in FP64 (no refinement steps) -- the answer is right either way."""
-    grid = bi.Grid(2, (64, 64), 1.0, 0.1, 32)
+    grid = bi.Grid(2, (64, 64), 1.0, 0.1, 32 if driver == HOST_LOOP else 64)
     g = bi.random_general_rhs(grid, seed=37)[0]
     alpha = 1e-3
     want = O.solve_spectral(grid, Q.FORM_PQ, alpha, O.delta_rhs(grid, Q.FORM_PQ, alpha, g))
@@ -126,19 +133,21 @@ def test_refinement_at_extreme_data_scales(scale):
         assert iters == 0 and rel <= 1e-13
 
 
-def test_refined_n0_only():
-    grid = bi.Grid(2, (32, 32), 1.0, 0.1, 32)
+@pytest.mark.parametrize("driver", [HOST_LOOP, DEVICE_LOOP])
+def test_refined_n0_only(driver):
+    grid = bi.Grid(2, (32, 32), 1.0, 0.1, 32) if driver == HOST_LOOP else bi.Grid(2, (64, 128), 1.0, 0.1, 64)
     F = bi.random_general_rhs(grid, seed=32)
     full, _, _ = refine_solve(grid, Q.FORM_PQ, 1e-3, F, Q.RHS_GENERAL)
     y0, _, _ = refine_solve(grid, Q.FORM_PQ, 1e-3, F, Q.RHS_GENERAL, n0_only=True)
     np.testing.assert_allclose(y0[0], full[0], rtol=0, atol=1e-13 * np.abs(full).max())
 
 
+@pytest.mark.parametrize("driver", [HOST_LOOP, DEVICE_LOOP])
 @pytest.mark.parametrize("alpha", [1e-6, 1e-8, 1e-9])
-def test_refinement_is_never_silently_wrong(alpha):
+def test_refinement_is_never_silently_wrong(alpha, driver):
     """|omega| up to 1e9: the refinement either converges to the oracle's answer
     or reports QBVM_ERR_DIVERGED -- it never returns a wrong answer."""
-    grid = bi.Grid(2, (16, 16), 1.0, 0.1, 16)
+    grid = bi.Grid(2, (16, 16), 1.0, 0.1, 16) if driver == HOST_LOOP else bi.Grid(2, (64, 64), 1.0, 0.1, 64)
     g = bi.random_general_rhs(grid, seed=33)[0]
     want = O.solve_spectral(grid, Q.FORM_PQ, alpha, O.delta_rhs(grid, Q.FORM_PQ, alpha, g))
     try:
@@ -149,10 +158,25 @@ def test_refinement_is_never_silently_wrong(alpha):
     assert O.rel_l2(got, want) <= TOL, (iters, rel)
 
 
-def test_refinement_cap_reports_divergence():
+@pytest.mark.parametrize("driver", [HOST_LOOP, DEVICE_LOOP])
+def test_refinement_to_the_floor_ends_cleanly(driver):
+    """An unreachable tolerance: the corrections go on until they stop
+    contracting at the double-float floor (three or more corrections), then the
+    solve ends without an error and with the oracle's answer."""
+    grid = bi.Grid(2, (32, 32), 1.0, 0.1, 64) if driver == HOST_LOOP else bi.Grid(2, (64, 128), 1.0, 0.1, 64)
+    g = bi.random_general_rhs(grid, seed=35)[0]
+    alpha = 1e-3
+    want = O.solve_spectral(grid, Q.FORM_PQ, alpha, O.delta_rhs(grid, Q.FORM_PQ, alpha, g))
+    got, iters, rel = refine_solve(grid, Q.FORM_PQ, alpha, g, Q.RHS_DELTA, tol=1e-300)
+    assert iters >= 3 and rel <= 1e-10, (iters, rel)
+    assert O.rel_l2(got, want) <= TOL
+
+
+@pytest.mark.parametrize("driver", [HOST_LOOP, DEVICE_LOOP])
+def test_refinement_cap_reports_divergence(driver):
     """A one-step cap with an unreachable tolerance ends with QBVM_ERR_DIVERGED
     (did not reach the tolerance; the iterate is left in y)."""
-    grid = bi.Grid(2, (32, 32), 1.0, 0.1, 64)
+    grid = bi.Grid(2, (32, 32), 1.0, 0.1, 64) if driver == HOST_LOOP else bi.Grid(2, (64, 128), 1.0, 0.1, 64)
     g = bi.random_general_rhs(grid, seed=34)[0]
     with pytest.raises(Q.QbvmError) as ei:
         refine_solve(grid, Q.FORM_PQ, 1e-8, g, Q.RHS_DELTA, tol=1e-300, maxit=1)
