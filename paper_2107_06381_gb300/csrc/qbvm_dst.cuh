@@ -65,7 +65,9 @@ constexpr int DST_TILE = 2048;     // complex elements per (full-width) DST tile
 // the column separation then drop out (w'_j = 2 s_j (x_j + x_{M-j}) +
 // (x_j - x_{M-j}) is one fused multiply-add), 2 operations fewer per element;
 // the caller folds the exact power of two into its normalisation.
-template <typename R, typename TIN, int OMODE, int MAXB4, bool LDCG, bool X4 = false>
+// PDL: programmatic dependent launch (tables before the wait; the kernels of
+// the solve pipelines set it, the persistent sweep does not).
+template <typename R, typename TIN, int OMODE, int MAXB4, bool LDCG, bool X4 = false, bool PDL = false>
 __device__ __forceinline__ void dst_tile(const TIN* in, void* out, int n, int lm, int lw, long long outer,
                                          long long inner, long long tile, const cplx<R>* __restrict__ tw,
                                          const R* __restrict__ sn, unsigned char* smem_raw) {
@@ -80,9 +82,11 @@ __device__ __forceinline__ void dst_tile(const TIN* in, void* out, int n, int lm
     R* seg = ssn + (H + 2);                          // prefix-sum segment totals
     R* bufr = reinterpret_cast<R*>(buf);
 
+    if (PDL) pdl_trigger();
     for (int i = tid; i < M; i += nth) stw[i] = tw[i];
     for (int i = tid; i <= H; i += nth) ssn[i] = X4 ? R(2) * sn[i] : sn[i];
     for (int p = tid; p < W; p += nth) buf[p] = mkc(R(0), R(0));
+    if (PDL) pdl_wait();
 
     long long base_row = 0, o = 0, i0 = 0;
     int rows_here = ncol;

@@ -24,6 +24,24 @@ template <> struct C2<double> { using type = double2; };
 template <> struct C2<float>  { using type = float2;  };
 template <typename R> using cplx = typename C2<R>::type;
 
+// Programmatic dependent launch.  A kernel launched with programmatic stream
+// serialisation may start while the kernel before it in the stream finishes:
+// it signals at entry that its own successor may be scheduled
+// (pdl_trigger), loads its constant tables, and waits (pdl_wait) until the
+// predecessor has completed and its writes are visible before it touches any
+// buffer a predecessor writes.  In a kernel launched the ordinary way both are
+// no-ops.
+__device__ __forceinline__ void pdl_trigger() {
+#if defined(__CUDA_ARCH__) && __CUDA_ARCH__ >= 900
+    asm volatile("griddepcontrol.launch_dependents;" ::: "memory");
+#endif
+}
+__device__ __forceinline__ void pdl_wait() {
+#if defined(__CUDA_ARCH__) && __CUDA_ARCH__ >= 900
+    asm volatile("griddepcontrol.wait;" ::: "memory");
+#endif
+}
+
 __device__ __forceinline__ double2 mkc(double a, double b) { return make_double2(a, b); }
 __device__ __forceinline__ float2  mkc(float a, float b)   { return make_float2(a, b); }
 __device__ __forceinline__ double2 cadd(double2 a, double2 b) { return make_double2(a.x + b.x, a.y + b.y); }

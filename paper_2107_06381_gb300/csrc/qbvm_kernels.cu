@@ -62,6 +62,33 @@ static cudaError_t set_smem(K kern, size_t smem) {
     return cudaSuccess;
 }
 
+// Launch with programmatic stream serialisation (see pdl_wait): the kernel's
+// CTAs may be scheduled while its predecessor in the stream finishes, which
+// hides the launch and the table loads of the ~25 dependent launches of a
+// refined solve or the 5 of a y^0-only one.  Only kernels that call pdl_wait
+// before touching a predecessor's data are launched this way.
+template <typename... P, typename... A>
+static cudaError_t launch_pdl(void (*kern)(P...), unsigned grid, unsigned block, size_t smem, cudaStream_t s,
+                              A... args) {
+    cudaLaunchAttribute attr[1];
+    attr[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
+    attr[0].val.programmaticStreamSerializationAllowed = 1;
+    cudaLaunchConfig_t cfg = {};
+    cfg.gridDim = dim3(grid);
+    cfg.blockDim = dim3(block);
+    cfg.dynamicSmemBytes = smem;
+    cfg.stream = s;
+    cfg.attrs = attr;
+    cfg.numAttrs = 1;
+    return cudaLaunchKernelEx(&cfg, kern, args...);
+}
+
+#define QBVM_PDL(...)                                   \
+    do {                                                \
+        cudaError_t le__ = launch_pdl(__VA_ARGS__);     \
+        if (le__ != cudaSuccess) return le__;           \
+    } while (0)
+
 // SMs of the current device, queried once per device.
 static int device_sms() {
     static std::mutex mu;
@@ -84,8 +111,8 @@ __global__ void __launch_bounds__(TILE_THREADS)
 k_dst(const TIN* in, void* out, int n, int lm, int lw, long long outer, long long inner,
       const cplx<R>* __restrict__ tw, const R* __restrict__ sn) {
     extern __shared__ __align__(16) unsigned char smem_raw[];
-    dst_tile<R, TIN, OMODE, MAXB4, false, X4>(in, out, n, lm, lw, outer, inner, (long long)blockIdx.x, tw, sn,
-                                              smem_raw);
+    dst_tile<R, TIN, OMODE, MAXB4, false, X4, true>(in, out, n, lm, lw, outer, inner, (long long)blockIdx.x, tw,
+                                                    sn, smem_raw);
 }
 
 // The same tile with the transform length fixed at compile time (the tile
@@ -98,7 +125,7 @@ k_dst_ct(const TIN* in, void* out, long long outer, long long inner, const cplx<
     extern __shared__ __align__(16) unsigned char smem_raw[];
     constexpr int LW = 11 - LM;                     // 2^LM * 2^LW = DST_TILE complex values
     static_assert((1 << (LM + LW)) == DST_TILE, "DST tile size");
-    dst_tile<R, TIN, OMODE, DST_TILE / 4 / TILE_THREADS, false, X4>(in, out, (1 << LM) - 1, LM, LW, outer, inner,
+    dst_tile<R, TIN, OMODE, DST_TILE / 4 / TILE_THREADS, false, X4, true>(in, out, (1 << LM) - 1, LM, LW, outer, inner,
                                                                     (long long)blockIdx.x, tw, sn, smem_raw);
 }
 
@@ -108,7 +135,7 @@ static cudaError_t launch_dst_ct(const TIN* in, void* out, long long outer, long
     auto kern = k_dst_ct<R, TIN, OMODE, LM, X4>;
     cudaError_t e = set_smem(kern, smem);
     if (e != cudaSuccess) return e;
-    kern<<<(unsigned)blocks, TILE_THREADS, smem, s>>>(in, out, outer, inner, reinterpret_cast<const cplx<R>*>(tw),
+    QBVM_PDL(kern, (unsigned)blocks, TILE_THREADS, smem, s, in, out, outer, inner, reinterpret_cast<const cplx<R>*>(tw),
                                                       reinterpret_cast<const R*>(sn));
     return cudaGetLastError();
 }
@@ -133,7 +160,7 @@ static cudaError_t launch_dst_reg(const TIN* in, void* out, long long outer, lon
     cudaError_t e = set_smem(kern, smem);
     if (e != cudaSuccess) return e;
     const long long blocks = XAX ? (outer + rd::NCOL - 1) / rd::NCOL : outer * ((inner + rd::NCOL - 1) / rd::NCOL);
-    kern<<<(unsigned)blocks, rd::threads<LM>(), smem, s>>>(in, out, outer, inner,
+    QBVM_PDL(kern, (unsigned)blocks, rd::threads<LM>(), smem, s, in, out, outer, inner,
                                                            reinterpret_cast<const float2*>(tw),
                                                            reinterpret_cast<const float*>(sn));
     return cudaGetLastError();
@@ -192,7 +219,7 @@ cudaError_t launch_dst(const TIN* in, void* out, int n, int lm, long long outer,
     auto kern = k_dst<R, TIN, OMODE, DST_TILE / 4 / TILE_THREADS, X4>;
     cudaError_t e = set_smem(kern, smem);
     if (e != cudaSuccess) return e;
-    kern<<<(unsigned)blocks, TILE_THREADS, smem, s>>>(in, out, n, lm, lw, outer, inner,
+    QBVM_PDL(kern, (unsigned)blocks, TILE_THREADS, smem, s, in, out, n, lm, lw, outer, inner,
                                                       reinterpret_cast<const cplx<R>*>(tw),
                                                       reinterpret_cast<const R*>(sn));
     return cudaGetLastError();
@@ -240,7 +267,9 @@ __device__ __forceinline__ void time_solve_tile(const R* in, R* out, long long N
     const int tid = threadIdx.x, nth = blockDim.x;
     const long long l0 = tile * W;
 
+    pdl_trigger();
     for (int i = tid; i < H; i += nth) stw[i] = tw[i];
+    pdl_wait();                                          // the input is a predecessor's output
     if (delta_rhs) {
         // f = f^0 e_0: Step (a) of a single level-0 value is that value (times
         // gamma^0) at every frequency, so the forward transform is not computed
@@ -403,12 +432,14 @@ k_time_solve_reg(const float* in, float* out, long long Nx, const float2* __rest
     float2* fbuf = sak + H;                                            // transpose buffers ...
     float* st = reinterpret_cast<float*>(fbuf);                        // ... aliasing the tile [NT][RS]
     const int tid = threadIdx.x;
+    pdl_trigger();
     for (int i = tid; i < H; i += NTH) {
         stw[i] = tw[i];
         sgp[i] = gpow[i];
         sgi[i] = gipw[i];
         sak[i] = ak[i];
     }
+    pdl_wait();                                                        // the input is a predecessor's output
     const long long l0 = (long long)blockIdx.x * TS_MODES;
     {   // load phase: rows of TS_MODES consecutive modes, a batch of loads in flight per thread
         const int cc = tid % TS_MODES, r0 = tid / TS_MODES;
@@ -533,7 +564,7 @@ static cudaError_t launch_time_solve_reg(const float* in, float* out, const Tabl
     cudaError_t e = set_smem(kern, smem);
     if (e != cudaSuccess) return e;
     const long long blocks = (tb.Nx + TS_MODES - 1) / TS_MODES;
-    kern<<<(unsigned)blocks, TS_MODES * TsCfg<LH>::N2, smem, s>>>(
+    QBVM_PDL(kern, (unsigned)blocks, TS_MODES * TsCfg<LH>::N2, smem, s, 
         in, out, tb.Nx, reinterpret_cast<const float2*>(tb.tw_t32), reinterpret_cast<const float2*>(tb.gpow32),
         reinterpret_cast<const float2*>(tb.gipw32), reinterpret_cast<const float2*>(tb.ak32),
         reinterpret_cast<const float*>(tb.lamtau32), cnorm, (float)tb.rho_h, (float)tb.rho_hinv, delta_rhs, n0_only);
@@ -582,6 +613,8 @@ __global__ void k_y0fac_gen(const double2* __restrict__ dk, const double* __rest
 
 __global__ void k_mul_modes(const double* __restrict__ x, const double* __restrict__ fac, double* __restrict__ y,
                             long long n) {
+    pdl_trigger();
+    pdl_wait();
     for (long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (long long)gridDim.x * blockDim.x)
         y[i] = fac[i] * x[i];
 }
@@ -597,7 +630,7 @@ cudaError_t launch_make_y0fac(const Tables& tb, double cnorm, double* out, cudaS
 cudaError_t launch_mul_modes(const double* x, const double* fac, double* y, long long n, cudaStream_t s) {
     long long blocks = (n + 255) / 256;
     if (blocks > 152 * 32) blocks = 152 * 32;
-    k_mul_modes<<<(unsigned)blocks, 256, 0, s>>>(x, fac, y, n);
+    QBVM_PDL(k_mul_modes, (unsigned)blocks, 256, 0, s, x, fac, y, n);
     return cudaGetLastError();
 }
 
@@ -650,7 +683,7 @@ cudaError_t launch_time_solve(const R* in, R* out, const Tables& tb, double cnor
         auto kern = k_time_solve_ct<R, MB, LHV>;                                                               \
         cudaError_t e = set_smem(kern, smem);                                                                  \
         if (e != cudaSuccess) return e;                                                                        \
-        kern<<<(unsigned)blocks, TILE_THREADS, smem, s>>>(in, out, tb.Nx, pick(tb.tw_t, tb.tw_t32),            \
+        QBVM_PDL(kern, (unsigned)blocks, TILE_THREADS, smem, s, in, out, tb.Nx, pick(tb.tw_t, tb.tw_t32),            \
                                                           pick(tb.gpow, tb.gpow32), pick(tb.gipw, tb.gipw32),  \
                                                           pick(tb.ak, tb.ak32), lt, R(cnorm),                  \
                                                           pick(tb.gpowr, tb.gpowr32), pick(tb.gipr, tb.gipr32), \
@@ -670,7 +703,7 @@ cudaError_t launch_time_solve(const R* in, R* out, const Tables& tb, double cnor
     auto kern = k_time_solve<R, MB>;
     cudaError_t e = set_smem(kern, smem);
     if (e != cudaSuccess) return e;
-    kern<<<(unsigned)blocks, TILE_THREADS, smem, s>>>(in, out, tb.Nx, lh, lw, pick(tb.tw_t, tb.tw_t32),
+    QBVM_PDL(kern, (unsigned)blocks, TILE_THREADS, smem, s, in, out, tb.Nx, lh, lw, pick(tb.tw_t, tb.tw_t32),
                                                       pick(tb.gpow, tb.gpow32), pick(tb.gipw, tb.gipw32),
                                                       pick(tb.ak, tb.ak32), lt, R(cnorm), pick(tb.gpowr, tb.gpowr32),
                                                       pick(tb.gipr, tb.gipr32), qv, delta_rhs, n0_only);
@@ -701,7 +734,7 @@ cudaError_t launch_time_solve_batched(const double* in, double* out, const Table
         auto kern = k_time_solve_batched<MB, LHV>;                                                               \
         cudaError_t e = set_smem(kern, smem);                                                                    \
         if (e != cudaSuccess) return e;                                                                          \
-        kern<<<(unsigned)blocks, TILE_THREADS, smem, s>>>(in, out, tb.Nx, lh, lw, tiles, in_stride, out_stride,  \
+        QBVM_PDL(kern, (unsigned)blocks, TILE_THREADS, smem, s, in, out, tb.Nx, lh, lw, tiles, in_stride, out_stride,  \
                                                           tb.tw_t, gpow, gipw, gpowr, gipr, qinv, delta_rhs,     \
                                                           n0_only);                                              \
         return cudaGetLastError();                                                                               \
@@ -1057,6 +1090,8 @@ k_residual(const double* __restrict__ y, const double* __restrict__ f, int delta
 }
 
 __global__ void k_reduce_pairs(const double* partials, int n, double* sums) {
+    pdl_trigger();
+    pdl_wait();
     __shared__ double sh[32];
     double a = 0.0, b = 0.0;
     for (int i = threadIdx.x; i < n; i += blockDim.x) {
@@ -1090,6 +1125,8 @@ template <bool EQ>
 __global__ void __launch_bounds__(RES_THREADS)
 k_residual_df(const float2* __restrict__ y, const double* __restrict__ f, int delta_rhs, int nt, int nx, int ny,
               int nz, DfCoef k, double f0_scale, float* __restrict__ r_out, double* partials) {
+    pdl_trigger();
+    pdl_wait();
     __shared__ double sh[32];
     const long long Nx = (long long)nx * ny * nz;
     const long long pl = (long long)nx * ny;
@@ -1190,6 +1227,8 @@ template <bool EQ, int DIMS>
 __global__ void __launch_bounds__(RES_THREADS)
 k_residual_df4(const float2* __restrict__ y, const double* __restrict__ f, int delta_rhs, int nt, int nx, int ny,
                int nz, DfCoef k, double f0_scale, float* __restrict__ r_out, double* partials) {
+    pdl_trigger();
+    pdl_wait();
     __shared__ double sh[32];
     const long long Nx = (long long)nx * ny * nz, N = (long long)nt * Nx, pl = (long long)nx * ny;
     const long long ngroups = (N + 3) >> 2;
@@ -1330,6 +1369,8 @@ k_residual_df4(const float2* __restrict__ y, const double* __restrict__ f, int d
 
 // In place: a double-float array (8 bytes per value) becomes the FP64 array.
 __global__ void k_df_to_double(void* buf, long long n) {
+    pdl_trigger();
+    pdl_wait();
     const float2* src = reinterpret_cast<const float2*>(buf);
     double* dst = reinterpret_cast<double*>(buf);
     for (long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (long long)gridDim.x * blockDim.x) {
@@ -1346,6 +1387,8 @@ __global__ void k_df_to_double(void* buf, long long n) {
 // Requires a 16-byte aligned buffer; values past the last group of four are
 // taken one per thread by the first threads of the grid.
 __global__ void __launch_bounds__(256) k_df_to_double4(void* buf, long long n) {
+    pdl_trigger();
+    pdl_wait();
     const long long ng = n >> 2;
     const long long tid = (long long)blockIdx.x * blockDim.x + threadIdx.x;
     const long long stride = (long long)gridDim.x * blockDim.x;
@@ -1389,30 +1432,30 @@ cudaError_t launch_residual_df(const void* y_df, const double* f, int delta_rhs,
         const double fs = -tb.omega * it;
         const int nx = tb.n[0], ny = tb.n[1], nz = tb.n[2];
         if (tb.dim == 1) {
-            k_residual_df4<true, 1><<<(unsigned)nb, RES_THREADS, 0, s>>>(yy, f, delta_rhs, tb.nt, nx, ny, nz, k, fs, r_out, partials);
+            QBVM_PDL(k_residual_df4<true, 1>, (unsigned)nb, RES_THREADS, 0, s, yy, f, delta_rhs, tb.nt, nx, ny, nz, k, fs, r_out, partials);
         } else if (tb.dim == 2) {
-            if (eq) k_residual_df4<true, 2><<<(unsigned)nb, RES_THREADS, 0, s>>>(yy, f, delta_rhs, tb.nt, nx, ny, nz, k, fs, r_out, partials);
-            else k_residual_df4<false, 2><<<(unsigned)nb, RES_THREADS, 0, s>>>(yy, f, delta_rhs, tb.nt, nx, ny, nz, k, fs, r_out, partials);
+            if (eq) QBVM_PDL(k_residual_df4<true, 2>, (unsigned)nb, RES_THREADS, 0, s, yy, f, delta_rhs, tb.nt, nx, ny, nz, k, fs, r_out, partials);
+            else QBVM_PDL(k_residual_df4<false, 2>, (unsigned)nb, RES_THREADS, 0, s, yy, f, delta_rhs, tb.nt, nx, ny, nz, k, fs, r_out, partials);
         } else {
-            if (eq) k_residual_df4<true, 3><<<(unsigned)nb, RES_THREADS, 0, s>>>(yy, f, delta_rhs, tb.nt, nx, ny, nz, k, fs, r_out, partials);
-            else k_residual_df4<false, 3><<<(unsigned)nb, RES_THREADS, 0, s>>>(yy, f, delta_rhs, tb.nt, nx, ny, nz, k, fs, r_out, partials);
+            if (eq) QBVM_PDL(k_residual_df4<true, 3>, (unsigned)nb, RES_THREADS, 0, s, yy, f, delta_rhs, tb.nt, nx, ny, nz, k, fs, r_out, partials);
+            else QBVM_PDL(k_residual_df4<false, 3>, (unsigned)nb, RES_THREADS, 0, s, yy, f, delta_rhs, tb.nt, nx, ny, nz, k, fs, r_out, partials);
         }
         cudaError_t e = cudaGetLastError();
         if (e != cudaSuccess) return e;
-        k_reduce_pairs<<<1, 1024, 0, s>>>(partials, (int)nb, sums);
+        QBVM_PDL(k_reduce_pairs, 1, 1024, 0, s, partials, (int)nb, sums);
         return cudaGetLastError();
     }
     if (eq)
-        k_residual_df<true><<<nblocks, RES_THREADS, 0, s>>>(reinterpret_cast<const float2*>(y_df), f, delta_rhs, tb.nt,
+        QBVM_PDL(k_residual_df<true>, nblocks, RES_THREADS, 0, s, reinterpret_cast<const float2*>(y_df), f, delta_rhs, tb.nt,
                                                             tb.n[0], tb.n[1], tb.n[2], k, -tb.omega * it, r_out,
                                                             partials);
     else
-        k_residual_df<false><<<nblocks, RES_THREADS, 0, s>>>(reinterpret_cast<const float2*>(y_df), f, delta_rhs,
+        QBVM_PDL(k_residual_df<false>, nblocks, RES_THREADS, 0, s, reinterpret_cast<const float2*>(y_df), f, delta_rhs,
                                                              tb.nt, tb.n[0], tb.n[1], tb.n[2], k, -tb.omega * it,
                                                              r_out, partials);
     cudaError_t e = cudaGetLastError();
     if (e != cudaSuccess) return e;
-    k_reduce_pairs<<<1, 1024, 0, s>>>(partials, nblocks, sums);
+    QBVM_PDL(k_reduce_pairs, 1, 1024, 0, s, partials, nblocks, sums);
     return cudaGetLastError();
 }
 
@@ -1421,13 +1464,13 @@ cudaError_t launch_df_to_double(void* buf, long long n, cudaStream_t s) {
         long long blocks = ((n >> 2) + 255) / 256;
         if (blocks > 152 * 8) blocks = 152 * 8;
         if (blocks < 1) blocks = 1;
-        k_df_to_double4<<<(unsigned)blocks, 256, 0, s>>>(buf, n);
+        QBVM_PDL(k_df_to_double4, (unsigned)blocks, 256, 0, s, buf, n);
         return cudaGetLastError();
     }
     long long blocks = (n + 1023) / 1024;
     if (blocks > 152 * 32) blocks = 152 * 32;
     if (blocks < 1) blocks = 1;
-    k_df_to_double<<<(unsigned)blocks, 256, 0, s>>>(buf, n);
+    QBVM_PDL(k_df_to_double, (unsigned)blocks, 256, 0, s, buf, n);
     return cudaGetLastError();
 }
 
@@ -1447,7 +1490,7 @@ cudaError_t launch_residual(const double* y, const double* f, int delta_rhs, con
                                                partials, r_out);
     cudaError_t e = cudaGetLastError();
     if (e != cudaSuccess) return e;
-    k_reduce_pairs<<<1, 1024, 0, s>>>(partials, nblocks, sums);
+    QBVM_PDL(k_reduce_pairs, 1, 1024, 0, s, partials, nblocks, sums);
     return cudaGetLastError();
 }
 

@@ -142,8 +142,10 @@ __device__ __forceinline__ void tile(const TIN* in, void* out, long long outer, 
     float* ssn = reinterpret_cast<float*>(stw + M);
     const int tid = threadIdx.x;
 
+    pdl_trigger();
     for (int i = tid; i < M; i += NTH) stw[i] = tw[i];
     for (int i = tid; i <= H; i += NTH) ssn[i] = sn[i];
+    pdl_wait();                                      // the input is a predecessor's output
 
     // ---- load phase (CTA-wide): each thread issues a batch of global loads
     // before it scatters them into the staging area
