@@ -151,16 +151,22 @@ int qbvm_plan(const qbvm_desc* desc, qbvm_plan_t** out);
  * rhs_kind GENERAL (FP32_REFINE then copies F into plan memory first, since
  * the refinement re-reads it).  FP32_REFINE solves data whose root-mean-square
  * magnitude lies outside [1e-18, 1e28] (where FP32 cannot carry the residuals)
- * with the FP64 pipeline; last_refine_iters is then 0.  Errors: BAD_ARG (NULL
- * arguments, mixed host/device), DIVERGED (FP32_REFINE only; y holds the last
- * iterate), NONFINITE, CUDA. */
+ * with the FP64 pipeline; last_refine_iters is then 0, and so it does data
+ * FP32 cannot hold at all (finite values beyond its range, or so small that
+ * every one flushes to zero).  Non-finite input: the FP64 solve is
+ * asynchronous and carries NaN / Inf through by IEEE arithmetic (qbvm_residual
+ * then reports NONFINITE); the FP32_REFINE solve, which synchronises, returns
+ * NONFINITE for NaN or Inf in g_or_F.  Errors: BAD_ARG (NULL arguments, mixed
+ * host/device), DIVERGED (FP32_REFINE only; y holds the last iterate),
+ * NONFINITE, CUDA. */
 int qbvm_solve(qbvm_plan_t* plan, const double* g_or_F, double* y, int n0_only, void* stream);
 
 /* qbvm_residual -- the relative all-at-once residual ||f - A y||_2 / ||f||_2
  * in FP64 (A applied as the stencil of eq. 3.3/3.6 without assembling it),
  * for y with all nt levels and f built from `g_or_F` as in qbvm_solve.
  * Synchronises `stream` and writes the scalar to *rel_norm_out (host).
- * Errors: BAD_ARG, CUDA. */
+ * Errors: BAD_ARG, NONFINITE (NaN or Inf in y or f: a sum of squares is not
+ * finite), CUDA. */
 int qbvm_residual(qbvm_plan_t* plan, const double* y, const double* g_or_F,
                   double* rel_norm_out, void* stream);
 

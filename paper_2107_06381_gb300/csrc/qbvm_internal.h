@@ -114,6 +114,9 @@ cudaError_t launch_residual(const double* y, const double* f, int delta_rhs, con
                             const double h2inv[3], double* partials, int nblocks, double* sums,
                             double* r_out, cudaStream_t s);
 int residual_blocks(const Tables& tb);
+// flags[0] = 1 if x[0..n) holds a NaN or an infinity, flags[1] = 1 if any
+// value is nonzero (two device ints).
+cudaError_t launch_classify(const double* x, long long n, int* flags, cudaStream_t s);
 
 // Double-float residual of the refinement: y_df is a (hi, lo) float2 array,
 // f FP64 (F, or g for the delta right-hand side); writes r.hi (FP32) to r_out

@@ -1474,6 +1474,30 @@ cudaError_t launch_df_to_double(void* buf, long long n, cudaStream_t s) {
     return cudaGetLastError();
 }
 
+// flags[0] = 1 if any of x[0..n) is NaN or infinite (exponent field all
+// ones), flags[1] = 1 if any is nonzero; tested on the words of each value
+// (integer pipes).
+__global__ void k_classify(const double* __restrict__ x, long long n, int* flags) {
+    int bad = 0, nonzero = 0;
+    for (long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (long long)gridDim.x * blockDim.x) {
+        const unsigned int h = qbvm_dhi(x[i]), l = qbvm_dlo(x[i]);
+        bad |= ((h >> 20) & 0x7FFu) == 0x7FFu;
+        nonzero |= ((h << 1) | l) != 0u;
+    }
+    if (__syncthreads_or(bad) && threadIdx.x == 0) atomicOr(flags, 1);
+    if (__syncthreads_or(nonzero) && threadIdx.x == 0) atomicOr(flags + 1, 1);
+}
+
+cudaError_t launch_classify(const double* x, long long n, int* flags, cudaStream_t s) {
+    cudaError_t e = cudaMemsetAsync(flags, 0, 2 * sizeof(int), s);
+    if (e != cudaSuccess) return e;
+    long long blocks = (n + 255) / 256;
+    if (blocks > 152 * 8) blocks = 152 * 8;
+    if (blocks < 1) blocks = 1;
+    k_classify<<<(unsigned)blocks, 256, 0, s>>>(x, n, flags);
+    return cudaGetLastError();
+}
+
 int residual_blocks(const Tables& tb) {
     long long rows = (long long)tb.nt * tb.n[1] * tb.n[2];
     long long b = rows;

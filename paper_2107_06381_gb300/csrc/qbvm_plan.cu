@@ -12,6 +12,8 @@
 #include <new>
 #include <vector>
 
+#include <nvtx3/nvToolsExt.h>
+
 #include "qbvm.h"
 #include "qbvm_internal.h"
 
@@ -38,6 +40,7 @@ struct qbvm_plan {
     // FP32 refinement workspace
     float* f32 = nullptr;         // [nt][Nx] FP32 work array (and the residual's r.hi)
     double* fcopy = nullptr;      // FP32_REFINE: copy of an F that aliases y
+    int* flag = nullptr;          // FP32_REFINE: non-finite input test
     // host-pointer solves: a copy stream and events that pipeline the staging
     cudaStream_t copy_stream = nullptr;
     cudaStream_t aux_stream = nullptr;   // second compute stream for alternate chunks
@@ -227,15 +230,20 @@ cudaEvent_t take_event(qbvm_plan_t* p) {
 }
 
 // Brackets one kernel launch with events when the plan is profiling.
+// One stage of a solve: an NVTX range around its launches (header-only NVTX;
+// a no-op without a tool attached) and, while profiling is on, CUDA events
+// on the stream around its kernel.
 struct Span {
     qbvm_plan_t* p;
     const char* name;
     cudaStream_t s;
     cudaEvent_t a = nullptr;
     Span(qbvm_plan_t* p_, const char* n, cudaStream_t s_) : p(p_), name(n), s(s_) {
+        nvtxRangePushA(n);
         if (p->profiling && (a = take_event(p)) != nullptr) cudaEventRecord(a, s);
     }
     ~Span() {
+        nvtxRangePop();
         if (!a) return;
         cudaEvent_t b = take_event(p);
         if (!b) {
@@ -435,7 +443,25 @@ int solve_fp32r_dev(qbvm_plan_t* p, const double* in, double* y, int n0_only, cu
             first = false;
             const double cnt = (double)tb.Nx * (delta ? 1 : tb.nt);
             const double rms = std::sqrt(fn2 / cnt);
-            if (rc == QBVM_ERR_NONFINITE || (rms > 0 && (rms < FP32_RMS_LO || rms > FP32_RMS_HI))) {
+            bool fp64 = rms > 0 && (rms < FP32_RMS_LO || rms > FP32_RMS_HI);
+            if (rc == QBVM_ERR_NONFINITE || fn2 == 0.0) {
+                // NaN or Inf in the input itself, or finite data FP32 cannot hold
+                // (beyond its range, or so small that every value flushes to zero):
+                // the former is an error, the latter goes to the FP64 pipeline
+                if (!p->flag) {
+                    rc = dalloc(p, &p->flag, 2);
+                    if (rc) return rc;
+                }
+                int fl[2] = {0, 0};
+                CK(qbvm::launch_classify(in, (long long)cnt, p->flag, s));
+                CK(cudaMemcpyAsync(fl, p->flag, sizeof(fl), cudaMemcpyDeviceToHost, s));
+                CK(cudaStreamSynchronize(s));
+                ++launches;
+                if (fl[0]) return QBVM_ERR_NONFINITE;
+                fp64 = fp64 || rc == QBVM_ERR_NONFINITE || fl[1];
+                rc = QBVM_OK;
+            }
+            if (fp64) {
                 rc = solve_fp64_dev(p, in, y, n0_only, s);     // wreal exists for n0_only (solve_dev)
                 if (rc) return rc;
                 double r64 = 0.0;
@@ -867,6 +893,10 @@ static int solve_fp64_host(qbvm_plan_t* p, const double* hin, double* hout, int 
 }
 
 int qbvm_solve(qbvm_plan_t* p, const double* g_or_F, double* y, int n0_only, void* stream) {
+    struct Range {
+        Range() { nvtxRangePushA("qbvm_solve"); }
+        ~Range() { nvtxRangePop(); }
+    } range_;
     if (!p || !g_or_F || !y) return QBVM_ERR_BAD_ARG;
     cudaStream_t s = static_cast<cudaStream_t>(stream);
     const int kin = ptr_kind(g_or_F), kout = ptr_kind(y);

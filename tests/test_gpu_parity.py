@@ -323,3 +323,21 @@ def test_y0_only_full_size_delta(form):
     y0 = gpu_solve(grid, form, alpha, p.g_delta, Q.RHS_DELTA, n0_only=True)
     want = O.solve_spectral(grid, form, alpha, O.delta_rhs(grid, form, alpha, p.g_delta), levels=[0])
     assert O.rel_l2(y0, want) <= TOL
+
+
+@pytest.mark.parametrize("bad", [float("nan"), float("inf")], ids=["nan", "inf"])
+def test_nonfinite_input_fp64_propagates_and_residual_reports(bad):
+    """The asynchronous FP64 solve carries an injected NaN / Inf through by IEEE
+    arithmetic (no status without a synchronisation); qbvm_residual reports it."""
+    grid = bi.Grid(2, (16, 16), 1.0, 0.1, 16)
+    g = bi.random_general_rhs(grid, seed=15)[0].copy()
+    g.flat[7] = bad
+    with Q.Plan(2, grid.M, grid.L, grid.T, grid.nt, Q.FORM_PQ, 1e-3, 0.0, Q.FP64, Q.RHS_DELTA) as plan:
+        gd = torch.as_tensor(g.ravel()).cuda()
+        y = torch.zeros(grid.unknowns, dtype=torch.float64, device="cuda")
+        plan.solve(gd, y)
+        torch.cuda.synchronize()
+        assert not bool(torch.isfinite(y).all())
+        with pytest.raises(Q.QbvmError) as ei:
+            plan.residual(y, gd)
+        assert ei.value.code == -3

@@ -208,3 +208,42 @@ def test_c3_full_size_refined_sampled_levels():
     err = O.rel_l2(got[levels], want)
     print(f"C3: refinement steps {iters}, rel residual {rel:.2e}, rel err vs oracle (sampled) {err:.2e}")
     assert err <= TOL
+
+
+@pytest.mark.parametrize("driver", [HOST_LOOP, DEVICE_LOOP])
+@pytest.mark.parametrize("bad", [float("nan"), float("inf"), -float("inf")], ids=["nan", "inf", "-inf"])
+@pytest.mark.parametrize("rhs_kind", [Q.RHS_DELTA, Q.RHS_GENERAL], ids=["delta", "general"])
+@pytest.mark.parametrize("n0_only", [False, True], ids=["full", "y0"])
+def test_nonfinite_input_is_reported(bad, rhs_kind, n0_only, driver):
+    """A NaN or an infinity injected into the input: QBVM_ERR_NONFINITE, never a
+    silent result (full solution or y^0 alone)."""
+    grid = bi.Grid(2, (16, 16), 1.0, 0.1, 16) if driver == HOST_LOOP else bi.Grid(2, (64, 64), 1.0, 0.1, 64)
+    F = bi.random_general_rhs(grid, seed=38)
+    rhs = (F[0] if rhs_kind == Q.RHS_DELTA else F).copy()
+    rhs.flat[rhs.size // 3] = bad
+    with pytest.raises(Q.QbvmError) as ei:
+        refine_solve(grid, Q.FORM_PQ, 1e-3, rhs, rhs_kind, n0_only=n0_only)
+    assert ei.value.code == -3
+
+
+@pytest.mark.parametrize("driver", [HOST_LOOP, DEVICE_LOOP])
+@pytest.mark.parametrize("scale", [1e-300, 1e100])
+@pytest.mark.parametrize("n0_only", [False, True], ids=["full", "y0"])
+def test_data_fp32_cannot_hold_takes_the_fp64_pipeline(scale, n0_only, driver):
+    """Finite data that flushes to zero in FP32 (1e-300) or overflows it (1e100;
+    its squares still fit FP64's range for the residual): solved by the FP64
+    pipeline, with the scaled answer."""
+    grid = bi.Grid(2, (16, 16), 1.0, 0.1, 16) if driver == HOST_LOOP else bi.Grid(2, (64, 64), 1.0, 0.1, 64)
+    g = bi.random_general_rhs(grid, seed=39)[0]
+    alpha = 1e-3
+    want = O.solve_spectral(grid, Q.FORM_PQ, alpha, O.delta_rhs(grid, Q.FORM_PQ, alpha, g),
+                            levels=[0] if n0_only else None)
+    got, iters, _ = refine_solve(grid, Q.FORM_PQ, alpha, g * scale, Q.RHS_DELTA, n0_only=n0_only)
+    assert iters == 0
+    assert O.rel_l2(got / scale, want) <= TOL
+
+
+def test_zero_input_gives_zero():
+    grid = bi.Grid(2, (64, 64), 1.0, 0.1, 64)
+    got, _, rel = refine_solve(grid, Q.FORM_PQ, 1e-3, np.zeros(grid.shape), Q.RHS_DELTA)
+    assert not got.any() and rel == 0.0
