@@ -49,6 +49,8 @@ struct SwInst {
     int tiles_gx, tiles_gy, tiles_spec, tiles_fin, tiles_iy, tiles_ix;
     int has_z0, has_y0;
     double delta, tau_dp, tau, wnorm, zscale;
+    double sscale, sinv;         // 2^-floor(log2 delta) and its inverse: the scan runs on
+                                 // g, z0 scaled so that delta ~ 1 (exact; any data scale)
     const double* g;
     const double* z0;
     double* y0;
@@ -130,8 +132,8 @@ __device__ void spectral_tile(const SwInst& I, int tile, unsigned char* smem) {
             int lx = (int)(l % I.nx), ly = (int)(l / I.nx);
             double lt = __ldcg(I.lamx + lx) + (I.dim == 2 ? __ldcg(I.lamy + ly) : 0.0);
             lam[q] = R(lt);
-            gh[q] = R(__ldcg(I.ghat + l));
-            if (I.has_z0) zh[q] = R(__ldcg(I.zhat + l) * I.zscale);
+            gh[q] = R(__ldcg(I.ghat + l) * I.sscale);
+            if (I.has_z0) zh[q] = R(__ldcg(I.zhat + l) * I.zscale * I.sscale);
         }
     }
     for (int a = 0; a < I.n_alpha; ++a) {
@@ -180,18 +182,19 @@ __device__ void pick_alpha(const SwInst& I) {
     int pick = -1, best = 0, closest = 0;
     double bestv = INFINITY, closev = INFINITY;
     for (int a = 0; a < I.n_alpha; ++a) {
+        // stats are of the scaled data: compare and rank scaled, report unscaled
         double d2 = __ldcg(I.stats + 2 * a), e2 = __ldcg(I.stats + 2 * a + 1);
         double dsc = I.coef[a] * sqrt(I.wnorm * d2);
-        I.disc[a] = dsc;
+        I.disc[a] = dsc * I.sinv;
         if (I.has_z0) {
             double ev = sqrt(I.wnorm * e2);
-            I.err[a] = ev;
+            I.err[a] = ev * I.sinv;
             if (ev < bestv) {
                 bestv = ev;
                 best = a;
             }
         }
-        if (dsc <= I.tau_dp * I.delta && (pick < 0 || I.alphas[a] > I.alphas[pick])) pick = a;
+        if (dsc <= I.tau_dp * (I.delta * I.sscale) && (pick < 0 || I.alphas[a] > I.alphas[pick])) pick = a;
         if (dsc < closev) {
             closev = dsc;
             closest = a;
@@ -636,6 +639,12 @@ int qbvm_sweep_plan(const qbvm_sweep_desc* d, qbvm_sweep_t** out) {
         I.H = in.nt / 2;
         I.n_alpha = na;
         I.delta = in.delta;
+        {
+            int e = -std::ilogb(in.delta);
+            e = e < -1000 ? -1000 : (e > 1000 ? 1000 : e);
+            I.sscale = std::ldexp(1.0, e);
+            I.sinv = std::ldexp(1.0, -e);
+        }
         I.tau_dp = d->tau_dp;
         I.tau = in.T / (in.nt - 1);
         const double hx = in.L / in.m[0], hy = in.dim == 2 ? in.L / in.m[1] : 1.0;

@@ -60,16 +60,16 @@ def _oracle_sweep(grid, form, z0, gd, delta, alphas):
     return disc, err, pick, ys
 
 
-def _run_sweep(problems, precision, n_alpha=8, autotune=False):
+def _run_sweep(problems, precision, n_alpha=8, autotune=False, bases=None):
     dev = []
     insts = []
-    for grid, form, z0, gd, delta in problems:
+    for i, (grid, form, z0, gd, delta) in enumerate(problems):
         g = torch.as_tensor(gd.ravel(), dtype=torch.float64).cuda()
         z = torch.as_tensor(z0.ravel(), dtype=torch.float64).cuda()
         y0 = torch.zeros(grid.Nx, dtype=torch.float64, device="cuda")
         dev.append((g, z, y0))
         insts.append(dict(dim=grid.dim, m=grid.M, L=grid.L, T=grid.T, nt=grid.nt, form=form, delta=delta,
-                          g=g, z0=z, y0=y0))
+                          g=g, z0=z, y0=y0, **({} if bases is None else {"alpha_base": bases[i]})))
     sw = Q.Sweep(insts, n_alpha=n_alpha, log10_lo=-1.5, log10_hi=1.5, tau_dp=TAU_DP, precision=precision)
     if autotune:
         sw.autotune(repeats=2)
@@ -164,3 +164,28 @@ def test_bounded_wait_gives_up_and_the_context_survives(ctas):
         torch.cuda.synchronize()
     want = O.solve_spectral(grid, O.PQ, 1e-3, O.delta_rhs(grid, O.PQ, 1e-3, g))
     assert O.rel_l2(y.cpu().numpy(), want) <= 1e-10
+
+
+@pytest.mark.parametrize("precision", [Q.FP64, Q.FP32_REFINE], ids=["fp64", "fp32"])
+def test_sweep_is_scale_invariant(precision):
+    """At fixed alphas the sweep is linear in the data: g, z0 and delta scaled
+    together by 1e-300 ... 1e200 (beyond FP32's range both ways, and past where
+    FP64 squares overflow) give the same picks and the scaled discrepancies,
+    errors and y^0.  The scan works on data scaled by a power of two near 1/delta."""
+    problems = _problems()
+    bases = [O.alpha_apriori(form, delta, grid.tau) for grid, form, z0, gd, delta in problems]
+    sw, (alphas, disc, err, pick), y0s, _ = _run_sweep(problems, precision, bases=bases)
+    sw.close()
+    rtol = 1e-9 if precision == Q.FP64 else 1e-4      # the scaled inputs round differently
+    for scale in (1e-300, 1e-20, 1e20, 1e200):
+        scaled = [(grid, form, z0 * scale, gd * scale, delta * scale) for grid, form, z0, gd, delta in problems]
+        sw2, (a2, d2, e2, p2), y2, _ = _run_sweep(scaled, precision, bases=bases)     # the same alphas
+        try:
+            np.testing.assert_allclose(a2, alphas, rtol=1e-14)
+            np.testing.assert_array_equal(p2[:, 0], pick[:, 0])
+            np.testing.assert_allclose(d2 / scale, disc, rtol=rtol)
+            np.testing.assert_allclose(e2 / scale, err, rtol=rtol)
+            for u, v in zip(y2, y0s):
+                np.testing.assert_allclose(u / scale, v, rtol=0, atol=1e-10 * np.abs(v).max())
+        finally:
+            sw2.close()
