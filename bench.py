@@ -42,8 +42,8 @@ UNIT = "unknowns/s"
 FP64_PEAK_TOPS = 152 * 2 * 2.07e9 / 1e12
 # DRAM bytes (read + write) per launch from one ncu capture of the current
 # kernels on this workload (profiles/); None once a kernel changes.
-PROFILED_TRAFFIC = {"dst_x": 133.223424e6 + 84.495104e6, "dst_y": 133.222144e6 + 76.901120e6,
-                    "time_solve": 266.523136e6 + 89.683712e6}
+PROFILED_TRAFFIC = {"dst_x": 133.416704e6 + 84.831488e6, "dst_y": 133.236992e6 + 77.190912e6,
+                    "time_solve": 266.473728e6 + 89.289984e6}
 
 
 def _peaks():
