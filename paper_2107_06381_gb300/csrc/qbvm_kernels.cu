@@ -62,11 +62,17 @@ static cudaError_t set_smem(K kern, size_t smem) {
     return cudaSuccess;
 }
 
-// Launch with programmatic stream serialisation (see pdl_wait): the kernel's
-// CTAs may be scheduled while its predecessor in the stream finishes, which
-// hides the launch and the table loads of the ~25 dependent launches of a
-// refined solve or the 5 of a y^0-only one.  Only kernels that call pdl_wait
-// before touching a predecessor's data are launched this way.
+static int device_sms();
+
+// Launch with programmatic stream serialisation (see pdl_wait) when the grid
+// is small -- at most two CTAs per SM, as in the latency-bound chains of the
+// y^0-only solve or of small grids, where the successor's launch and table
+// loads then overlap the predecessor's tail (y^0-only on 255^2: 53 -> 42 us).
+// Larger grids launch the ordinary way: with the attribute the 3D refined
+// solve (127^3 x 128) measured 20.7 ms against 18.8 ms without.  Only kernels
+// that call pdl_wait before touching a predecessor's data come through here
+// (for the others the attribute would not be safe; for these, pdl_wait is a
+// no-op in an ordinary launch).
 template <typename... P, typename... A>
 static cudaError_t launch_pdl(void (*kern)(P...), unsigned grid, unsigned block, size_t smem, cudaStream_t s,
                               A... args) {
@@ -79,7 +85,8 @@ static cudaError_t launch_pdl(void (*kern)(P...), unsigned grid, unsigned block,
     cfg.dynamicSmemBytes = smem;
     cfg.stream = s;
     cfg.attrs = attr;
-    cfg.numAttrs = 1;
+    const int sms = device_sms();
+    cfg.numAttrs = (sms > 0 && grid <= 2u * (unsigned)sms) ? 1 : 0;
     return cudaLaunchKernelEx(&cfg, kern, args...);
 }
 
