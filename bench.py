@@ -456,6 +456,11 @@ def our_arm(args, rank, world, device):
         "y0_delta_rhs": y0m,
         **extra,
     }
+    if args.refine_only:
+        # profiling aid: the FP64 leg did not run, so it has no numbers
+        out.update({"value": None, "ms_per_step": None, "roofline": None, "kernels": {}, "e2e": None,
+                    "e2e_matches_device_path": None, "gpu_launches": refine["gpu_launches"] if refine else 0,
+                    "note": "--refine-only: only the FP32 + refinement leg ran (fp32_refine)"})
     for plan in plans:
         plan.close()
     return out
