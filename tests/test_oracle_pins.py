@@ -129,6 +129,27 @@ def test_eigenfunction_data_closed_form(grid, form):
 
 
 @pytest.mark.parametrize("grid", _tiny_grids())
+@pytest.mark.parametrize("method", ["qbvm", "mqbvm"])
+def test_original_systems_eigenfunction_closed_form(grid, method):
+    """The original systems of Section 2 on g = c sin(k.pi x/L) (an eigenvector
+    of Delta_h, eigenvalue -lam): backward Euler gives y^n = r^n y^0 with
+    r = 1/(1 + tau lam), and the first block row then fixes y^0 --
+        QBVM  (eq. 2.3):  alpha y^0 + y^N = g          ->  y^0 = c / (alpha + r^N),
+        MQBVM (eq. 2.6):  (alpha/tau)(y^0 - y^1) + y^N = g
+                                                       ->  y^0 = c / ((alpha/tau)(1 - r) + r^N)."""
+    kvec = tuple(max(1, (m - 1) // 2) for m in grid.M)
+    alpha, c = 3e-3, 0.6
+    tau, N = grid.tau, grid.nt - 1
+    lam = sum((4.0 / (grid.L / m) ** 2) * math.sin(k * math.pi / (2 * m)) ** 2 for k, m in zip(kvec, grid.M))
+    r = 1.0 / (1.0 + tau * lam)
+    den = alpha + r ** N if method == "qbvm" else (alpha / tau) * (1.0 - r) + r ** N
+    phi = bi.sine_field(grid, [kvec], [1.0])
+    want = np.stack([r ** n * c / den * phi for n in range(grid.nt)])
+    got = solve_original(grid, method, alpha, c * phi)
+    np.testing.assert_allclose(got, want, atol=1e-10 * np.abs(want).max())
+
+
+@pytest.mark.parametrize("grid", _tiny_grids())
 @pytest.mark.parametrize("form", [O.PQ, O.PM])
 def test_solvers_agree_on_general_rhs(grid, form):
     """Dense LU (brute force), sparse LU, the three-step diagonalisation and the
