@@ -373,7 +373,7 @@ k_time_solve_ct(const R* in, R* out, long long Nx, const cplx<R>* __restrict__ t
 // the single-instance width, fewer when Nx is small); LH < 0: lh is taken at
 // run time.
 template <int MAXB4, int LH>
-__global__ void __launch_bounds__(TILE_THREADS)
+__global__ void __launch_bounds__(TILE_THREADS, 3)
 k_time_solve_batched(const double* in, double* out, long long Nx, int lh, int lw, long long tiles,
                      long long in_stride, long long out_stride, const double2* __restrict__ tw,
                      const double2* __restrict__ gpow, const double2* __restrict__ gipw,
