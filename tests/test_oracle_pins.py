@@ -128,6 +128,49 @@ def test_eigenfunction_data_closed_form(grid, form):
         np.testing.assert_allclose(got, want, atol=1e-10 * scale, err_msg=solver.__name__)
 
 
+@pytest.mark.parametrize("grid", _tiny_grids()[:4])
+@pytest.mark.parametrize("form", [O.PQ, O.PM])
+def test_kronecker_factorisation_of_the_pint_matrix(grid, form):
+    """Section 3.3: A = tau^-1 C_omega (x) I - I (x) Delta_h and C_omega = V D V^-1
+    with V^-1 = F Gamma_omega, V = Gamma_omega^-1 F*, D = diag(sqrt(N_t) F Gamma_omega
+    C_omega(:, 1)) give A = (V (x) I)(tau^-1 D (x) I - I (x) Delta_h)(V^-1 (x) I).
+    Built here with dense Kronecker products (vec with the time level slowest) and
+    compared with the assembled sparse matrix: pins V, D, the root of omega and
+    the ordering the three-step oracle applies as matrix products."""
+    from oracle.qbvm_oracle import principal_root
+    nt, tau = grid.nt, grid.tau
+    alpha = 2e-2
+    om = O.omega_of(form, alpha, tau)
+    k = np.arange(nt)
+    Fm = np.exp(2j * np.pi * np.outer(k, k) / nt) / math.sqrt(nt)
+    gam = principal_root(om, nt) ** k
+    Vinv = Fm @ np.diag(gam)
+    V = np.diag(1.0 / gam) @ Fm.conj().T
+    D = np.diag(math.sqrt(nt) * (Vinv @ O.c_omega(nt, om)[:, 0]))
+    np.testing.assert_allclose(V @ D @ Vinv, O.c_omega(nt, om), atol=1e-12 * max(1.0, abs(om)))
+    Lap = O.laplacian(grid.dim, grid.M, grid.L).toarray()
+    Ix, It = np.eye(Lap.shape[0]), np.eye(nt)
+    A = np.kron(V, Ix) @ (np.kron(D / tau, Ix) - np.kron(It, Lap)) @ np.kron(Vinv, Ix)
+    want = O.assemble_pint(grid, form, alpha).toarray()
+    assert np.abs(A.imag).max() <= 1e-9 * np.abs(want).max()
+    np.testing.assert_allclose(A.real, want, atol=1e-9 * np.abs(want).max())
+
+
+@pytest.mark.parametrize("grid", _tiny_grids())
+@pytest.mark.parametrize("form", [O.PQ, O.PM])
+def test_solutions_are_linear_in_the_right_hand_side(grid, form):
+    """The solve is linear: solve(a F1 + b F2) = a solve(F1) + b solve(F2) for
+    every oracle (a cached factor, a wrong scaling of one level or a dropped
+    term on one right-hand side breaks it)."""
+    rng = np.random.default_rng(17)
+    F1, F2 = rng.standard_normal(grid.full_shape), rng.standard_normal(grid.full_shape)
+    a, b = 0.75, -2.5
+    for solver in (O.solve_sparse_lu, O.solve_pint_three_step, O.solve_spectral):
+        y = solver(grid, form, 1e-3, a * F1 + b * F2)
+        want = a * solver(grid, form, 1e-3, F1) + b * solver(grid, form, 1e-3, F2)
+        np.testing.assert_allclose(y, want, atol=1e-11 * np.abs(want).max(), err_msg=solver.__name__)
+
+
 @pytest.mark.parametrize("grid", _tiny_grids())
 @pytest.mark.parametrize("method", ["qbvm", "mqbvm"])
 def test_original_systems_eigenfunction_closed_form(grid, method):
