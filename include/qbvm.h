@@ -33,7 +33,8 @@
  *  - `stream` is a cudaStream_t (NULL = legacy default stream).  A plan may be
  *    used by one stream at a time; calls on one plan must not overlap.
  *  - The caller owns every array it passes; the plan owns its device tables
- *    and workspace and frees them in qbvm_destroy.
+ *    and workspace and frees them in qbvm_destroy.  Every *_destroy accepts
+ *    NULL (and returns QBVM_OK), as free() does.
  *  - Every entry point returns QBVM_OK (0) or a negative QBVM_ERR_* code; on an
  *    error nothing has been enqueued unless the code is QBVM_ERR_CUDA.
  */

@@ -287,7 +287,7 @@ int qbvm_batch_info(const qbvm_batch_t* bt, double* alphas, long long* unknowns_
 }
 
 int qbvm_batch_destroy(qbvm_batch_t* bt) {
-    if (!bt) return QBVM_ERR_BAD_ARG;
+    if (!bt) return QBVM_OK;                      // NULL is accepted, as by every destroy
     destroy_batch(bt);
     return QBVM_OK;
 }

@@ -129,3 +129,23 @@ def test_batch_plan_rejects_before_a_gpu(lib, case):
 def test_selftest_rejects_bad_cta_counts(lib):
     assert lib.qbvm_selftest_bounded_wait(0, None, None) == -1
     assert lib.qbvm_selftest_bounded_wait(65, None, None) == -1
+
+
+def test_abi_from_plain_c(lib):
+    """include/qbvm.h compiles as C99 and the library links into a C program;
+    the host-side checks hold there too (tests/native/abi_c_check.c)."""
+    import shutil
+    import subprocess
+    import tempfile
+    gcc = shutil.which("gcc") or shutil.which("cc")
+    if gcc is None:
+        pytest.skip("no C compiler")
+    libdir = os.path.join(ROOT, "paper_2107_06381_gb300", "_lib")
+    with tempfile.TemporaryDirectory() as d:
+        exe = os.path.join(d, "abi_c_check")
+        subprocess.run([gcc, "-std=c99", "-Wall", "-Werror", "-I", os.path.join(ROOT, "include"), "-o", exe,
+                        os.path.join(ROOT, "tests", "native", "abi_c_check.c"), "-L", libdir, "-lqbvm",
+                        "-Wl,-rpath," + libdir], check=True, capture_output=True)
+        res = subprocess.run([exe], capture_output=True, text=True, timeout=120)
+        assert res.returncode == 0, res.stdout + res.stderr
+        assert "0 failures" in res.stdout
