@@ -234,10 +234,12 @@ int qbvm_residual_noalloc(const qbvm_desc* desc, const double* y, const double* 
  * the instance's own omega tables -- so a batch costs the launches of one
  * solve, whatever `count` is.  Asynchronous on `stream`.
  * Supported: space-first order (2D/3D; 1D with m a power of two), nt a power
- * of two <= 1024, device pointers.  The batch owns its tables ([count][nt/2]
- * omega factors and [count][nt/2][Nx] Step (b) reciprocals) and a base plan.
- * Errors: BAD_ARG (count < 1, an alpha not finite and positive, host
- * pointers), UNSUPPORTED, OOM, CUDA. */
+ * of two <= 1024.  Device pointers (asynchronous), or host pointers (staged
+ * through batch-owned device copies; the call then synchronises `stream`).
+ * The batch owns its tables ([count][nt/2] omega factors and [count][nt/2][Nx]
+ * Step (b) reciprocals) and a base plan.  Errors: BAD_ARG (count < 1, an
+ * alpha not finite and positive, one host and one device pointer),
+ * UNSUPPORTED, OOM, CUDA. */
 typedef struct qbvm_batch qbvm_batch_t;
 int qbvm_batch_plan(const qbvm_desc* desc, int count, const double* alphas, qbvm_batch_t** out);
 int qbvm_solve_batched(qbvm_batch_t* batch, const double* g_or_F, double* y, int n0_only, void* stream);

@@ -66,6 +66,8 @@ struct qbvm_batch {
     double* y0fac = nullptr;      // delta right-hand side: [count][Nx]
     double* ghat = nullptr;       // delta right-hand side: the DST of every g, [count][Nx]
     double* work = nullptr;       // general right-hand side with n0_only: [count][nt][Nx]
+    double* stage_in = nullptr;   // host-pointer solves: device copies of the input and output
+    double* stage_out = nullptr;
     std::vector<void*> allocs;
 };
 
@@ -125,6 +127,8 @@ bool is_dev(const void* p) {
     }
     return a.type == cudaMemoryTypeDevice || a.type == cudaMemoryTypeManaged;
 }
+
+int solve_batched_dev(qbvm_batch_t* bt, const double* g_or_F, double* y, int n0_only, cudaStream_t s);
 
 }  // namespace
 
@@ -239,8 +243,40 @@ int qbvm_batch_plan(const qbvm_desc* desc, int count, const double* alphas, qbvm
 
 int qbvm_solve_batched(qbvm_batch_t* bt, const double* g_or_F, double* y, int n0_only, void* stream) {
     if (!bt || !g_or_F || !y) return QBVM_ERR_BAD_ARG;
-    if (!is_dev(g_or_F) || !is_dev(y)) return QBVM_ERR_BAD_ARG;
+    const bool din = is_dev(g_or_F), dout = is_dev(y);
+    if (din != dout) return QBVM_ERR_BAD_ARG;                 // both on the device or both on the host
     cudaStream_t s = static_cast<cudaStream_t>(stream);
+    if (din) return solve_batched_dev(bt, g_or_F, y, n0_only, s);
+    // host arrays: through batch-owned device copies, synchronous
+    qbvm::PlanView v;
+    qbvm::plan_view(bt->base, &v);
+    const long long B = bt->count, Nx = v.tb->Nx, nt = v.tb->nt;
+    const size_t nin = (size_t)(B * Nx * (bt->d.rhs_kind == QBVM_RHS_DELTA ? 1 : nt));
+    const size_t nout = (size_t)(B * Nx * (n0_only ? 1 : nt));
+    if (!bt->stage_in) {
+        int rc = balloc(bt, &bt->stage_in, (size_t)(B * Nx * nt));
+        if (!rc) rc = balloc(bt, &bt->stage_out, (size_t)(B * Nx * nt));
+        if (rc) return rc;
+    }
+    if (cudaMemcpyAsync(bt->stage_in, g_or_F, nin * sizeof(double), cudaMemcpyHostToDevice, s) != cudaSuccess) {
+        cudaGetLastError();
+        return QBVM_ERR_CUDA;
+    }
+    int rc = solve_batched_dev(bt, bt->stage_in, bt->stage_out, n0_only, s);
+    if (rc) return rc;
+    if (cudaMemcpyAsync(y, bt->stage_out, nout * sizeof(double), cudaMemcpyDeviceToHost, s) != cudaSuccess ||
+        cudaStreamSynchronize(s) != cudaSuccess) {
+        cudaGetLastError();
+        return QBVM_ERR_CUDA;
+    }
+    return QBVM_OK;
+}
+
+}  // extern "C"
+
+namespace {
+
+int solve_batched_dev(qbvm_batch_t* bt, const double* g_or_F, double* y, int n0_only, cudaStream_t s) {
     qbvm::PlanView v;
     qbvm::plan_view(bt->base, &v);
     const qbvm::Tables& tb = *v.tb;
@@ -275,6 +311,10 @@ int qbvm_solve_batched(qbvm_batch_t* bt, const double* g_or_F, double* y, int n0
         return QBVM_ERR_CUDA;
     return dst_levels(tb, y, y, n0_only ? B : lev, s);
 }
+
+}  // namespace
+
+extern "C" {
 
 int qbvm_batch_info(const qbvm_batch_t* bt, double* alphas, long long* unknowns_per_instance) {
     if (!bt) return QBVM_ERR_BAD_ARG;

@@ -90,11 +90,21 @@ def test_many_instances_of_the_1d_shape():
     assert np.isfinite(got).all()
 
 
-def test_host_pointers_are_refused():
+@pytest.mark.parametrize("rhs_kind", [Q.RHS_DELTA, Q.RHS_GENERAL], ids=["delta", "general"])
+def test_host_pointers_match_device_and_mixed_are_refused(rhs_kind):
     grid = GRIDS[0]
-    with Q.Batch(grid.dim, grid.M, grid.L, grid.T, grid.nt, Q.FORM_PQ, alphas=[1e-3, 1e-2]) as bt:
-        x = np.zeros(2 * grid.Nx)
-        y = np.zeros(2 * grid.unknowns)
+    alphas = [1e-3, 1e-2, 3e-4]
+    F = np.stack([bi.random_general_rhs(grid, seed=90 + b) for b in range(3)])
+    rhs = np.ascontiguousarray(F[:, 0] if rhs_kind == Q.RHS_DELTA else F).ravel()
+    dev = _batched(grid, Q.FORM_PQ, alphas, rhs, rhs_kind, False).ravel()
+    with Q.Batch(grid.dim, grid.M, grid.L, grid.T, grid.nt, Q.FORM_PQ, alphas=alphas, rhs_kind=rhs_kind) as bt:
+        y = np.full(3 * grid.unknowns, np.nan)
+        bt.solve(rhs, y)                                   # host arrays: staged, synchronous
+        np.testing.assert_array_equal(y, dev)
+        y0 = np.full(3 * grid.Nx, np.nan)
+        bt.solve(rhs, y0, n0_only=True)
+        np.testing.assert_allclose(y0.reshape(3, -1), dev.reshape(3, grid.nt, -1)[:, 0], rtol=0,
+                                   atol=1e-12 * np.abs(dev).max())
         with pytest.raises(Q.QbvmError) as ei:
-            bt.solve(x, y)
+            bt.solve(rhs, torch.zeros(3 * grid.unknowns, dtype=torch.float64, device="cuda"))
         assert ei.value.code == -1
