@@ -299,6 +299,14 @@ def our_arm(args, rank, world, device):
             ach = byts / avg_s / 1e9
             roof = {"bound": "hbm", "kernel": dname, "achieved": round(ach, 1), "peak": hbm_peak, "unit": "GB/s",
                     "frac": round(ach / hbm_peak, 4), "traffic": traffic, "peak_source": hbm_src}
+        # the other two HBM figures: DRAM bytes ncu measured for this kernel over its
+        # event-timed duration, and the whole solve's algorithmic bytes (F in + y
+        # out, or g in + y out) at the measured unknowns/s -- both over the copy peak
+        bpu = 16 if args.rhs == "general" else 8
+        roof["dram_gbs_ncu"] = round(traffic / avg_s / 1e9, 1) if traffic else None
+        roof["dram_frac_ncu"] = round(traffic / avg_s / 1e9 / hbm_peak, 4) if traffic else None
+        roof["solve_algorithmic_gbs"] = round(bpu * value / 1e9, 1)
+        roof["solve_algorithmic_frac"] = round(bpu * value / 1e9 / hbm_peak, 4)
     kernels = {k: {"launches": v[0], "avg_ms": round(v[1] / v[0], 4), "share": round(v[1] / sum(x[1] for x in kstats.values()), 4)}
                for k, v in sorted(kstats.items(), key=lambda kv: -kv[1][1])}
 
