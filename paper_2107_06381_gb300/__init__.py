@@ -358,6 +358,19 @@ class Sweep:
     def autotune(self, repeats=3, stream=None):
         return qbvm_sweep_autotune(self.handle, repeats, stream)
 
+    def autotune_cached(self, path, repeats=3, stream=None):
+        """The launch shape from the JSON cache at `path` when this kind of batch
+        (shapes, alphas, precision, GPU) was tuned before, else autotune and
+        store it (tune_cache).  Returns (modes_per_thread, ctas_per_sm, hit)."""
+        from . import tune_cache
+        try:
+            import torch
+            device = torch.cuda.get_device_name() if torch.cuda.is_available() else "unknown"
+        except Exception:
+            device = "unknown"
+        key = tune_cache.workload_key(self._keep, self.n_alpha, self.desc.precision, device)
+        return tune_cache.autotune_cached(self, key, path, repeats=repeats, device=device, stream=stream)
+
     @property
     def config(self):
         return qbvm_sweep_get_config(self.handle)
