@@ -272,7 +272,7 @@ def our_arm(args, rank, world, device):
         plan.profile(False)
     launches_per_solve = plans[0].info.kernels_per_solve
     unknowns_step = grid.unknowns * len(forms)
-    value = world * unknowns_step * args.steps / (total_ms / 1e3)
+    value = world * unknowns_step * args.steps / (total_ms / 1e3) if total_ms > 0 else 0.0
 
     # ---- roofline of the dominant kernel
     hbm_peak, hbm_src = _peaks()
