@@ -16,7 +16,8 @@ def _declared_functions():
     for h in glob.glob(os.path.join(ROOT, "include", "*.h")):
         text = open(h).read()
         text = re.sub(r"/\*.*?\*/", "", text, flags=re.S)
-        for m in re.finditer(r"^\s*(?:const\s+)?[A-Za-z_][A-Za-z0-9_]*\s*\**\s+\**\s*(qbvm_[A-Za-z0-9_]+)\s*\(",
+        # return type of one or more words ("int", "const char*", "long long"), then the name
+        for m in re.finditer(r"^\s*(?:[A-Za-z_][A-Za-z0-9_]*\s*\**\s+)+\**\s*(qbvm_[A-Za-z0-9_]+)\s*\(",
                              text, flags=re.M):
             names.add(m.group(1))
     return sorted(names)
@@ -149,3 +150,26 @@ def test_abi_from_plain_c(lib):
         res = subprocess.run([exe], capture_output=True, text=True, timeout=120)
         assert res.returncode == 0, res.stdout + res.stderr
         assert "0 failures" in res.stdout
+
+
+def test_every_exported_entry_point_is_declared(lib):
+    """No C entry point is exported without a declaration (and its documentation)
+    in include/qbvm.h: the exported qbvm_* names (nm, the library's own symbol
+    table) equal the declared ones."""
+    import shutil
+    import subprocess
+    nm = shutil.which("nm")
+    if nm is None:
+        pytest.skip("nm not available")
+    so = os.path.join(ROOT, "paper_2107_06381_gb300", "_lib", "libqbvm.so")
+    out = subprocess.run([nm, "-D", "--defined-only", so], capture_output=True, text=True, check=True).stdout
+    exported = {ln.split()[-1] for ln in out.splitlines() if ln.split() and ln.split()[-1].startswith("qbvm_")}
+    assert exported == set(_declared_functions()), (exported ^ set(_declared_functions()))
+
+
+def test_every_status_code_has_its_own_message(lib):
+    text = open(os.path.join(ROOT, "include", "qbvm.h")).read()
+    codes = {int(v) for v in re.findall(r"#define QBVM_ERR_[A-Z_]+\s+(-\d+)", text)}
+    assert codes == set(range(-7, 0))
+    msgs = [Q.qbvm_strerror(c) for c in sorted(codes)]
+    assert len(set(msgs)) == len(msgs) and "unknown status code" not in msgs
