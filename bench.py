@@ -107,6 +107,26 @@ def cpu_oracle_leg(prob, forms, steps):
     return grid.unknowns / statistics.median(times), times, sols
 
 
+def cpu_oracle_one_core(timeout_s=180):
+    """One full solve of the 2D workload by the oracle on ONE host core (for the
+    comparison with a serial code): a child process with every BLAS / OpenMP
+    thread count set to 1 before numpy loads.  Returns seconds, or None."""
+    import subprocess
+    env = dict(os.environ)
+    for v in ("OMP_NUM_THREADS", "OPENBLAS_NUM_THREADS", "MKL_NUM_THREADS", "BLIS_NUM_THREADS"):
+        env[v] = "1"
+    code = ("import time, bhcp_inputs as bi, oracle as O\n"
+            "p = bi.make_c2(); a = O.alpha_apriori(O.PQ, p.delta, p.grid.tau)\n"
+            "F = O.delta_rhs(p.grid, O.PQ, a, p.g_delta)\n"
+            "t = time.perf_counter(); O.solve_spectral(p.grid, O.PQ, a, F); print(time.perf_counter() - t)\n")
+    try:
+        r = subprocess.run([sys.executable, "-c", code], cwd=ROOT, env=env, capture_output=True, text=True,
+                           timeout=timeout_s)
+        return float(r.stdout.strip().splitlines()[-1]) if r.returncode == 0 else None
+    except Exception:
+        return None
+
+
 # ------------------------------------------------------------------ clocks
 
 class ClockSampler:
@@ -428,6 +448,10 @@ def our_arm(args, rank, world, device):
                          "FP64 sine-basis oracle (dense DST-I matrices + exact per-mode recurrence) after one "
                          "warm-up solve; median",
                "seconds": [round(t, 3) for t in cpu_times]}
+        one = cpu_oracle_one_core()
+        if one:
+            cpu["one_core"] = {"value": grid.unknowns / one, "unit": UNIT, "cores": 1, "seconds": round(one, 3),
+                               "sample": "one full solve (PinT-QBVM), BLAS / OpenMP limited to one thread"}
         def max_err(ys):
             errs = []
             for form, y in zip(forms, ys):
