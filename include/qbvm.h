@@ -29,7 +29,9 @@
  *    pinned).  Device pointers: the call only enqueues work on `stream` and
  *    returns.  Host pointers: the call stages through device buffers owned by
  *    the plan and returns after the result has been copied back (it
- *    synchronises `stream`).  Input and output may not be a mix of the two.
+ *    synchronises `stream`).  Input and output may not be a mix of the two,
+ *    and device pointers must be memory of the device the plan was made on
+ *    (or managed memory): another GPU's memory is BAD_ARG.
  *  - `stream` is a cudaStream_t (NULL = legacy default stream).  A plan may be
  *    used by one stream at a time; calls on one plan must not overlap.
  *  - The caller owns every array it passes; the plan owns its device tables
@@ -191,9 +193,28 @@ typedef struct qbvm_kernel_stat {
 int qbvm_profile_enable(qbvm_plan_t* plan, int on);
 int qbvm_profile_read(qbvm_plan_t* plan, qbvm_kernel_stat* out, int capacity, int* count);
 
+/* ------------------------------------------------------------------------
+ * qbvm_measure_peak -- the fused multiply-add throughput of the current GPU,
+ * measured: the ALU roofline against which the FP64 kernels of the solve are
+ * rated (on GB300 they are bound by the FP64 pipe, not by HBM: the time
+ * solve and the DST-I passes of Section 3.3 need tens of FP64 operations per
+ * 16 bytes moved).  The paper has no counterpart; it reports no hardware
+ * rates.
+ * kind  QBVM_PEAK_FP64_FMA (DFMA) or QBVM_PEAK_FP32_FMA (FFMA).
+ * A kernel of independent FMA chains (8 per thread, 32 warps per SM, every
+ * SM) is launched six times on `stream`; the first launch is a warm-up and
+ * the best of the other five, timed with CUDA events, is written to
+ * *fma_per_s_out in FMA instructions per second (flops = 2x).  About 25 ms of
+ * GPU time.  The call synchronises `stream`.  Allocates nothing but two
+ * events.  Errors: BAD_ARG (unknown kind, NULL output), CUDA. */
+#define QBVM_PEAK_FP64_FMA 0
+#define QBVM_PEAK_FP32_FMA 1
+int qbvm_measure_peak(int kind, double* fma_per_s_out, void* stream);
+
 /* qbvm_residual_noalloc -- the value qbvm_residual returns, ||f - A y||_2 /
  * ||f||_2 in FP64, for callers that cannot allocate device memory: no plan is
- * needed and the call makes no cudaMalloc/cudaFree or other allocating call.
+ * needed and the call makes no cudaMalloc/cudaFree or other allocating call
+ * (but see "Module loading" below for the first use of the library).
  * Such callers include code whose device memory is entirely reserved by
  * another allocator or memory pool (a framework's caching allocator holding
  * the HBM), and monitoring or real-time loops that must not change the
@@ -213,9 +234,18 @@ int qbvm_profile_read(qbvm_plan_t* plan, qbvm_kernel_stat* out, int capacity, in
  * calls on a device share the array and each call overwrites what it reads,
  * so nothing carries over between calls -- but calls that overlap on the GPU
  * (other streams, other host threads) race on it and must be serialised by
- * the caller.  The first call on each device looks up the array's device
- * address (cudaGetSymbolAddress, with that device current) and caches it;
- * make that first call before any stream capture.
+ * the caller.  Every call looks up the array's device address
+ * (cudaGetSymbolAddress, with the caller's device current); the lookup
+ * allocates nothing.  Module loading: under CUDA's default lazy loading the
+ * library's device code, this array included, is loaded into a context the
+ * first time one of its kernels or symbols is used there, and that load
+ * reserves device memory for the code and the 64 KiB array.  A caller that
+ * must not see that happen later should make the first call (on every
+ * device, before any stream capture) at set-up, or run the process with
+ * CUDA_MODULE_LOADING=EAGER so that the load happens when the context is
+ * created.
+ * y and g_or_F must be memory of the current device (or managed memory);
+ * another GPU's pointer is BAD_ARG.
  * Errors: BAD_ARG, UNSUPPORTED, NONFINITE, CUDA. */
 int qbvm_residual_noalloc(const qbvm_desc* desc, const double* y, const double* g_or_F,
                           double* rel_norm_out, void* stream);
@@ -238,7 +268,8 @@ int qbvm_residual_noalloc(const qbvm_desc* desc, const double* y, const double* 
  * through batch-owned device copies; the call then synchronises `stream`).
  * The batch owns its tables ([count][nt/2] omega factors and [count][nt/2][Nx]
  * Step (b) reciprocals) and a base plan.  Errors: BAD_ARG (count < 1, an
- * alpha not finite and positive, one host and one device pointer),
+ * alpha not finite and positive, one host and one device pointer, memory of
+ * a GPU other than the one the batch was planned on),
  * UNSUPPORTED, OOM, CUDA. */
 typedef struct qbvm_batch qbvm_batch_t;
 int qbvm_batch_plan(const qbvm_desc* desc, int count, const double* alphas, qbvm_batch_t** out);

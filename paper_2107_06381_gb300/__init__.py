@@ -16,7 +16,7 @@ from .build import LIB_PATH, build as build_library
 __all__ = [
     "QbvmDesc", "QbvmInfo", "QbvmError", "load_library",
     "qbvm_plan", "qbvm_solve", "qbvm_residual", "qbvm_plan_info", "qbvm_destroy",
-    "qbvm_profile_enable", "qbvm_profile_read", "qbvm_residual_noalloc",
+    "qbvm_profile_enable", "qbvm_profile_read", "qbvm_residual_noalloc", "qbvm_measure_peak",
     "qbvm_strerror", "qbvm_version", "Plan", "Sweep", "QbvmSweepInstance", "QbvmSweepDesc", "QbvmSweepConfig",
     "qbvm_sweep_plan", "qbvm_sweep_run", "qbvm_sweep_read", "qbvm_sweep_autotune", "qbvm_sweep_set_config",
     "qbvm_sweep_get_config", "qbvm_sweep_destroy", "MLP", "Features", "Batch", "GMRES",
@@ -169,6 +169,8 @@ def load_library(path: str | None = None) -> ctypes.CDLL:
     lib.qbvm_features_run.restype = ip
     lib.qbvm_features_destroy.argtypes = [vp]
     lib.qbvm_features_destroy.restype = ip
+    lib.qbvm_measure_peak.argtypes = [ip, ctypes.POINTER(dp), vp]
+    lib.qbvm_measure_peak.restype = ip
     lib.qbvm_version.argtypes = []
     lib.qbvm_version.restype = ip
     if path is None:
@@ -250,6 +252,16 @@ def qbvm_residual_noalloc(desc: QbvmDesc, y, g_or_F, stream=None) -> float:
     out = ctypes.c_double()
     _check(load_library().qbvm_residual_noalloc(ctypes.byref(desc), _ptr(y), _ptr(g_or_F), ctypes.byref(out),
                                                 _stream(stream, y, g_or_F)), "qbvm_residual_noalloc")
+    return out.value
+
+
+PEAK_FP64_FMA, PEAK_FP32_FMA = 0, 1
+
+
+def qbvm_measure_peak(kind: int = PEAK_FP64_FMA, stream=None) -> float:
+    """Measured FMA instructions per second of the current GPU (FP64 or FP32)."""
+    out = ctypes.c_double()
+    _check(load_library().qbvm_measure_peak(int(kind), ctypes.byref(out), _stream(stream)), "qbvm_measure_peak")
     return out.value
 
 

@@ -119,13 +119,17 @@ int dst_levels(const qbvm::Tables& tb, const double* in, double* out, long long 
     return QBVM_OK;
 }
 
-bool is_dev(const void* p) {
+// 1: memory of device `dev` (or managed), 0: host memory, -1: another GPU's
+// memory (the batch's kernels would read it as a peer: refused).
+int dev_kind(const void* p, int dev) {
     cudaPointerAttributes a;
     if (cudaPointerGetAttributes(&a, p) != cudaSuccess) {
         cudaGetLastError();
-        return false;
+        return 0;
     }
-    return a.type == cudaMemoryTypeDevice || a.type == cudaMemoryTypeManaged;
+    if (a.type == cudaMemoryTypeManaged) return 1;
+    if (a.type == cudaMemoryTypeDevice) return a.device == dev ? 1 : -1;
+    return 0;
 }
 
 int solve_batched_dev(qbvm_batch_t* bt, const double* g_or_F, double* y, int n0_only, cudaStream_t s);
@@ -243,13 +247,14 @@ int qbvm_batch_plan(const qbvm_desc* desc, int count, const double* alphas, qbvm
 
 int qbvm_solve_batched(qbvm_batch_t* bt, const double* g_or_F, double* y, int n0_only, void* stream) {
     if (!bt || !g_or_F || !y) return QBVM_ERR_BAD_ARG;
-    const bool din = is_dev(g_or_F), dout = is_dev(y);
-    if (din != dout) return QBVM_ERR_BAD_ARG;                 // both on the device or both on the host
+    qbvm::PlanView v;
+    qbvm::plan_view(bt->base, &v);
+    const int din = dev_kind(g_or_F, v.dev), dout = dev_kind(y, v.dev);
+    // both on the batch's device or both on the host
+    if (din != dout || din < 0) return QBVM_ERR_BAD_ARG;
     cudaStream_t s = static_cast<cudaStream_t>(stream);
     if (din) return solve_batched_dev(bt, g_or_F, y, n0_only, s);
     // host arrays: through batch-owned device copies, synchronous
-    qbvm::PlanView v;
-    qbvm::plan_view(bt->base, &v);
     const long long B = bt->count, Nx = v.tb->Nx, nt = v.tb->nt;
     const size_t nin = (size_t)(B * Nx * (bt->d.rhs_kind == QBVM_RHS_DELTA ? 1 : nt));
     const size_t nout = (size_t)(B * Nx * (n0_only ? 1 : nt));

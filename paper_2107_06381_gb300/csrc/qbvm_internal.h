@@ -151,6 +151,7 @@ double time_cn(const Tables& tb);
 struct PlanView {
     const Tables* tb;
     int form, precision, rhs_kind, dim;
+    int dev;                       // the device the plan was made on (its tables live there)
     double alpha, tau, h2inv[3];
 };
 int plan_view(const struct ::qbvm_plan* p, PlanView* out);

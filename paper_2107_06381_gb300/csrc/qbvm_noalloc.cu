@@ -4,10 +4,12 @@
 // Its only scratch (the residual kernel's per-block partial sums and their
 // two totals) lives in the file-scope array below, which every GPU that loads
 // this library holds until the process exits.  Host code cannot use the
-// array's name as a device address, so the address is looked up once per
-// device with cudaGetSymbolAddress (with that device current) and cached.
+// array's name as a device address, so every call looks the address up with
+// cudaGetSymbolAddress, with the call's device current.  The lookup allocates
+// nothing and is not cached: a cached address would go stale if the caller
+// reset the device (cudaDeviceReset) and the module were loaded again in a
+// new context.
 #include <cmath>
-#include <mutex>
 
 #include "qbvm.h"
 #include "qbvm_internal.h"
@@ -16,35 +18,31 @@ namespace {
 
 constexpr int NOALLOC_BLOCKS = 4096;                      // residual blocks the scratch holds
 constexpr int NOALLOC_DOUBLES = 2 * NOALLOC_BLOCKS + 2;   // (r^2, f^2) per block + the two totals
-constexpr int NOALLOC_MAX_DEVICES = 64;
 
 static __device__ __align__(256) double qbvm_noalloc_scratch[NOALLOC_DOUBLES];
 
-std::mutex g_scratch_mu;
-double* g_scratch_addr[NOALLOC_MAX_DEVICES] = {};
-
-// Device address of the scratch array on the current device `dev`.
-int scratch_address(int dev, double** out) {
-    std::lock_guard<std::mutex> lock(g_scratch_mu);
-    if (!g_scratch_addr[dev]) {
-        void* p = nullptr;
-        if (cudaGetSymbolAddress(&p, qbvm_noalloc_scratch) != cudaSuccess || !p) {
-            cudaGetLastError();
-            return QBVM_ERR_CUDA;
-        }
-        g_scratch_addr[dev] = static_cast<double*>(p);
+// Device address of the scratch array in the current device's context.
+int scratch_address(double** out) {
+    void* p = nullptr;
+    if (cudaGetSymbolAddress(&p, qbvm_noalloc_scratch) != cudaSuccess || !p) {
+        cudaGetLastError();
+        return QBVM_ERR_CUDA;
     }
-    *out = g_scratch_addr[dev];
+    *out = static_cast<double*>(p);
     return QBVM_OK;
 }
 
-bool on_device(const void* ptr) {
+// True when `ptr` is device (or managed) memory of device `dev`, the device
+// that owns the scratch and runs the kernel: memory of another GPU would be a
+// peer access, which without peer mapping is an illegal address.
+bool on_device(const void* ptr, int dev) {
     cudaPointerAttributes a;
     if (cudaPointerGetAttributes(&a, ptr) != cudaSuccess) {
         cudaGetLastError();
         return false;
     }
-    return a.type == cudaMemoryTypeDevice || a.type == cudaMemoryTypeManaged;
+    if (a.type == cudaMemoryTypeManaged) return true;
+    return a.type == cudaMemoryTypeDevice && a.device == dev;
 }
 
 }  // namespace
@@ -54,7 +52,13 @@ extern "C" int qbvm_residual_noalloc(const qbvm_desc* desc, const double* y, con
     if (!desc || !y || !g_or_F || !rel_norm_out) return QBVM_ERR_BAD_ARG;
     int rc = qbvm::validate_desc(desc);
     if (rc) return rc;
-    if (!on_device(y) || !on_device(g_or_F)) return QBVM_ERR_BAD_ARG;   // host data would need staging memory
+    int dev = 0;
+    if (cudaGetDevice(&dev) != cudaSuccess) {
+        cudaGetLastError();
+        return QBVM_ERR_CUDA;
+    }
+    // host data would need staging memory; another GPU's memory is not ours to read
+    if (!on_device(y, dev) || !on_device(g_or_F, dev)) return QBVM_ERR_BAD_ARG;
 
     // tau, alpha and omega exactly as qbvm_plan derives them (Sections 3.1/3.2, 5)
     const qbvm_desc& d = *desc;
@@ -78,14 +82,8 @@ extern "C" int qbvm_residual_noalloc(const qbvm_desc* desc, const double* y, con
 
     const int nblocks = qbvm::residual_blocks(tb);
     if (nblocks > NOALLOC_BLOCKS) return QBVM_ERR_UNSUPPORTED;       // more partial sums than the scratch holds
-    int dev = 0;
-    if (cudaGetDevice(&dev) != cudaSuccess) {
-        cudaGetLastError();
-        return QBVM_ERR_CUDA;
-    }
-    if (dev < 0 || dev >= NOALLOC_MAX_DEVICES) return QBVM_ERR_UNSUPPORTED;
     double* scratch = nullptr;
-    rc = scratch_address(dev, &scratch);
+    rc = scratch_address(&scratch);
     if (rc) return rc;
 
     // Every block writes its own partial pair and the reduction overwrites the

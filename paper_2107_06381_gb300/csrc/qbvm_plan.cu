@@ -255,14 +255,19 @@ struct Span {
     }
 };
 
-enum { KIND_DEV = 0, KIND_HOST = 1 };
-int ptr_kind(const void* ptr) {
+enum { KIND_DEV = 0, KIND_HOST = 1, KIND_FOREIGN = 2 };
+// Device memory of the plan's device `dev` (or managed memory), host memory,
+// or device memory of another GPU (KIND_FOREIGN: the plan's kernels would read
+// it as a peer, an illegal address without peer mapping; refused as BAD_ARG).
+int ptr_kind(const void* ptr, int dev) {
     cudaPointerAttributes a;
     if (cudaPointerGetAttributes(&a, ptr) != cudaSuccess) {
         cudaGetLastError();
         return KIND_HOST;
     }
-    return (a.type == cudaMemoryTypeDevice || a.type == cudaMemoryTypeManaged) ? KIND_DEV : KIND_HOST;
+    if (a.type == cudaMemoryTypeManaged) return KIND_DEV;
+    if (a.type == cudaMemoryTypeDevice) return a.device == dev ? KIND_DEV : KIND_FOREIGN;
+    return KIND_HOST;
 }
 
 #define CK(...)                                     \
@@ -513,6 +518,7 @@ int qbvm::plan_view(const struct ::qbvm_plan* p, PlanView* out) {
     out->precision = p->d.precision;
     out->rhs_kind = p->d.rhs_kind;
     out->dim = p->d.dim;
+    out->dev = p->dev;
     out->alpha = p->alpha;
     out->tau = p->tau;
     for (int i = 0; i < 3; ++i) out->h2inv[i] = p->h2inv[i];
@@ -899,8 +905,8 @@ int qbvm_solve(qbvm_plan_t* p, const double* g_or_F, double* y, int n0_only, voi
     } range_;
     if (!p || !g_or_F || !y) return QBVM_ERR_BAD_ARG;
     cudaStream_t s = static_cast<cudaStream_t>(stream);
-    const int kin = ptr_kind(g_or_F), kout = ptr_kind(y);
-    if (kin != kout) return QBVM_ERR_BAD_ARG;
+    const int kin = ptr_kind(g_or_F, p->dev), kout = ptr_kind(y, p->dev);
+    if (kin != kout || kin == KIND_FOREIGN) return QBVM_ERR_BAD_ARG;
     if (kin == KIND_DEV) return solve_dev(p, g_or_F, y, n0_only, s);
     // host pointers: stage through plan buffers
     int rc = ensure_stage(p);
@@ -923,8 +929,8 @@ int qbvm_solve(qbvm_plan_t* p, const double* g_or_F, double* y, int n0_only, voi
 int qbvm_residual(qbvm_plan_t* p, const double* y, const double* g_or_F, double* rel_norm_out, void* stream) {
     if (!p || !y || !g_or_F || !rel_norm_out) return QBVM_ERR_BAD_ARG;
     cudaStream_t s = static_cast<cudaStream_t>(stream);
-    const int ky = ptr_kind(y), kf = ptr_kind(g_or_F);
-    if (ky != kf) return QBVM_ERR_BAD_ARG;
+    const int ky = ptr_kind(y, p->dev), kf = ptr_kind(g_or_F, p->dev);
+    if (ky != kf || ky == KIND_FOREIGN) return QBVM_ERR_BAD_ARG;
     const int delta = p->d.rhs_kind == QBVM_RHS_DELTA;
     const double* dy = y;
     const double* df = g_or_F;

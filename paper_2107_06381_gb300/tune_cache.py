@@ -2,8 +2,9 @@
 
 qbvm_sweep_autotune times every candidate launch shape (modes per thread in
 the alpha scan x CTAs per SM) on the actual batch.  The best shape depends on
-the batch's sizes, the number of alphas, the precision and the GPU, not on the
-data, so it is kept in a JSON file keyed by those and set directly
+the batch's sizes, the number of alphas, the precision, the GPU and the build
+of the kernel, not on the data, so it is kept in a JSON file keyed by those
+and set directly
 (qbvm_sweep_set_config) the next time the same kind of batch is planned.
 The file holds {key: {"modes_per_thread", "ctas_per_sm", "ms", "device"}};
 writes go to a temporary file that replaces the old one, so a reader never
@@ -17,12 +18,32 @@ import os
 import tempfile
 
 
-def workload_key(instances, n_alpha: int, precision: int, device: str) -> str:
+_SWEEP_SOURCES = ("qbvm_sweep.cu", "qbvm_dst.cuh", "qbvm_fft.cuh", "qbvm_internal.h")
+
+
+def build_id() -> str:
+    """Hash of the sources the sweep kernel is compiled from: a launch shape
+    tuned for one build of the kernel (its launch bounds, shared-memory use,
+    stage code) is not reused after any of them changes."""
+    h = hashlib.sha1()
+    csrc = os.path.join(os.path.dirname(os.path.abspath(__file__)), "csrc")
+    for name in _SWEEP_SOURCES:
+        try:
+            with open(os.path.join(csrc, name), "rb") as f:
+                h.update(name.encode() + b"\0" + f.read())
+        except OSError:
+            h.update(name.encode() + b"\0missing")
+    return h.hexdigest()[:16]
+
+
+def workload_key(instances, n_alpha: int, precision: int, device: str, build: str | None = None) -> str:
     """Stable key of a sweep: the shapes of its instances (dim, m, nt, form,
-    in order), the number of alphas, the precision and the device name."""
+    in order), the number of alphas, the precision, the device name and the
+    kernel build (`build_id()` unless given)."""
     shapes = [[int(d["dim"]), [int(x) for x in d["m"]], int(d["nt"]), int(d.get("form", 0))] for d in instances]
     blob = json.dumps({"shapes": shapes, "n_alpha": int(n_alpha), "precision": int(precision),
-                       "device": str(device)}, sort_keys=True, separators=(",", ":"))
+                       "device": str(device), "build": build if build is not None else build_id()},
+                      sort_keys=True, separators=(",", ":"))
     return hashlib.sha1(blob.encode()).hexdigest()
 
 

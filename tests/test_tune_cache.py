@@ -32,6 +32,14 @@ def test_key_depends_on_shapes_alphas_precision_device_not_data():
     assert k != T.workload_key([dict(INST[0], nt=64), INST[1]], 16, 1, "GB300")
 
 
+def test_key_depends_on_the_kernel_build():
+    """A shape tuned for one build of the sweep kernel is not reused by another."""
+    k = T.workload_key(INST, 16, 1, "GB300")
+    assert k == T.workload_key(INST, 16, 1, "GB300", build=T.build_id())
+    assert k != T.workload_key(INST, 16, 1, "GB300", build="0" * 16)
+    assert len(T.build_id()) == 16 and T.build_id() == T.build_id()
+
+
 def test_miss_tunes_and_stores_then_hit_sets_without_tuning(tmp_path):
     path = str(tmp_path / "sub" / "tune.json")
     key = T.workload_key(INST, 16, 1, "GB300")
