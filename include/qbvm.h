@@ -74,9 +74,12 @@ extern "C" {
 /* ------------------------------------------------------------ descriptor
  * dim     space dimension d = 1, 2 or 3.
  * m[3]    intervals per axis (x, y, z); m[d] >= 2; entries beyond dim ignored.
- *         Supported: m a power of two in [4, 1024] on every axis (the DST-I
- *         length m-1 is then 2^k - 1); in 1D with the time-first order any m
- *         with m-1 <= 2^20.
+ *         Supported: any m in [2, 2048] on every axis (space-first order:
+ *         the DST-I of length m-1 runs as a radix-4/2 FFT of length m when m
+ *         is a power of two in [4, 1024], else as a mixed-radix FFT -- radix
+ *         4, 2, 3, 5 passes and a direct DFT for any other prime factor, so
+ *         its cost per element grows with m's largest prime factor); in 1D
+ *         with the time-first order any m with m-1 <= 2^20.
  * L       side length of the domain (0, L)^d; h = L/m[d].
  * T       final time, > 0.
  * nt      time levels N_t: a power of two in [2, 1024] (half-length time
@@ -263,7 +266,7 @@ int qbvm_residual_noalloc(const qbvm_desc* desc, const double* y, const double* 
  * over count*nt levels, the time solve over every (instance, mode tile) with
  * the instance's own omega tables -- so a batch costs the launches of one
  * solve, whatever `count` is.  Asynchronous on `stream`.
- * Supported: space-first order (2D/3D; 1D with m a power of two), nt a power
+ * Supported: space-first order (2D/3D; 1D with m <= 2048), nt a power
  * of two <= 1024.  Device pointers (asynchronous), or host pointers (staged
  * through batch-owned device copies; the call then synchronises `stream`).
  * The batch owns its tables ([count][nt/2] omega factors and [count][nt/2][Nx]

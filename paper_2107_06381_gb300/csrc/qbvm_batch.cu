@@ -148,11 +148,10 @@ int qbvm_batch_plan(const qbvm_desc* desc, int count, const double* alphas, qbvm
     if (rc) return rc;
     if (desc->precision != QBVM_FP64) return QBVM_ERR_UNSUPPORTED;
     if ((desc->nt & (desc->nt - 1)) != 0) return QBVM_ERR_UNSUPPORTED;       // half-length time transforms only
-    if (desc->dim == 1 && desc->order != QBVM_ORDER_SPACE_FIRST) {
-        const int m = desc->m[0];                 // AUTO is space-first only when m allows the DST
-        if (desc->order == QBVM_ORDER_TIME_FIRST || m < 4 || m > 1024 || (m & (m - 1)) != 0)
-            return QBVM_ERR_UNSUPPORTED;
-    }
+    // the batch runs space-first; AUTO is space-first whenever m allows the DST
+    // (m <= 2048), which the descriptor check already required of every m when
+    // the order is space-first
+    if (desc->dim == 1 && (desc->order == QBVM_ORDER_TIME_FIRST || desc->m[0] > 2048)) return QBVM_ERR_UNSUPPORTED;
     const double tau = desc->T / (desc->nt - 1);
     std::vector<double> al((size_t)count);
     for (int b = 0; b < count; ++b) {
@@ -175,7 +174,7 @@ int qbvm_batch_plan(const qbvm_desc* desc, int count, const double* alphas, qbvm
     qbvm::PlanView v;
     qbvm::plan_view(bt->base, &v);
     const qbvm::Tables& tb = *v.tb;
-    if (!tb.sf || tb.gen) {                       // 1D with m not a power of two: time-first only
+    if (!tb.sf || tb.gen) {                       // time-first 1D (m beyond the DST lengths) or Bluestein nt
         destroy_batch(bt);
         return QBVM_ERR_UNSUPPORTED;
     }

@@ -14,6 +14,7 @@
 // workspace, one complex tridiagonal (Thomas) solve per frequency, inverse
 // FFT + unscaling.
 #include "qbvm_dst.cuh"
+#include "qbvm_dstgen.cuh"
 #include "qbvm_fft.cuh"
 #include "qbvm_regdst.cuh"
 #include "qbvm_internal.h"
@@ -187,6 +188,38 @@ static cudaError_t launch_dst_reg_any(const TIN* in, void* out, int lm, long lon
     }
 }
 
+// DST-I of any length n = M - 1 (mixed-radix transform, qbvm_dstgen.cuh).
+template <typename R, typename TIN, int OMODE, bool X4>
+__global__ void __launch_bounds__(TILE_THREADS)
+k_dst_gen(const TIN* in, void* out, int M, int lw, long long outer, long long inner,
+          const cplx<R>* __restrict__ tw, const R* __restrict__ sn, FftGenPlan fp) {
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    dstgen_tile<R, TIN, OMODE, X4>(in, out, M, lw, outer, inner, (long long)blockIdx.x, tw, sn, fp, smem_raw);
+}
+
+template <typename R, typename TIN, int OMODE, bool X4>
+static cudaError_t launch_dst_gen(const TIN* in, void* out, int M, long long outer, long long inner,
+                                  const void* tw, const void* sn, cudaStream_t s) {
+    FftGenPlan fp;
+    if (M < 2 || !fftgen_factor(M, &fp)) return cudaErrorInvalidValue;
+    int lw = dstgen_lw(M);
+    auto nblocks = [&](int l) {
+        const long long W2 = 2LL << l;
+        return inner == 1 ? (outer + W2 - 1) / W2 : outer * ((inner + W2 - 1) / W2);
+    };
+    // as for the power-of-two tiles: few tiles spread over at least two per SM
+    const int sms = device_sms();
+    while (sms > 0 && lw > 0 && nblocks(lw) < 2LL * sms) --lw;
+    const size_t smem = dstgen_smem<R>(M, lw);
+    auto kern = k_dst_gen<R, TIN, OMODE, X4>;
+    cudaError_t e = set_smem(kern, smem);
+    if (e != cudaSuccess) return e;
+    QBVM_PDL(kern, (unsigned)nblocks(lw), TILE_THREADS, smem, s, in, out, M, lw, outer, inner,
+                                                   reinterpret_cast<const cplx<R>*>(tw),
+                                                   reinterpret_cast<const R*>(sn), fp);
+    return cudaGetLastError();
+}
+
 template <typename R>
 size_t dst_smem_bytes(int lm) { return dst_smem<R>(lm); }
 template size_t dst_smem_bytes<double>(int);
@@ -196,6 +229,8 @@ int dst_tile_lw(int lm) { return dst_lw(lm); }
 template <typename R, typename TIN, int OMODE, bool X4>
 cudaError_t launch_dst(const TIN* in, void* out, int n, int lm, long long outer, long long inner,
                        const void* tw, const void* sn, cudaStream_t s) {
+    // lengths the power-of-two tiles do not take: the mixed-radix tile
+    if (n + 1 != (1 << lm) || lm < 2 || lm > 10) return launch_dst_gen<R, TIN, OMODE, X4>(in, out, n + 1, outer, inner, tw, sn, s);
     const int lw0 = dst_lw(lm);
     auto nblocks = [&](int l) {
         const long long W2 = 2LL << l;               // real columns per tile

@@ -63,7 +63,9 @@ namespace {
 bool is_pow2(long long v) { return v > 0 && (v & (v - 1)) == 0; }
 int ilog2(long long v) { int l = 0; while ((1LL << l) < v) ++l; return l; }
 
-bool dst_length_ok(int m) { return is_pow2(m) && m >= 4 && m <= 1024; }
+// DST-I lengths n = m - 1 the kernels take: m a power of two in [4, 1024] by
+// the radix-4/2 tiles, any other m in [2, 2048] by the mixed-radix tile.
+bool dst_length_ok(int m) { return m >= 2 && m <= 2048; }
 // Space-first always in 2D/3D; in 1D on request, or by default when m allows the DST.
 bool space_first(const qbvm_desc* d) {
     if (d->dim > 1) return true;

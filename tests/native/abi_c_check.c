@@ -62,8 +62,8 @@ int main(void) {
     d.nt = 2048;
     expect(qbvm_plan(&d, &plan) == QBVM_ERR_UNSUPPORTED, "nt 2048");
     d = good_desc();
-    d.m[0] = 24;
-    expect(qbvm_plan(&d, &plan) == QBVM_ERR_UNSUPPORTED, "m 24 in 2D");
+    d.m[0] = 2049;
+    expect(qbvm_plan(&d, &plan) == QBVM_ERR_UNSUPPORTED, "m 2049 in 2D");
     /* NULL arguments */
     expect(qbvm_plan(NULL, &plan) == QBVM_ERR_BAD_ARG, "plan(NULL)");
     expect(qbvm_solve(NULL, &x, &x, 0, NULL) == QBVM_ERR_BAD_ARG, "solve(NULL)");

@@ -67,12 +67,12 @@ def test_bad_descriptors_are_rejected_without_a_gpu(lib, change):
     assert ei.value.code == -1
 
 
-@pytest.mark.parametrize("change", [dict(nt=24, precision=1), dict(nt=2048), dict(nt=2049), dict(m=(24, 16, 1)),
-                                    dict(m=(2048, 16, 1))],
-                         ids=["nt24-fp32", "nt2048", "nt2049", "m24", "m2048"])
+@pytest.mark.parametrize("change", [dict(nt=24, precision=1), dict(nt=2048), dict(nt=2049), dict(m=(2049, 16, 1)),
+                                    dict(m=(16, 4096, 1))],
+                         ids=["nt24-fp32", "nt2048", "nt2049", "m2049", "m4096"])
 def test_unsupported_sizes(lib, change):
     """Power-of-two nt up to 1024; other nt (Bluestein time DFTs) up to 2048 and
-    FP64 only; DST lengths M = 2^k."""
+    FP64 only; DST lengths M - 1 with M up to 2048 (any M)."""
     args = dict(dim=2, m=(16, 16, 1), nt=16, precision=0)
     args.update(change)
     desc = Q.make_desc(2, args["m"], 1.0, 0.1, args["nt"], 0, 1e-3, 0.0, args["precision"])
@@ -82,7 +82,7 @@ def test_unsupported_sizes(lib, change):
 
 
 def test_fp32_refinement_needs_the_space_first_order(lib):
-    for m, order in (((100,), Q.ORDER_AUTO), ((64,), Q.ORDER_TIME_FIRST)):
+    for m, order in (((4000,), Q.ORDER_AUTO), ((64,), Q.ORDER_TIME_FIRST)):
         desc = Q.make_desc(1, m, 1.0, 0.1, 16, 0, 1e-3, 0.0, Q.FP32_REFINE, order=order)
         with pytest.raises(Q.QbvmError) as ei:
             Q.qbvm_plan(desc)
@@ -90,7 +90,7 @@ def test_fp32_refinement_needs_the_space_first_order(lib):
 
 
 def test_space_first_needs_a_dst_length(lib):
-    desc = Q.make_desc(1, (100,), 1.0, 0.1, 16, 0, 1e-3, order=Q.ORDER_SPACE_FIRST)
+    desc = Q.make_desc(1, (4000,), 1.0, 0.1, 16, 0, 1e-3, order=Q.ORDER_SPACE_FIRST)
     with pytest.raises(Q.QbvmError) as ei:
         Q.qbvm_plan(desc)
     assert ei.value.code == -7
@@ -107,9 +107,9 @@ def test_null_arguments(lib):
 
 @pytest.mark.parametrize("case", [
     dict(count=0, code=-1), dict(alphas=[1e-3, -1.0], code=-1), dict(alphas=[float("nan")], code=-1),
-    dict(precision=1, code=-7), dict(nt=24, code=-7), dict(dim=1, m=(24, 1, 1), code=-7),
+    dict(precision=1, code=-7), dict(nt=24, code=-7), dict(dim=1, m=(4000, 1, 1), code=-7),
     dict(dim=1, m=(64, 1, 1), order=1, code=-7), dict(dim=0, code=-1)],
-    ids=["count0", "alpha-neg", "alpha-nan", "fp32", "nt24", "1d-m24", "1d-time-first", "dim0"])
+    ids=["count0", "alpha-neg", "alpha-nan", "fp32", "nt24", "1d-m4000", "1d-time-first", "dim0"])
 def test_batch_plan_rejects_before_a_gpu(lib, case):
     """qbvm_batch_plan: same-shape FP64 space-first batches with power-of-two nt;
     everything else is refused on the host."""
