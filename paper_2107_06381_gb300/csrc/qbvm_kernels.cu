@@ -1260,15 +1260,60 @@ struct ScaledSsq {
     }
 };
 
+// FP64 -> double-float by truncation on the integer pipes: hi keeps the top 24
+// significand bits of x, lo the next 23 (as 2^K(1 + m) - 2^K, one exact FP32
+// subtraction).  |x - (hi + lo)| < 2^-46 |x|: the size of the double-float
+// iterate's own representation error, which is all the residual needs (the
+// round-to-nearest split, qbvm_split_d, costs about three times as many
+// instructions).  Values whose hi or lo would leave the normal FP32 range take
+// qbvm_split_d.
+__device__ __forceinline__ dfloat df_from_double_trunc(double x) {
+    const unsigned int H = (unsigned int)__double2hiint(x), L = (unsigned int)__double2loint(x);
+    const int fe = (int)((H >> 20) & 0x7FFu) - 1023 + 127;
+    if (fe < 30 || fe > 253) return df_from_double(x);
+    const unsigned int sg = H & 0x80000000u;
+    const float hi = __uint_as_float(sg | ((unsigned int)fe << 23) | ((H & 0xFFFFFu) << 3) | (L >> 29));
+    const unsigned int kb = sg | ((unsigned int)(fe - 23) << 23);
+    const float lo = __uint_as_float(kb | ((L & 0x1FFFFFFFu) >> 6)) - __uint_as_float(kb);
+    return {hi, lo};
+}
+
+// (a.hi + a.lo) * (c.hi + c.lo) as an unnormalised pair (the c.lo * a.lo term,
+// 2^-48 relative, dropped): 4 operations.
+__device__ __forceinline__ dfloat df_mul_un(dfloat c, dfloat a) {
+    const float p = c.hi * a.hi;
+    float e = fmaf(c.hi, a.hi, -p);
+    e = fmaf(c.hi, a.lo, e);
+    e = fmaf(c.lo, a.hi, e);
+    return {p, e};
+}
+// a - b as an unnormalised pair: exact two-sum of the high parts, low parts
+// and the rounding error summed in FP32 (error O(u^2 (|a| + |b|))).
+__device__ __forceinline__ dfloat df_sub_un(dfloat a, dfloat b) {
+    const dfloat s = df_two_sum(a.hi, -b.hi);
+    return {s.hi, s.lo + (a.lo - b.lo)};
+}
+__device__ __forceinline__ dfloat df_add_un(dfloat a, dfloat b) {
+    const dfloat s = df_two_sum(a.hi, b.hi);
+    return {s.hi, s.lo + (a.lo + b.lo)};
+}
+
 // The same residual, four consecutive unknowns of the flattened [nt][nz][ny][nx]
 // array per thread: the iterate, f and r move as 16-byte vectors, the x
 // neighbours across a group boundary come from the adjacent lanes, and the
 // (t, z, y, x) position is advanced incrementally (no divisions in the loop).
 // Requires 16-byte aligned y, f and r_out.
+// Intermediate pairs are left unnormalised (the high parts combined by exact
+// two-sums, the low parts and rounding errors summed in FP32: error O(u^2)
+// times the terms' magnitudes, the size the double-float inputs carry), f is
+// split by truncation (df_from_double_trunc), 6 y is an exact product pair,
+// and ||f||^2 is summed only when `fnorm` is set (the first residual of a
+// solve).  Bounded to 64 registers (4 CTAs per SM): the 3D stencil took 97
+// and ran at a quarter of the warp slots.
 template <bool EQ, int DIMS>
-__global__ void __launch_bounds__(RES_THREADS)
+__global__ void __launch_bounds__(RES_THREADS, 4)
 k_residual_df4(const float2* __restrict__ y, const double* __restrict__ f, int delta_rhs, int nt, int nx, int ny,
-               int nz, DfCoef k, double f0_scale, float* __restrict__ r_out, double* partials) {
+               int nz, DfCoef k, double f0_scale, int fnorm, float* __restrict__ r_out, double* partials) {
     pdl_trigger();
     pdl_wait();
     __shared__ double sh[32];
@@ -1343,44 +1388,46 @@ k_residual_df4(const float2* __restrict__ y, const double* __restrict__ f, int d
             rv[e] = 0.f;
             if (!(act && idx < N)) continue;
             const dfloat yc = yv[e];
-            const dfloat pv = et > 0 ? ld(idx - Nx) : df_mul(k.omega, ld(idx + (long long)(nt - 1) * Nx));
-            dfloat Ay = df_mul(k.ct, df_add_sloppy(yc, df_neg(pv)));
+            dfloat pv = et > 0 ? ld(idx - Nx) : ld(idx + (long long)(nt - 1) * Nx);
+            if (et == 0) pv = df_mul_un(k.omega, pv);
+            dfloat Ay = df_mul_un(k.ct, df_sub_un(yc, pv));
             const dfloat L = e > 0 ? yv[e - 1] : xl, R = e < 3 ? yv[e + 1] : xr;
-            dfloat sx = ex > 0 ? L : dfloat{0.f, 0.f};
-            if (ex < nx - 1) sx = df_add_sloppy(sx, R);
-            dfloat sy = {0.f, 0.f}, sz = {0.f, 0.f};
+            const dfloat zero = {0.f, 0.f};
+            const dfloat sxl = ex > 0 ? L : zero, sxr = ex < nx - 1 ? R : zero;
+            dfloat ys = zero, yn = zero, zd = zero, zu = zero;
             if (DIMS >= 2) {
-                if (ey > 0) sy = ld(idx - nx);
-                if (ey < ny - 1) sy = df_add_sloppy(sy, ld(idx + nx));
+                if (ey > 0) ys = ld(idx - nx);
+                if (ey < ny - 1) yn = ld(idx + nx);
             }
             if (DIMS >= 3) {
-                if (ez > 0) sz = ld(idx - pl);
-                if (ez < nz - 1) sz = df_add_sloppy(sz, ld(idx + pl));
+                if (ez > 0) zd = ld(idx - pl);
+                if (ez < nz - 1) zu = ld(idx + pl);
             }
             if (EQ) {
-                dfloat S = sx;
-                if (DIMS >= 2) S = df_add_sloppy(S, sy);
-                if (DIMS >= 3) S = df_add_sloppy(S, sz);
-                // 2 d y: scalings by 2 and 4 are exact; 6 y = 4 y + 2 y in double-float
-                const dfloat my = DIMS == 3 ? df_add_sloppy(dfloat{4.f * yc.hi, 4.f * yc.lo}, dfloat{2.f * yc.hi, 2.f * yc.lo})
-                                            : dfloat{2.f * DIMS * yc.hi, 2.f * DIMS * yc.lo};
-                Ay = df_add_sloppy(Ay, df_mul(k.cx, df_add_sloppy(my, df_neg(S))));
+                dfloat S = df_add_un(sxl, sxr);
+                if (DIMS >= 2) S = df_add_un(S, df_add_un(ys, yn));
+                if (DIMS >= 3) S = df_add_un(S, df_add_un(zd, zu));
+                const float c2d = 2.f * DIMS;
+                dfloat my = {c2d * yc.hi, c2d * yc.lo};
+                if (DIMS == 3) my.lo = fmaf(c2d, yc.hi, -my.hi) + my.lo;       // 6 y exactly
+                Ay = df_add_un(Ay, df_mul_un(k.cx, df_sub_un(my, S)));
             } else {
                 const dfloat y2 = {2.f * yc.hi, 2.f * yc.lo};
-                Ay = df_add_sloppy(Ay, df_mul(k.cx, df_add_sloppy(y2, df_neg(sx))));
-                if (DIMS >= 2) Ay = df_add_sloppy(Ay, df_mul(k.cy, df_add_sloppy(y2, df_neg(sy))));
-                if (DIMS >= 3) Ay = df_add_sloppy(Ay, df_mul(k.cz, df_add_sloppy(y2, df_neg(sz))));
+                Ay = df_add_un(Ay, df_mul_un(k.cx, df_sub_un(y2, df_add_un(sxl, sxr))));
+                if (DIMS >= 2) Ay = df_add_un(Ay, df_mul_un(k.cy, df_sub_un(y2, df_add_un(ys, yn))));
+                if (DIMS >= 3) Ay = df_add_un(Ay, df_mul_un(k.cz, df_sub_un(y2, df_add_un(zd, zu))));
             }
-            dfloat fv = {0.f, 0.f};
+            dfloat fv = zero;
             if (delta_rhs) {
-                if (et == 0) fv = df_from_double(f0_scale * f[((long long)ez * ny + ey) * nx + ex]);
+                if (et == 0) fv = df_from_double_trunc(f0_scale * f[((long long)ez * ny + ey) * nx + ex]);
             } else {
-                fv = df_from_double(fd[e]);
+                fv = df_from_double_trunc(fd[e]);
             }
-            const dfloat r = df_add_sloppy(fv, df_neg(Ay));
-            rv[e] = r.hi;
-            nr.add(r.hi);
-            nf.add(fv.hi);
+            const dfloat r = df_sub_un(fv, Ay);
+            const float rh = r.hi + r.lo;
+            rv[e] = rh;
+            nr.add(rh);
+            if (fnorm) nf.add(fv.hi);
         }
         if (full) {
             reinterpret_cast<float4*>(r_out)[g] = make_float4(rv[0], rv[1], rv[2], rv[3]);
@@ -1455,7 +1502,7 @@ static dfloat df_const(double c) {
 
 cudaError_t launch_residual_df(const void* y_df, const double* f, int delta_rhs, const Tables& tb,
                                const double h2inv[3], float* r_out, double* partials, int nblocks, double* sums,
-                               cudaStream_t s) {
+                               int fnorm, cudaStream_t s) {
     DfCoef k;
     const double it = 1.0 / tb.tau;
     k.ct = df_const(it);
@@ -1474,13 +1521,13 @@ cudaError_t launch_residual_df(const void* y_df, const double* f, int delta_rhs,
         const double fs = -tb.omega * it;
         const int nx = tb.n[0], ny = tb.n[1], nz = tb.n[2];
         if (tb.dim == 1) {
-            QBVM_PDL(k_residual_df4<true, 1>, (unsigned)nb, RES_THREADS, 0, s, yy, f, delta_rhs, tb.nt, nx, ny, nz, k, fs, r_out, partials);
+            QBVM_PDL(k_residual_df4<true, 1>, (unsigned)nb, RES_THREADS, 0, s, yy, f, delta_rhs, tb.nt, nx, ny, nz, k, fs, fnorm, r_out, partials);
         } else if (tb.dim == 2) {
-            if (eq) QBVM_PDL(k_residual_df4<true, 2>, (unsigned)nb, RES_THREADS, 0, s, yy, f, delta_rhs, tb.nt, nx, ny, nz, k, fs, r_out, partials);
-            else QBVM_PDL(k_residual_df4<false, 2>, (unsigned)nb, RES_THREADS, 0, s, yy, f, delta_rhs, tb.nt, nx, ny, nz, k, fs, r_out, partials);
+            if (eq) QBVM_PDL(k_residual_df4<true, 2>, (unsigned)nb, RES_THREADS, 0, s, yy, f, delta_rhs, tb.nt, nx, ny, nz, k, fs, fnorm, r_out, partials);
+            else QBVM_PDL(k_residual_df4<false, 2>, (unsigned)nb, RES_THREADS, 0, s, yy, f, delta_rhs, tb.nt, nx, ny, nz, k, fs, fnorm, r_out, partials);
         } else {
-            if (eq) QBVM_PDL(k_residual_df4<true, 3>, (unsigned)nb, RES_THREADS, 0, s, yy, f, delta_rhs, tb.nt, nx, ny, nz, k, fs, r_out, partials);
-            else QBVM_PDL(k_residual_df4<false, 3>, (unsigned)nb, RES_THREADS, 0, s, yy, f, delta_rhs, tb.nt, nx, ny, nz, k, fs, r_out, partials);
+            if (eq) QBVM_PDL(k_residual_df4<true, 3>, (unsigned)nb, RES_THREADS, 0, s, yy, f, delta_rhs, tb.nt, nx, ny, nz, k, fs, fnorm, r_out, partials);
+            else QBVM_PDL(k_residual_df4<false, 3>, (unsigned)nb, RES_THREADS, 0, s, yy, f, delta_rhs, tb.nt, nx, ny, nz, k, fs, fnorm, r_out, partials);
         }
         cudaError_t e = cudaGetLastError();
         if (e != cudaSuccess) return e;

@@ -410,15 +410,20 @@ int fp32_solve(qbvm_plan_t* p, const void* rhs, int rhs_fp64, int delta, void* y
     return QBVM_OK;
 }
 
+// ||f - A y|| / ||f|| with r.hi written to p->f32.  *fnorm2 < 0 on entry: sum
+// ||f||^2 too and return it there (the first residual of a solve); otherwise
+// it holds ||f||^2 from that first call.
 int residual_norm_df(qbvm_plan_t* p, const void* ydf, const double* in, int delta, double* rel, double* fnorm2,
                      cudaStream_t s) {
-    { Span sp_(p, "residual_df", s); CK(qbvm::launch_residual_df(ydf, in, delta, p->tb, p->h2inv, p->f32, p->partials, p->nres, p->sums, s)); }
+    const int want_f = *fnorm2 < 0;
+    { Span sp_(p, "residual_df", s); CK(qbvm::launch_residual_df(ydf, in, delta, p->tb, p->h2inv, p->f32, p->partials, p->nres, p->sums, want_f, s)); }
     double h[2] = {0, 0};
     CK(cudaMemcpyAsync(h, p->sums, sizeof(h), cudaMemcpyDeviceToHost, s));
     CK(cudaStreamSynchronize(s));
+    if (want_f) *fnorm2 = h[1];
+    else h[1] = *fnorm2;
     if (!std::isfinite(h[0]) || !std::isfinite(h[1])) return QBVM_ERR_NONFINITE;
     *rel = h[1] > 0 ? std::sqrt(h[0] / h[1]) : std::sqrt(h[0]);
-    *fnorm2 = h[1];
     return QBVM_OK;
 }
 
@@ -441,8 +446,8 @@ int solve_fp32r_dev(qbvm_plan_t* p, const double* in, double* y, int n0_only, cu
     int it = 0;
     int status = QBVM_OK;
     bool first = true;
+    double fn2 = -1.0;                               // ||f||^2, summed by the first residual
     for (;;) {
-        double fn2 = 0.0;
         rc = residual_norm_df(p, yfull, in, delta, &rel, &fn2, s);     // r.hi lands in p->f32
         launches += 2;
         if (rc && !(first && rc == QBVM_ERR_NONFINITE)) return rc;
