@@ -547,7 +547,10 @@ def our_arm(args, rank, world, device):
     if not args.no_extra and not args.refine_only:
         extra["c3_3d"] = c3_leg(args, device, stream, flush, rank == 0 and world == 1 and not args.no_cpu_baseline)
         extra["c4_sweep"] = c4_leg(args, device, stream)
-        extra["c1_batched"] = c1_batched_leg(args, device, stream, flush)
+        extra["c1_batched"] = c1_batched_leg(args, device, stream, flush,
+                                             with_oracle=rank == 0 and world == 1 and not args.no_cpu_baseline)
+        extra["batched_2d"] = batched_2d_leg(args, device, stream, flush,
+                                             with_oracle=rank == 0 and world == 1 and not args.no_cpu_baseline)
         extra["learned_alpha"] = learned_alpha_leg(with_oracle=rank == 0 and world == 1 and not args.no_cpu_baseline)
 
     out = {
@@ -681,12 +684,15 @@ def c4_leg(args, device, stream):
     return out
 
 
-def c1_batched_leg(args, device, stream, flush, count=10_000):
+def c1_batched_leg(args, device, stream, flush, count=10_000, with_oracle=True):
     """The 1D problem (63 interior points x 64 levels, T = 0.1, z0 = sin(pi x) +
     0.5 sin(3 pi x), multiplicative uniform noise eps = 1e-3) as a batch of
     `count` instances with their own noise draw and alpha = their own delta
-    (PinT-QBVM, Section 5), full y of every instance: one qbvm_solve_batched
-    call = 3 kernel launches for the whole batch."""
+    (PinT-QBVM, Section 5), full y of every instance, one qbvm_solve_batched
+    call per batch: FP64 (3 kernel launches for the whole batch) and FP32
+    transforms + double-float refinement (about 20 launches and one
+    synchronisation per refinement step), each with its error against the
+    FP64 oracle on sampled instances."""
     import numpy as np
     import torch
     import bhcp_inputs as bi
@@ -699,34 +705,94 @@ def c1_batched_leg(args, device, stream, flush, count=10_000):
     gd = torch.as_tensor(g.ravel(), dtype=torch.float64, device=device)
     y = torch.empty(count * grid.unknowns, dtype=torch.float64, device=device)
     out = {"workload": f"c1_1d_63x64_batch{count}_delta_rhs", "instances": count,
-           "unknowns_per_batch": count * grid.unknowns}
-    with Q.Batch(1, grid.M, grid.L, grid.T, grid.nt, Q.FORM_PQ, alphas=list(alphas), rhs_kind=Q.RHS_DELTA) as bt:
-        steps = max(3, args.steps // 2)
-        evs = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(steps)]
-        with torch.cuda.stream(stream):
-            for _ in range(3):
-                bt.solve(gd, y, stream=stream)
-            for i in range(steps):
-                evs[i][0].record(stream)
-                bt.solve(gd, y, stream=stream)
-                evs[i][1].record(stream)
-                flush.zero_()
-        torch.cuda.synchronize()
-        ms = sum(a.elapsed_time(b) for a, b in evs) / steps
-        # two instances against single-instance plans (the same kernels, one instance each)
-        diffs = []
-        for b in (0, count - 1):
-            with Q.Plan(1, grid.M, grid.L, grid.T, grid.nt, Q.FORM_PQ, float(alphas[b]), 0.0, Q.FP64,
-                        Q.RHS_DELTA) as plan:
-                one = torch.empty(grid.unknowns, dtype=torch.float64, device=device)
-                plan.solve(gd[b * grid.Nx:(b + 1) * grid.Nx].contiguous(), one)
-                torch.cuda.synchronize()
-                mine = y[b * grid.unknowns:(b + 1) * grid.unknowns]
-                diffs.append(float((mine - one).norm() / one.norm()))
-    out.update({"ms_per_batch": ms, "value": count * grid.unknowns / (ms / 1e3), "unit": UNIT,
-                "solves_per_s": count / (ms / 1e3), "kernel_launches_per_batch": 3,
-                "rel_diff_vs_single_instance_plans": max(diffs),
-                "l2": "flushed between batches; output 322 MB"})
+           "unknowns_per_batch": count * grid.unknowns, "l2": "flushed between batches; output 322 MB"}
+    sample = (0, 1, count // 2, count - 1)
+    for name, prec in (("fp64", Q.FP64), ("fp32_refine", Q.FP32_REFINE)):
+        with Q.Batch(1, grid.M, grid.L, grid.T, grid.nt, Q.FORM_PQ, alphas=list(alphas), rhs_kind=Q.RHS_DELTA,
+                     precision=prec) as bt:
+            steps = max(3, args.steps // 2)
+            evs = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(steps)]
+            with torch.cuda.stream(stream):
+                for _ in range(3):
+                    bt.solve(gd, y, stream=stream)
+                for i in range(steps):
+                    evs[i][0].record(stream)
+                    bt.solve(gd, y, stream=stream)
+                    evs[i][1].record(stream)
+                    flush.zero_()
+            torch.cuda.synchronize()
+            ms = sum(a.elapsed_time(b) for a, b in evs) / steps
+            leg = {"ms_per_batch": ms, "value": count * grid.unknowns / (ms / 1e3), "unit": UNIT,
+                   "solves_per_s": count / (ms / 1e3)}
+            if prec == Q.FP64:
+                leg["kernel_launches_per_batch"] = 3
+            else:
+                it, rel = bt.refine_info
+                leg.update({"refine_steps": it, "max_rel_residual": rel,
+                            "dtype": "f32 transforms + double-float residual/update"})
+            if with_oracle:
+                import oracle as O
+                errs = []
+                for b in sample:
+                    want = O.solve_spectral(grid, O.PQ, float(alphas[b]),
+                                            O.delta_rhs(grid, O.PQ, float(alphas[b]), g[b]))
+                    got = y[b * grid.unknowns:(b + 1) * grid.unknowns].cpu().numpy()
+                    errs.append(O.rel_l2(got, want))
+                leg["rel_err_vs_oracle"] = max(errs)
+                leg["rel_err_sample"] = f"instances {list(sample)}"
+            out[name] = leg
+    # headline keys of the row: the FP64 batch (as before)
+    out.update({k: out["fp64"][k] for k in ("ms_per_batch", "value", "unit", "solves_per_s")})
+    out["kernel_launches_per_batch"] = 3
+    out["fp32_refine_over_fp64_solves_per_s"] = out["fp32_refine"]["solves_per_s"] / out["fp64"]["solves_per_s"]
+    return out
+
+
+def batched_2d_leg(args, device, stream, flush, count=64, with_oracle=True):
+    """A batch of `count` 2D instances of the learned-alpha shape (127^2
+    interior points x 128 levels, T = 0.1, 16 decaying sine modes, relative
+    noise log-uniform in [1e-4, 1e-2]), alpha = each instance's delta, full y:
+    the FP64 batch against the FP32 + double-float refinement batch, each with
+    its error against the FP64 oracle on two sampled instances."""
+    import numpy as np
+    import torch
+    import bhcp_inputs as bi
+    import paper_2107_06381_gb300 as Q
+    grid, z0, gd, delta = bi.alpha_training_batch(count, 77, M=128, nt=128, T=0.1)
+    g = torch.as_tensor(gd.reshape(count, -1), dtype=torch.float64, device=device).contiguous()
+    y = torch.empty(count * grid.unknowns, dtype=torch.float64, device=device)
+    out = {"workload": f"batch{count}_2d_127sq_x128_delta_rhs", "instances": count,
+           "unknowns_per_batch": count * grid.unknowns, "l2": "flushed between batches; output 1.06 GB"}
+    for name, prec in (("fp64", Q.FP64), ("fp32_refine", Q.FP32_REFINE)):
+        with Q.Batch(2, grid.M, grid.L, grid.T, grid.nt, Q.FORM_PQ, alphas=list(delta), rhs_kind=Q.RHS_DELTA,
+                     precision=prec) as bt:
+            steps = max(3, args.steps // 4)
+            evs = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(steps)]
+            with torch.cuda.stream(stream):
+                bt.solve(g, y, stream=stream)
+                for i in range(steps):
+                    evs[i][0].record(stream)
+                    bt.solve(g, y, stream=stream)
+                    evs[i][1].record(stream)
+                    flush.zero_()
+            torch.cuda.synchronize()
+            ms = sum(a.elapsed_time(b) for a, b in evs) / steps
+            leg = {"ms_per_batch": ms, "value": count * grid.unknowns / (ms / 1e3), "unit": UNIT,
+                   "solves_per_s": count / (ms / 1e3)}
+            if prec == Q.FP32_REFINE:
+                it, rel = bt.refine_info
+                leg.update({"refine_steps": it, "max_rel_residual": rel})
+            if with_oracle:
+                import oracle as O
+                errs = []
+                for b in (0, count - 1):
+                    a = float(delta[b])
+                    want = O.solve_spectral(grid, O.PQ, a, O.rhs_block0(O.PQ, a, grid.tau, gd[b]), levels=[0, 127])
+                    got = y[b * grid.unknowns:(b + 1) * grid.unknowns].view(grid.full_shape)[[0, 127]].cpu().numpy()
+                    errs.append(O.rel_l2(got, want))
+                leg["rel_err_vs_oracle_sampled_levels"] = max(errs)
+            out[name] = leg
+    out["fp32_refine_over_fp64_solves_per_s"] = out["fp32_refine"]["solves_per_s"] / out["fp64"]["solves_per_s"]
     return out
 
 

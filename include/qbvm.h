@@ -256,7 +256,7 @@ int qbvm_residual_noalloc(const qbvm_desc* desc, const double* y, const double* 
 /* ------------------------------------------------------------------------
  * Batched solve: `count` instances of ONE shape, each with its own alpha.
  * `desc` fixes everything but alpha (dim, m, L, T, nt, form, rhs_kind,
- * order; precision must be QBVM_FP64); `alphas` is a host array of `count`
+ * order, precision, refine_tol, refine_max_iters); `alphas` is a host array of `count`
  * values (NULL: desc's alpha, or its a-priori rule, for every instance), and
  * each alpha gives its instance's omega (-1/alpha for PinT-QBVM, -tau/alpha
  * for PinT-MQBVM, eqs. 3.3 / 3.6).  The instances are stored back to back in
@@ -269,8 +269,19 @@ int qbvm_residual_noalloc(const qbvm_desc* desc, const double* y, const double* 
  * Supported: space-first order (2D/3D; 1D with m <= 2048), nt a power
  * of two <= 1024.  Device pointers (asynchronous), or host pointers (staged
  * through batch-owned device copies; the call then synchronises `stream`).
+ * precision QBVM_FP32_REFINE: the refinement of the single plan over the
+ * whole batch -- FP32 DST passes over count*nt levels, the FP32 time solve
+ * with each instance's omega, one batched double-float residual with
+ * per-instance norms per step -- until the LARGEST relative residual of the
+ * batch is <= refine_tol (DIVERGED as for the single plan); the call then
+ * synchronises `stream` after every residual.  Needs (m-1)^d * nt divisible
+ * by 4.  Data FP32 cannot hold (root mean square of some instance's f outside
+ * [1e-18, 1e28]) or NaN / Inf send the batch to the FP64 pipeline (NaN / Inf:
+ * QBVM_ERR_NONFINITE after it).  qbvm_batch_refine_info reports the steps
+ * and the largest relative residual of the last solve.
  * The batch owns its tables ([count][nt/2] omega factors and [count][nt/2][Nx]
- * Step (b) reciprocals) and a base plan.  Errors: BAD_ARG (count < 1, an
+ * Step (b) reciprocals; FP32_REFINE: their FP32 roundings, the FP32 work
+ * array [count][nt][Nx] and per-instance norms) and a base plan.  Errors: BAD_ARG (count < 1, an
  * alpha not finite and positive, one host and one device pointer, memory of
  * a GPU other than the one the batch was planned on),
  * UNSUPPORTED, OOM, CUDA. */
@@ -279,6 +290,10 @@ int qbvm_batch_plan(const qbvm_desc* desc, int count, const double* alphas, qbvm
 int qbvm_solve_batched(qbvm_batch_t* batch, const double* g_or_F, double* y, int n0_only, void* stream);
 /* alphas: host [count] (may be NULL); unknowns_per_instance = nt * Nx (may be NULL). */
 int qbvm_batch_info(const qbvm_batch_t* batch, double* alphas, long long* unknowns_per_instance);
+/* FP32_REFINE batches: refinement steps and the largest relative residual
+ * ||f_b - A_b y_b|| / ||f_b|| over the instances after the last solve (NaN
+ * after an FP64 fallback).  Either output may be NULL. */
+int qbvm_batch_refine_info(const qbvm_batch_t* batch, int* iters, double* max_rel_residual);
 int qbvm_batch_destroy(qbvm_batch_t* batch);
 
 /* ------------------------------------------------------------------------

@@ -124,6 +124,8 @@ def load_library(path: str | None = None) -> ctypes.CDLL:
     lib.qbvm_solve_batched.restype = ip
     lib.qbvm_batch_info.argtypes = [vp, ctypes.POINTER(dp), ctypes.POINTER(ctypes.c_longlong)]
     lib.qbvm_batch_info.restype = ip
+    lib.qbvm_batch_refine_info.argtypes = [vp, ctypes.POINTER(ip), ctypes.POINTER(dp)]
+    lib.qbvm_batch_refine_info.restype = ip
     lib.qbvm_batch_destroy.argtypes = [vp]
     lib.qbvm_batch_destroy.restype = ip
     lib.qbvm_selftest_bounded_wait.argtypes = [ip, ctypes.POINTER(dp), vp]
@@ -589,8 +591,9 @@ class Batch:
     (or its a-priori rule from delta) for all B instances."""
 
     def __init__(self, dim, m, L, T, nt, form=FORM_PQ, alphas=None, count=None, alpha=0.0, delta=0.0,
-                 rhs_kind=RHS_DELTA, order=0):
-        self.desc = make_desc(dim, m, L, T, nt, form, alpha, delta, FP64, rhs_kind, 0.0, 0, order)
+                 rhs_kind=RHS_DELTA, order=0, precision=FP64, refine_tol=0.0, refine_max_iters=0):
+        self.desc = make_desc(dim, m, L, T, nt, form, alpha, delta, precision, rhs_kind, refine_tol,
+                              refine_max_iters, order)
         if alphas is not None:
             arr = (ctypes.c_double * len(alphas))(*[float(a) for a in alphas])
             n = len(alphas)
@@ -607,6 +610,14 @@ class Batch:
         _check(load_library().qbvm_solve_batched(self.handle, _ptr(g_or_F), _ptr(y), int(bool(n0_only)),
                                                  _stream(stream, g_or_F, y)), "qbvm_solve_batched")
         return y
+
+    @property
+    def refine_info(self):
+        """(refinement steps, largest relative residual) of the last FP32_REFINE solve."""
+        it, rel = ctypes.c_int(), ctypes.c_double()
+        _check(load_library().qbvm_batch_refine_info(self.handle, ctypes.byref(it), ctypes.byref(rel)),
+               "qbvm_batch_refine_info")
+        return it.value, rel.value
 
     @property
     def alphas(self):

@@ -12,6 +12,7 @@
 //   gipr[t] = 2 rho^{-H} gamma^{-t}  (t < H = nt/2, gamma = |omega|^{1/nt} e^{i pi/nt}),
 //   d_{2m} = 1 - gamma theta^{2m},
 // and on the device the Step (b) reciprocals cnorm / (d_{2m} + tau Lambda_l).
+#include <algorithm>
 #include <cmath>
 #include <new>
 #include <vector>
@@ -68,6 +69,21 @@ struct qbvm_batch {
     double* work = nullptr;       // general right-hand side with n0_only: [count][nt][Nx]
     double* stage_in = nullptr;   // host-pointer solves: device copies of the input and output
     double* stage_out = nullptr;
+    // FP32 transforms + double-float refinement (precision QBVM_FP32_REFINE)
+    std::vector<double2> h_gpow, h_gipw, h_gpowr, h_gipr, h_ak;   // FP64 omega tables, kept for the FP64 pipeline
+    std::vector<double> h_cnorm;
+    bool fp64_ready = false;      // FP64 tables on the device (FP64 batches, or an FP32 batch's fallback)
+    qbvm::BatchTables32 t32_delta, t32_gen;   // the FP32 tables with the delta / general cnorm
+    float2* omega_df = nullptr;   // omega_b as a double-float pair, [count]
+    double* omega64 = nullptr;    // omega_b, [count]
+    float* f32 = nullptr;         // FP32 work array [count][nt][Nx] (also r.hi of the residual)
+    float* g32 = nullptr;         // delta right-hand side: the FP32 DST of every g, [count][Nx]
+    double* partials = nullptr;   // residual partial sums [count][bpi][2]
+    double* sums = nullptr;       // per-instance ||r||^2, ||f||^2 [count][2]
+    int* flags = nullptr;         // input classification (NaN/Inf, nonzero)
+    int bpi = 1;
+    int last_iters = 0;
+    double last_rel = 0.0;        // largest relative residual over the instances at the end
     std::vector<void*> allocs;
 };
 
@@ -119,6 +135,97 @@ int dst_levels(const qbvm::Tables& tb, const double* in, double* out, long long 
     return QBVM_OK;
 }
 
+// The FP64 device tables of the batch (its per-instance omega factors, the
+// Step (b) reciprocals and, for the delta right-hand side, the y^0 factors)
+// from the FP64 host tables.
+int fp64_tables(qbvm_batch* bt) {
+    if (bt->fp64_ready) return QBVM_OK;
+    qbvm::PlanView v;
+    qbvm::plan_view(bt->base, &v);
+    const qbvm::Tables& tb = *v.tb;
+    const long long count = bt->count, H = tb.nt / 2, Nx = tb.Nx;
+    int rc = bupload(bt, &bt->gpow, bt->h_gpow);
+    if (!rc) rc = bupload(bt, &bt->gipw, bt->h_gipw);
+    if (!rc) rc = bupload(bt, &bt->gpowr, bt->h_gpowr);
+    if (!rc) rc = bupload(bt, &bt->gipr, bt->h_gipr);
+    if (!rc) rc = bupload(bt, &bt->ak, bt->h_ak);
+    if (!rc) rc = bupload(bt, &bt->cnorm, bt->h_cnorm);
+    if (!rc) rc = balloc(bt, &bt->qinv, (size_t)(count * H * Nx));
+    if (!rc) {
+        // the FP64 plan's lamtau: the base plan of an FP32 batch has it too
+        k_make_qinv_batched<<<grid_for(count * H * Nx), 256>>>(bt->ak, tb.lamtau, bt->cnorm, (int)H, Nx, count,
+                                                              bt->qinv);
+        if (cudaGetLastError() != cudaSuccess) rc = QBVM_ERR_CUDA;
+    }
+    if (!rc && bt->d.rhs_kind == QBVM_RHS_DELTA) {
+        if (!bt->ghat) rc = balloc(bt, &bt->ghat, (size_t)(count * Nx));
+        if (!rc) rc = balloc(bt, &bt->y0fac, (size_t)(count * Nx));
+        if (!rc) {
+            k_y0fac_batched<<<grid_for(count * Nx), 256>>>(bt->qinv, (int)H, Nx, count, bt->y0fac);
+            if (cudaGetLastError() != cudaSuccess) rc = QBVM_ERR_CUDA;
+        }
+    }
+    if (!rc) bt->fp64_ready = true;
+    return rc;
+}
+
+// The FP32 tables (the FP64 ones rounded once), omega per instance, and the
+// workspace of the refinement.
+int fp32_tables(qbvm_batch* bt) {
+    qbvm::PlanView v;
+    qbvm::plan_view(bt->base, &v);
+    const qbvm::Tables& tb = *v.tb;
+    const long long count = bt->count, Nx = tb.Nx, nt = tb.nt;
+    auto to32 = [](const std::vector<double2>& a) {
+        std::vector<float2> o(a.size());
+        for (size_t i = 0; i < a.size(); ++i) o[i] = make_float2((float)a[i].x, (float)a[i].y);
+        return o;
+    };
+    double cn = 1.0;                               // FP32 DSTs: prod 2/(n_d + 1) (not the FP64 4x), 1/nt
+    for (int i = 0; i < tb.dim; ++i) cn *= 2.0 / (tb.n[i] + 1);
+    cn /= nt;
+    std::vector<float> cd((size_t)count), cg((size_t)count, (float)(v.tau * cn)), rh((size_t)count), ri((size_t)count);
+    std::vector<float2> odf((size_t)count);
+    std::vector<double> o64((size_t)count);
+    for (long long b = 0; b < count; ++b) {
+        const double a = bt->alpha[(size_t)b];
+        const double om = bt->d.form == QBVM_FORM_PQ ? -1.0 / a : -v.tau / a;
+        o64[(size_t)b] = om;
+        const float oh = (float)om;
+        odf[(size_t)b] = make_float2(oh, (float)(om - (double)oh));
+        cd[(size_t)b] = (float)(-om * cn);
+        rh[(size_t)b] = (float)std::sqrt(std::fabs(om));
+        ri[(size_t)b] = (float)(1.0 / std::sqrt(std::fabs(om)));
+    }
+    float2 *gp, *gi, *gr, *gir, *ak;
+    float *pcd, *pcg, *prh, *pri;
+    int rc = bupload(bt, &gp, to32(bt->h_gpow));
+    if (!rc) rc = bupload(bt, &gi, to32(bt->h_gipw));
+    if (!rc) rc = bupload(bt, &gr, to32(bt->h_gpowr));
+    if (!rc) rc = bupload(bt, &gir, to32(bt->h_gipr));
+    if (!rc) rc = bupload(bt, &ak, to32(bt->h_ak));
+    if (!rc) rc = bupload(bt, &pcd, cd);
+    if (!rc) rc = bupload(bt, &pcg, cg);
+    if (!rc) rc = bupload(bt, &prh, rh);
+    if (!rc) rc = bupload(bt, &pri, ri);
+    if (!rc) rc = bupload(bt, &bt->omega_df, odf);
+    if (!rc) rc = bupload(bt, &bt->omega64, o64);
+    if (rc) return rc;
+    bt->t32_delta = {gp, gi, gr, gir, ak, pcd, prh, pri};
+    bt->t32_gen = {gp, gi, gr, gir, ak, pcg, prh, pri};
+    // blocks per instance: about four groups of four unknowns per thread
+    // (measured on 10 000 instances of 63 x 64: one, two and four groups per
+    // thread took 2.51, 2.12 and 1.93 ms per refined batch)
+    bt->bpi = qbvm::residual_blocks_per_instance(tb);
+    if (count * (long long)bt->bpi > 0x7fffffffLL) bt->bpi = (int)std::max(1LL, 0x7fffffffLL / count);
+    rc = balloc(bt, &bt->f32, (size_t)(count * nt * Nx));
+    if (!rc && bt->d.rhs_kind == QBVM_RHS_DELTA) rc = balloc(bt, &bt->g32, (size_t)(count * Nx));
+    if (!rc) rc = balloc(bt, &bt->partials, (size_t)(2 * count * bt->bpi));
+    if (!rc) rc = balloc(bt, &bt->sums, (size_t)(2 * count));
+    if (!rc) rc = balloc(bt, &bt->flags, 2);
+    return rc;
+}
+
 // 1: memory of device `dev` (or managed), 0: host memory, -1: another GPU's
 // memory (the batch's kernels would read it as a peer: refused).
 int dev_kind(const void* p, int dev) {
@@ -133,6 +240,7 @@ int dev_kind(const void* p, int dev) {
 }
 
 int solve_batched_dev(qbvm_batch_t* bt, const double* g_or_F, double* y, int n0_only, cudaStream_t s);
+int solve_batched_fp64(qbvm_batch_t* bt, const double* g_or_F, double* y, int n0_only, cudaStream_t s);
 
 }  // namespace
 
@@ -146,8 +254,13 @@ int qbvm_batch_plan(const qbvm_desc* desc, int count, const double* alphas, qbvm
     if (!(std::isfinite(d0.alpha) && (d0.alpha > 0 || d0.delta > 0))) return QBVM_ERR_BAD_ARG;
     int rc = qbvm::validate_desc(&d0);
     if (rc) return rc;
-    if (desc->precision != QBVM_FP64) return QBVM_ERR_UNSUPPORTED;
     if ((desc->nt & (desc->nt - 1)) != 0) return QBVM_ERR_UNSUPPORTED;       // half-length time transforms only
+    if (desc->precision == QBVM_FP32_REFINE) {
+        // the batched residual moves groups of four unknowns per thread
+        long long nx = 1;
+        for (int i = 0; i < desc->dim; ++i) nx *= desc->m[i] - 1;
+        if ((nx * desc->nt) % 4 != 0) return QBVM_ERR_UNSUPPORTED;
+    }
     // the batch runs space-first; AUTO is space-first whenever m allows the DST
     // (m <= 2048), which the descriptor check already required of every m when
     // the order is space-first
@@ -211,27 +324,13 @@ int qbvm_batch_plan(const qbvm_desc* desc, int count, const double* alphas, qbvm
             d[m] = make_double2(1.0 - g1 * std::cos(a), -g1 * std::sin(a));
         }
     }
-    rc = bupload(bt, &bt->gpow, gpow);
-    if (!rc) rc = bupload(bt, &bt->gipw, gipw);
-    if (!rc) rc = bupload(bt, &bt->gpowr, gpowr);
-    if (!rc) rc = bupload(bt, &bt->gipr, gipr);
-    if (!rc) rc = bupload(bt, &bt->ak, ak);
-    if (!rc) rc = bupload(bt, &bt->cnorm, cnv);
-    const long long Nx = tb.Nx;
-    if (!rc) rc = balloc(bt, &bt->qinv, (size_t)count * H * Nx);
-    if (!rc) {
-        k_make_qinv_batched<<<grid_for((long long)count * H * Nx), 256>>>(bt->ak, tb.lamtau, bt->cnorm, H, Nx, count,
-                                                                          bt->qinv);
-        if (cudaGetLastError() != cudaSuccess) rc = QBVM_ERR_CUDA;
-    }
-    if (!rc && desc->rhs_kind == QBVM_RHS_DELTA) {
-        rc = balloc(bt, &bt->ghat, (size_t)count * Nx);
-        if (!rc) rc = balloc(bt, &bt->y0fac, (size_t)count * Nx);
-        if (!rc) {
-            k_y0fac_batched<<<grid_for((long long)count * Nx), 256>>>(bt->qinv, H, Nx, count, bt->y0fac);
-            if (cudaGetLastError() != cudaSuccess) rc = QBVM_ERR_CUDA;
-        }
-    }
+    bt->h_gpow = std::move(gpow);
+    bt->h_gipw = std::move(gipw);
+    bt->h_gpowr = std::move(gpowr);
+    bt->h_gipr = std::move(gipr);
+    bt->h_ak = std::move(ak);
+    bt->h_cnorm = std::move(cnv);
+    rc = desc->precision == QBVM_FP64 ? fp64_tables(bt) : fp32_tables(bt);
     if (!rc && cudaDeviceSynchronize() != cudaSuccess) {
         cudaGetLastError();
         rc = QBVM_ERR_CUDA;
@@ -280,7 +379,145 @@ int qbvm_solve_batched(qbvm_batch_t* bt, const double* g_or_F, double* y, int n0
 
 namespace {
 
+// ---- FP32 transforms + double-float refinement over the whole batch --------
+//
+// As the single plan's refinement (y_0 = A32^{-1} f, then r = f - A y,
+// y += A32^{-1} r), every stage once over all instances: the FP32 DST passes
+// over count * nt levels, the FP32 time solve with each instance's omega
+// tables, one batched double-float residual with per-instance norms.  The
+// batch stops when the largest relative residual is at most the tolerance;
+// a stall above 1e-10 or the cap above the tolerance is QBVM_ERR_DIVERGED.
+
+#define BCK(...)                                      \
+    do {                                              \
+        if ((__VA_ARGS__) != cudaSuccess) {           \
+            cudaGetLastError();                       \
+            return QBVM_ERR_CUDA;                     \
+        }                                             \
+    } while (0)
+
+// One FP32 solve of every instance: rhs (FP64 when rhs_fp64, else the FP32
+// work array; one level per instance when delta) -> ydf (store, or add when
+// accumulate, into the double-float iterate).
+int fp32_solve_batched(qbvm_batch* bt, const qbvm::Tables& tb, const void* rhs, int rhs_fp64, int delta, void* ydf,
+                       int accumulate, cudaStream_t s) {
+    const long long B = bt->count, nx = tb.n[0], ny = tb.n[1], nz = tb.n[2], nt = tb.nt, Nx = tb.Nx;
+    const long long lev = B * nt;
+    float* w = bt->f32;
+    if (delta) {
+        BCK(qbvm::launch_dst<float, double, 0>((const double*)rhs, bt->g32, tb.n[0], tb.lpd[0], B * ny * nz, 1, tb.tw_s32[0], tb.sn_s32[0], s));
+        if (tb.dim >= 2) BCK(qbvm::launch_dst<float, float, 0>(bt->g32, bt->g32, tb.n[1], tb.lpd[1], B * nz, nx, tb.tw_s32[1], tb.sn_s32[1], s));
+        if (tb.dim == 3) BCK(qbvm::launch_dst<float, float, 0>(bt->g32, bt->g32, tb.n[2], tb.lpd[2], B, nx * ny, tb.tw_s32[2], tb.sn_s32[2], s));
+        BCK(qbvm::launch_time_solve_batched32(bt->g32, w, tb, B, Nx, nt * Nx, bt->t32_delta, 1, 0, s));
+    } else {
+        if (rhs_fp64) BCK(qbvm::launch_dst<float, double, 0>((const double*)rhs, w, tb.n[0], tb.lpd[0], lev * ny * nz, 1, tb.tw_s32[0], tb.sn_s32[0], s));
+        else BCK(qbvm::launch_dst<float, float, 0>((const float*)rhs, w, tb.n[0], tb.lpd[0], lev * ny * nz, 1, tb.tw_s32[0], tb.sn_s32[0], s));
+        if (tb.dim >= 2) BCK(qbvm::launch_dst<float, float, 0>(w, w, tb.n[1], tb.lpd[1], lev * nz, nx, tb.tw_s32[1], tb.sn_s32[1], s));
+        if (tb.dim == 3) BCK(qbvm::launch_dst<float, float, 0>(w, w, tb.n[2], tb.lpd[2], lev, nx * ny, tb.tw_s32[2], tb.sn_s32[2], s));
+        BCK(qbvm::launch_time_solve_batched32(w, w, tb, B, nt * Nx, nt * Nx, bt->t32_gen, 0, 0, s));
+    }
+    if (tb.dim == 3) BCK(qbvm::launch_dst<float, float, 0>(w, w, tb.n[2], tb.lpd[2], lev, nx * ny, tb.tw_s32[2], tb.sn_s32[2], s));
+    if (tb.dim >= 2) BCK(qbvm::launch_dst<float, float, 0>(w, w, tb.n[1], tb.lpd[1], lev * nz, nx, tb.tw_s32[1], tb.sn_s32[1], s));
+    if (accumulate) BCK(qbvm::launch_dst<float, float, 1>(w, ydf, tb.n[0], tb.lpd[0], lev * ny * nz, 1, tb.tw_s32[0], tb.sn_s32[0], s));
+    else BCK(qbvm::launch_dst<float, float, 2>(w, ydf, tb.n[0], tb.lpd[0], lev * ny * nz, 1, tb.tw_s32[0], tb.sn_s32[0], s));
+    return QBVM_OK;
+}
+
+int solve_batched_fp32r(qbvm_batch* bt, const double* in, double* y, int n0_only, cudaStream_t s) {
+    qbvm::PlanView v;
+    qbvm::plan_view(bt->base, &v);
+    const qbvm::Tables& tb = *v.tb;
+    const long long B = bt->count, Nx = tb.Nx, nt = tb.nt;
+    const int delta = bt->d.rhs_kind == QBVM_RHS_DELTA;
+    const double tol = bt->d.refine_tol > 0 ? bt->d.refine_tol : 1e-13;
+    const int maxit = bt->d.refine_max_iters > 0 ? bt->d.refine_max_iters : 10;
+    double* yfull = y;
+    if (n0_only) {                                   // the iterate needs every level
+        if (!bt->work) {
+            int rc = balloc(bt, &bt->work, (size_t)(B * nt * Nx));
+            if (rc) return rc;
+        }
+        yfull = bt->work;
+    }
+    int rc = fp32_solve_batched(bt, tb, in, 1, delta, yfull, 0, s);
+    if (rc) return rc;
+    std::vector<double> h((size_t)(2 * B)), fn2((size_t)B, 0.0);
+    double prev = INFINITY, rel = 0.0;
+    int it = 0, status = QBVM_OK;
+    for (bool first = true;; first = false) {
+        BCK(qbvm::launch_residual_df_batched(yfull, in, delta, tb, v.h2inv, B, bt->omega_df, bt->omega64, bt->f32,
+                                             bt->partials, bt->sums, first ? 1 : 0, bt->bpi, s));
+        BCK(cudaMemcpyAsync(h.data(), bt->sums, sizeof(double) * 2 * B, cudaMemcpyDeviceToHost, s));
+        BCK(cudaStreamSynchronize(s));
+        rel = 0.0;
+        bool finite = true, fp32_range = true;
+        for (long long b = 0; b < B; ++b) {
+            if (first) {
+                fn2[(size_t)b] = h[(size_t)(2 * b + 1)];
+                const double cnt = (double)Nx * (delta ? 1 : nt);
+                const double rms = std::sqrt(fn2[(size_t)b] / cnt);
+                // data FP32 cannot hold (beyond its range, or flushed to zero)
+                if (rms > 0 && (rms < 1e-18 || rms > 1e28)) fp32_range = false;
+            }
+            const double r2 = h[(size_t)(2 * b)], f2 = fn2[(size_t)b];
+            if (!std::isfinite(r2) || !std::isfinite(f2)) finite = false;
+            rel = std::max(rel, f2 > 0 ? std::sqrt(r2 / f2) : std::sqrt(r2));
+        }
+        if (first && finite && fp32_range) {
+            // ||f_b|| = 0: all-zero data (y_b = 0 is right) or data so small that
+            // FP32 flushed it to zero -- the input decides
+            const long long per_in = delta ? Nx : nt * Nx;
+            for (long long b = 0; b < B && fp32_range; ++b) {
+                if (fn2[(size_t)b] != 0.0) continue;
+                int fl[2] = {0, 0};
+                BCK(qbvm::launch_classify(in + b * per_in, per_in, bt->flags, s));
+                BCK(cudaMemcpyAsync(fl, bt->flags, sizeof(fl), cudaMemcpyDeviceToHost, s));
+                BCK(cudaStreamSynchronize(s));
+                if (fl[0]) finite = false;
+                if (fl[1]) fp32_range = false;
+            }
+        }
+        if (first && (!finite || !fp32_range)) {
+            // NaN / Inf anywhere, or data outside the FP32 range: the FP64
+            // pipeline solves the batch (it carries NaN / Inf through IEEE
+            // arithmetic, as the single FP64 solve does)
+            rc = fp64_tables(bt);
+            if (rc) return rc;
+            rc = solve_batched_fp64(bt, in, y, n0_only, s);
+            bt->last_iters = 0;
+            bt->last_rel = NAN;
+            return rc ? rc : (finite ? QBVM_OK : QBVM_ERR_NONFINITE);
+        }
+        if (!finite) return QBVM_ERR_NONFINITE;
+        if (rel <= tol) break;
+        if (rel > 0.5 * prev) {                      // no contraction
+            if (rel > 1e-10) status = QBVM_ERR_DIVERGED;
+            break;
+        }
+        if (it >= maxit) {
+            status = QBVM_ERR_DIVERGED;
+            break;
+        }
+        prev = rel;
+        rc = fp32_solve_batched(bt, tb, bt->f32, 0, 0, yfull, 1, s);
+        if (rc) return rc;
+        ++it;
+    }
+    BCK(qbvm::launch_df_to_double(yfull, B * nt * Nx, s));
+    if (n0_only)
+        BCK(cudaMemcpy2DAsync(y, sizeof(double) * Nx, yfull, sizeof(double) * nt * Nx, sizeof(double) * Nx, B,
+                              cudaMemcpyDeviceToDevice, s));
+    bt->last_iters = it;
+    bt->last_rel = rel;
+    return status;
+}
+
 int solve_batched_dev(qbvm_batch_t* bt, const double* g_or_F, double* y, int n0_only, cudaStream_t s) {
+    if (bt->d.precision == QBVM_FP32_REFINE) return solve_batched_fp32r(bt, g_or_F, y, n0_only, s);
+    return solve_batched_fp64(bt, g_or_F, y, n0_only, s);
+}
+
+int solve_batched_fp64(qbvm_batch_t* bt, const double* g_or_F, double* y, int n0_only, cudaStream_t s) {
     qbvm::PlanView v;
     qbvm::plan_view(bt->base, &v);
     const qbvm::Tables& tb = *v.tb;
@@ -327,6 +564,13 @@ int qbvm_batch_info(const qbvm_batch_t* bt, double* alphas, long long* unknowns_
     if (alphas)
         for (long long b = 0; b < bt->count; ++b) alphas[b] = bt->alpha[(size_t)b];
     if (unknowns_per_instance) *unknowns_per_instance = v.tb->Nx * v.tb->nt;
+    return QBVM_OK;
+}
+
+int qbvm_batch_refine_info(const qbvm_batch_t* bt, int* iters, double* max_rel_residual) {
+    if (!bt) return QBVM_ERR_BAD_ARG;
+    if (iters) *iters = bt->last_iters;
+    if (max_rel_residual) *max_rel_residual = bt->last_rel;
     return QBVM_OK;
 }
 

@@ -86,6 +86,30 @@ cudaError_t launch_time_solve_batched(const double* in, double* out, const Table
 // is this factor times the mode's coefficient.  Power-of-two nt: from tb.qinv;
 // other nt: direct FP64 divisions over every frequency.
 cudaError_t launch_make_y0fac(const Tables& tb, double cnorm, double* out, cudaStream_t s);
+// Per-instance FP32 omega tables of a batch: gpow, gipw, gpowr, gipr, ak are
+// [count][H] (the FP64 tables rounded once), cnorm, rho_h = |omega|^{1/2},
+// rho_hinv [count].
+struct BatchTables32 {
+    const float2 *gpow = nullptr, *gipw = nullptr, *gpowr = nullptr, *gipr = nullptr, *ak = nullptr;
+    const float *cnorm = nullptr, *rho_h = nullptr, *rho_hinv = nullptr;
+};
+// The FP32 time solve of `count` instances (Step (a)-(c) in the sine basis,
+// each with its own omega); instance b reads in + b in_stride, writes
+// out + b out_stride.
+cudaError_t launch_time_solve_batched32(const float* in, float* out, const Tables& tb, long long count,
+                                        long long in_stride, long long out_stride, const BatchTables32& bt,
+                                        int delta_rhs, int n0_only, cudaStream_t s);
+// Double-float residual of `count` instances stored back to back ([count][nt][Nx]
+// y and r, f [count][nt][Nx] or [count][Nx] for the delta right-hand side),
+// instance b with omega_b as a double-float pair omega_df[b] and in FP64
+// omega64[b]; sums[2 b], sums[2 b + 1] receive ||r_b||^2 and (fnorm) ||f_b||^2.
+// partials: 2 * count * bpi doubles, bpi <= residual_blocks_per_instance(tb).
+// Requires nt * Nx divisible by 4 and 16-byte aligned y, r (and f, general).
+cudaError_t launch_residual_df_batched(const void* y_df, const double* f, int delta_rhs, const Tables& tb,
+                                       const double h2inv[3], long long count, const float2* omega_df,
+                                       const double* omega64, float* r_out, double* partials, double* sums,
+                                       int fnorm, int bpi, cudaStream_t s);
+int residual_blocks_per_instance(const Tables& tb);
 // y[l] = fac[l] * x[l], l < n
 cudaError_t launch_mul_modes(const double* x, const double* fac, double* y, long long n, cudaStream_t s);
 

@@ -458,11 +458,11 @@ constexpr size_t ts_reg_smem() { return (size_t)4 * (1 << LH) * sizeof(float2) +
 // Minimum CTAs per SM: 64 registers for H = 256 / 128 (from 80: 24 -> 32
 // resident warps, 4 % faster at H = 128), 48 below.
 template <int LH>
-__global__ void __launch_bounds__(TS_MODES * TsCfg<LH>::N2, LH == 8 ? 4 : LH == 7 ? 8 : LH == 6 ? 10 : 20)
-k_time_solve_reg(const float* in, float* out, long long Nx, const float2* __restrict__ tw,
-                 const float2* __restrict__ gpow, const float2* __restrict__ gipw, const float2* __restrict__ ak,
-                 const float* __restrict__ lamtau, float cnorm, float rho_h, float rho_hinv, int delta_rhs,
-                 int n0_only) {
+__device__ __forceinline__ void time_solve_reg_tile(const float* in, float* out, long long Nx,
+                                                    const float2* __restrict__ tw, const float2* __restrict__ gpow,
+                                                    const float2* __restrict__ gipw, const float2* __restrict__ ak,
+                                                    const float* __restrict__ lamtau, float cnorm, float rho_h,
+                                                    float rho_hinv, int delta_rhs, int n0_only, long long tile) {
     using G = TsCfg<LH>;
     constexpr int H = 1 << LH, NT = 2 * H, N1 = G::N1, N2 = G::N2, T = N2, NTH = TS_MODES * T, Q = N1 / T;
     constexpr int RS = G::RS, RSTEP = NTH / TS_MODES;
@@ -482,7 +482,7 @@ k_time_solve_reg(const float* in, float* out, long long Nx, const float2* __rest
         sak[i] = ak[i];
     }
     pdl_wait();                                                        // the input is a predecessor's output
-    const long long l0 = (long long)blockIdx.x * TS_MODES;
+    const long long l0 = tile * TS_MODES;
     {   // load phase: rows of TS_MODES consecutive modes, a batch of loads in flight per thread
         const int cc = tid % TS_MODES, r0 = tid / TS_MODES;
         const bool ok = l0 + cc < Nx;
@@ -596,6 +596,34 @@ k_time_solve_reg(const float* in, float* out, long long Nx, const float2* __rest
             for (int r = r0; r < rows; r += RSTEP) dst[(long long)r * Nx] = st[r * RS + cc];
         }
     }
+}
+
+template <int LH>
+__global__ void __launch_bounds__(TS_MODES * TsCfg<LH>::N2, LH == 8 ? 4 : LH == 7 ? 8 : LH == 6 ? 10 : 20)
+k_time_solve_reg(const float* in, float* out, long long Nx, const float2* __restrict__ tw,
+                 const float2* __restrict__ gpow, const float2* __restrict__ gipw, const float2* __restrict__ ak,
+                 const float* __restrict__ lamtau, float cnorm, float rho_h, float rho_hinv, int delta_rhs,
+                 int n0_only) {
+    time_solve_reg_tile<LH>(in, out, Nx, tw, gpow, gipw, ak, lamtau, cnorm, rho_h, rho_hinv, delta_rhs, n0_only,
+                            (long long)blockIdx.x);
+}
+
+// The same solve for `count` instances of one shape stored back to back, each
+// with its own omega: block = b * tiles + mode tile; instance b reads
+// in + b in_stride, writes out + b out_stride and takes the rows b of the
+// [count][H] tables gpow, gipw, ak and of cnorm, rho_h, rho_hinv.
+template <int LH>
+__global__ void __launch_bounds__(TS_MODES * TsCfg<LH>::N2, LH == 8 ? 4 : LH == 7 ? 8 : LH == 6 ? 10 : 20)
+k_time_solve_reg_batched(const float* in, float* out, long long Nx, long long tiles, long long in_stride,
+                         long long out_stride, const float2* __restrict__ tw, const float2* __restrict__ gpow,
+                         const float2* __restrict__ gipw, const float2* __restrict__ ak,
+                         const float* __restrict__ lamtau, const float* __restrict__ cnorm,
+                         const float* __restrict__ rho_h, const float* __restrict__ rho_hinv, int delta_rhs,
+                         int n0_only) {
+    const long long b = (long long)blockIdx.x / tiles, tile = (long long)blockIdx.x - b * tiles;
+    constexpr int H = 1 << LH;
+    time_solve_reg_tile<LH>(in + b * in_stride, out + b * out_stride, Nx, tw, gpow + b * H, gipw + b * H,
+                            ak + b * H, lamtau, cnorm[b], rho_h[b], rho_hinv[b], delta_rhs, n0_only, tile);
 }
 
 template <int LH>
@@ -789,6 +817,70 @@ cudaError_t launch_time_solve_batched(const double* in, double* out, const Table
         default: QBVM_TSB(-1)
     }
 #undef QBVM_TSB
+}
+
+template <int LH>
+static cudaError_t launch_time_solve_reg_batched_lh(const float* in, float* out, const Tables& tb, long long count,
+                                                    long long in_stride, long long out_stride, const float2* gpow,
+                                                    const float2* gipw, const float2* ak, const float* cnorm,
+                                                    const float* rho_h, const float* rho_hinv, int delta_rhs,
+                                                    int n0_only, cudaStream_t s) {
+    auto kern = k_time_solve_reg_batched<LH>;
+    constexpr size_t smem = ts_reg_smem<LH>();
+    cudaError_t e = set_smem(kern, smem);
+    if (e != cudaSuccess) return e;
+    const long long tiles = (tb.Nx + TS_MODES - 1) / TS_MODES;
+    if (count < 1 || tiles * count > 0x7fffffffLL) return cudaErrorInvalidValue;
+    QBVM_PDL(kern, (unsigned)(tiles * count), TS_MODES * TsCfg<LH>::N2, smem, s, in, out, tb.Nx, tiles, in_stride,
+             out_stride, reinterpret_cast<const float2*>(tb.tw_t32), gpow, gipw, ak,
+             reinterpret_cast<const float*>(tb.lamtau32), cnorm, rho_h, rho_hinv, delta_rhs, n0_only);
+    return cudaGetLastError();
+}
+
+// The generic FP32 tile for the other time lengths (nt = 2 ... 32, 1024):
+// instance b takes rows b of the [count][H] tables and cnorm[b].
+template <int MAXB4>
+__global__ void __launch_bounds__(TILE_THREADS)
+k_time_solve_batched32(const float* in, float* out, long long Nx, int lh, int lw, long long tiles,
+                       long long in_stride, long long out_stride, const float2* __restrict__ tw,
+                       const float2* __restrict__ gpow, const float2* __restrict__ gipw,
+                       const float2* __restrict__ gpowr, const float2* __restrict__ gipr,
+                       const float2* __restrict__ ak, const float* __restrict__ lamtau,
+                       const float* __restrict__ cnorm, int delta_rhs, int n0_only) {
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    const long long b = (long long)blockIdx.x / tiles, tile = (long long)blockIdx.x - b * tiles;
+    const long long H = 1LL << lh;
+    time_solve_tile<float, MAXB4>(in + b * in_stride, out + b * out_stride, Nx, lh, lw, tw, gpow + b * H,
+                                  gipw + b * H, ak + b * H, lamtau, cnorm[b], gpowr + b * H, gipr + b * H, nullptr,
+                                  delta_rhs, n0_only, tile, smem_raw);
+}
+
+cudaError_t launch_time_solve_batched32(const float* in, float* out, const Tables& tb, long long count,
+                                        long long in_stride, long long out_stride, const BatchTables32& bt,
+                                        int delta_rhs, int n0_only, cudaStream_t s) {
+    switch (tb.lnt - 1) {
+        case 5: return launch_time_solve_reg_batched_lh<5>(in, out, tb, count, in_stride, out_stride, bt.gpow, bt.gipw, bt.ak, bt.cnorm, bt.rho_h, bt.rho_hinv, delta_rhs, n0_only, s);
+        case 6: return launch_time_solve_reg_batched_lh<6>(in, out, tb, count, in_stride, out_stride, bt.gpow, bt.gipw, bt.ak, bt.cnorm, bt.rho_h, bt.rho_hinv, delta_rhs, n0_only, s);
+        case 7: return launch_time_solve_reg_batched_lh<7>(in, out, tb, count, in_stride, out_stride, bt.gpow, bt.gipw, bt.ak, bt.cnorm, bt.rho_h, bt.rho_hinv, delta_rhs, n0_only, s);
+        case 8: return launch_time_solve_reg_batched_lh<8>(in, out, tb, count, in_stride, out_stride, bt.gpow, bt.gipw, bt.ak, bt.cnorm, bt.rho_h, bt.rho_hinv, delta_rhs, n0_only, s);
+        default: break;
+    }
+    constexpr int MB = time_tile_maxb4<float>();
+    constexpr int TILE = 4 * MB * TILE_THREADS;
+    const int lh = tb.lnt - 1, H = 1 << lh;
+    int lw = tile_lw(lh, TILE);
+    while (lw > 0 && (1LL << (lw - 1)) >= tb.Nx) --lw;         // no wider than the modes
+    const int W = 1 << lw;
+    const long long tiles = (tb.Nx + W - 1) / W;
+    if (count < 1 || tiles * count > 0x7fffffffLL) return cudaErrorInvalidValue;
+    const size_t smem = sizeof(float2) * ((size_t)H * W + H);
+    auto kern = k_time_solve_batched32<MB>;
+    cudaError_t e = set_smem(kern, smem);
+    if (e != cudaSuccess) return e;
+    QBVM_PDL(kern, (unsigned)(tiles * count), TILE_THREADS, smem, s, in, out, tb.Nx, lh, lw, tiles, in_stride,
+             out_stride, reinterpret_cast<const float2*>(tb.tw_t32), bt.gpow, bt.gipw, bt.gpowr, bt.gipr, bt.ak,
+             reinterpret_cast<const float*>(tb.lamtau32), bt.cnorm, delta_rhs, n0_only);
+    return cudaGetLastError();
 }
 
 // ------------------------------------------------------------------ 1D path
@@ -1311,18 +1403,33 @@ __device__ __forceinline__ dfloat df_add_un(dfloat a, dfloat b) {
 // solve).  Bounded to 64 registers (4 CTAs per SM): the 3D stencil took 97
 // and ran at a quarter of the warp slots.
 template <bool EQ, int DIMS>
-__global__ void __launch_bounds__(RES_THREADS, 4)
-k_residual_df4(const float2* __restrict__ y, const double* __restrict__ f, int delta_rhs, int nt, int nx, int ny,
-               int nz, DfCoef k, double f0_scale, int fnorm, float* __restrict__ r_out, double* partials) {
-    pdl_trigger();
-    pdl_wait();
+__device__ __forceinline__ void residual_df4_body(const float2* __restrict__ y, const double* __restrict__ f,
+                                                  int delta_rhs, int nt, int nx, int ny, int nz, const DfCoef& k,
+                                                  double f0_scale, int fnorm, float* __restrict__ r_out,
+                                                  long long blk, long long nblk, double* part2) {
     __shared__ double sh[32];
     const long long Nx = (long long)nx * ny * nz, N = (long long)nt * Nx, pl = (long long)nx * ny;
     const long long ngroups = (N + 3) >> 2;
     const int lane = threadIdx.x & 31;
-    const long long wid = ((long long)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
-    const long long nw = ((long long)gridDim.x * blockDim.x) >> 5;
+    const long long wid = (blk * blockDim.x + threadIdx.x) >> 5;
+    const long long nw = (nblk * blockDim.x) >> 5;
+    // (t, z, y, x) of a flat index: 32-bit divisions when the index fits (a
+    // 64-bit division is a long software sequence, and short-lived threads --
+    // small instances of a batch -- pay it for few elements)
     auto split = [&](long long i, int& t, int& z, int& yy, int& x) {
+        if (i < 0x7fffffffLL && Nx < 0x7fffffffLL) {
+            const unsigned ui = (unsigned)i, uN = (unsigned)Nx, up = (unsigned)pl, ux = (unsigned)nx;
+            const unsigned ut = ui / uN;
+            unsigned r = ui - ut * uN;
+            const unsigned uz = r / up;
+            r -= uz * up;
+            const unsigned uy = r / ux;
+            t = (int)ut;
+            z = (int)uz;
+            yy = (int)uy;
+            x = (int)(r - uy * ux);
+            return;
+        }
         t = (int)(i / Nx);
         long long r = i - (long long)t * Nx;
         z = (int)(r / pl);
@@ -1451,8 +1558,60 @@ k_residual_df4(const float2* __restrict__ y, const double* __restrict__ f, int d
     double a = block_sum(nr.value(), sh);
     double b = block_sum(nf.value(), sh);
     if (threadIdx.x == 0) {
-        partials[2 * blockIdx.x] = a;
-        partials[2 * blockIdx.x + 1] = b;
+        part2[0] = a;
+        part2[1] = b;
+    }
+}
+
+template <bool EQ, int DIMS>
+__global__ void __launch_bounds__(RES_THREADS, 4)
+k_residual_df4(const float2* __restrict__ y, const double* __restrict__ f, int delta_rhs, int nt, int nx, int ny,
+               int nz, DfCoef k, double f0_scale, int fnorm, float* __restrict__ r_out, double* partials) {
+    pdl_trigger();
+    pdl_wait();
+    residual_df4_body<EQ, DIMS>(y, f, delta_rhs, nt, nx, ny, nz, k, f0_scale, fnorm, r_out, blockIdx.x, gridDim.x,
+                                partials + 2 * (long long)blockIdx.x);
+}
+
+// `count` instances back to back, bpi blocks per instance: block (b, j) runs
+// the instance's residual with its own omega (and f^0 = -omega_b g_b / tau).
+template <bool EQ, int DIMS>
+__global__ void __launch_bounds__(RES_THREADS, 4)
+k_residual_df4_batched(const float2* __restrict__ y, const double* __restrict__ f, int delta_rhs, int nt, int nx,
+                       int ny, int nz, DfCoef k, const float2* __restrict__ omega_df,
+                       const double* __restrict__ omega64, double inv_tau, int fnorm, int bpi,
+                       float* __restrict__ r_out, double* partials) {
+    pdl_trigger();
+    pdl_wait();
+    const long long b = blockIdx.x / bpi, j = blockIdx.x - b * bpi;
+    const long long per = (long long)nt * nx * ny * nz, Nx = (long long)nx * ny * nz;
+    DfCoef kb = k;
+    const float2 om = omega_df[b];
+    kb.omega = dfloat{om.x, om.y};
+    residual_df4_body<EQ, DIMS>(y + b * per, f + b * (delta_rhs ? Nx : per), delta_rhs, nt, nx, ny, nz, kb,
+                                -omega64[b] * inv_tau, fnorm, r_out + b * per, j, bpi,
+                                partials + 2 * (long long)blockIdx.x);
+}
+
+// sums[2 b], sums[2 b + 1] = the instance's partial pairs summed (one warp each).
+__global__ void k_reduce_instances(const double* partials, int bpi, long long count, double* sums) {
+    pdl_trigger();
+    pdl_wait();
+    const long long w = ((long long)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+    const int lane = threadIdx.x & 31;
+    if (w >= count) return;
+    double a = 0.0, c = 0.0;
+    for (int i = lane; i < bpi; i += 32) {
+        a += partials[2 * (w * bpi + i)];
+        c += partials[2 * (w * bpi + i) + 1];
+    }
+    for (int o = 16; o > 0; o >>= 1) {
+        a += __shfl_down_sync(0xffffffffu, a, o);
+        c += __shfl_down_sync(0xffffffffu, c, o);
+    }
+    if (lane == 0) {
+        sums[2 * w] = a;
+        sums[2 * w + 1] = c;
     }
 }
 
@@ -1545,6 +1704,46 @@ cudaError_t launch_residual_df(const void* y_df, const double* f, int delta_rhs,
     cudaError_t e = cudaGetLastError();
     if (e != cudaSuccess) return e;
     QBVM_PDL(k_reduce_pairs, 1, 1024, 0, s, partials, nblocks, sums);
+    return cudaGetLastError();
+}
+
+int residual_blocks_per_instance(const Tables& tb) {
+    const long long groups = ((long long)tb.nt * tb.Nx + 3) / 4;
+    long long b = (groups + 4 * RES_THREADS - 1) / (4 * RES_THREADS);        // four groups per thread
+    if (b > 1024) b = 1024;
+    return (int)(b < 1 ? 1 : b);
+}
+
+cudaError_t launch_residual_df_batched(const void* y_df, const double* f, int delta_rhs, const Tables& tb,
+                                       const double h2inv[3], long long count, const float2* omega_df,
+                                       const double* omega64, float* r_out, double* partials, double* sums,
+                                       int fnorm, int bpi, cudaStream_t s) {
+    if (((long long)tb.nt * tb.Nx) % 4 != 0 || count * bpi > 0x7fffffffLL) return cudaErrorInvalidValue;
+    if ((reinterpret_cast<uintptr_t>(y_df) | reinterpret_cast<uintptr_t>(r_out) |
+         (delta_rhs ? 0 : reinterpret_cast<uintptr_t>(f))) & 15)
+        return cudaErrorInvalidValue;
+    DfCoef k;
+    const double it = 1.0 / tb.tau;
+    k.ct = df_const(it);
+    k.omega = df_const(tb.omega);
+    k.cx = df_const(h2inv[0]);
+    k.cy = df_const(h2inv[1]);
+    k.cz = df_const(h2inv[2]);
+    const bool eq = (tb.dim < 2 || h2inv[1] == h2inv[0]) && (tb.dim < 3 || h2inv[2] == h2inv[0]);
+    const float2* yy = reinterpret_cast<const float2*>(y_df);
+    const int nx = tb.n[0], ny = tb.n[1], nz = tb.n[2];
+    const unsigned nb = (unsigned)(count * bpi);
+#define QBVM_RDB(E, D)                                                                                        \
+    QBVM_PDL(k_residual_df4_batched<E, D>, nb, RES_THREADS, 0, s, yy, f, delta_rhs, tb.nt, nx, ny, nz, k, omega_df, \
+             omega64, it, fnorm, bpi, r_out, partials)
+    if (tb.dim == 1) QBVM_RDB(true, 1);
+    else if (tb.dim == 2) { if (eq) QBVM_RDB(true, 2); else QBVM_RDB(false, 2); }
+    else { if (eq) QBVM_RDB(true, 3); else QBVM_RDB(false, 3); }
+#undef QBVM_RDB
+    cudaError_t e = cudaGetLastError();
+    if (e != cudaSuccess) return e;
+    const long long thr = count * 32;
+    QBVM_PDL(k_reduce_instances, (unsigned)((thr + 255) / 256), 256, 0, s, partials, bpi, count, sums);
     return cudaGetLastError();
 }
 

@@ -107,12 +107,12 @@ def test_null_arguments(lib):
 
 @pytest.mark.parametrize("case", [
     dict(count=0, code=-1), dict(alphas=[1e-3, -1.0], code=-1), dict(alphas=[float("nan")], code=-1),
-    dict(precision=1, code=-7), dict(nt=24, code=-7), dict(dim=1, m=(4000, 1, 1), code=-7),
+    dict(precision=1, dim=1, m=(4, 1, 1), nt=2, code=-7), dict(nt=24, code=-7), dict(dim=1, m=(4000, 1, 1), code=-7),
     dict(dim=1, m=(64, 1, 1), order=1, code=-7), dict(dim=0, code=-1)],
-    ids=["count0", "alpha-neg", "alpha-nan", "fp32", "nt24", "1d-m4000", "1d-time-first", "dim0"])
+    ids=["count0", "alpha-neg", "alpha-nan", "fp32-nt-nx-not-div4", "nt24", "1d-m4000", "1d-time-first", "dim0"])
 def test_batch_plan_rejects_before_a_gpu(lib, case):
-    """qbvm_batch_plan: same-shape FP64 space-first batches with power-of-two nt;
-    everything else is refused on the host."""
+    """qbvm_batch_plan: same-shape space-first batches with power-of-two nt (FP32
+    refinement: nt * Nx divisible by 4); everything else is refused on the host."""
     import ctypes
     a = dict(dim=2, m=(16, 16, 1), nt=16, precision=0, order=0, count=2, alphas=None)
     a.update(case)
