@@ -66,7 +66,7 @@ extern "C" {
 #define QBVM_FP32_REFINE 1        /* FP32 transforms (tables computed in FP64 and
                                      rounded once), double-float residual and
                                      iterate: iterative refinement.  Needs the
-                                     space-first order and a power-of-two nt. */
+                                     space-first order. */
 
 #define QBVM_RHS_DELTA   0        /* input is g (one level): f^0 = -omega g/tau */
 #define QBVM_RHS_GENERAL 1        /* input is a full right-hand side F [nt][..] */
@@ -83,8 +83,8 @@ extern "C" {
  * L       side length of the domain (0, L)^d; h = L/m[d].
  * T       final time, > 0.
  * nt      time levels N_t: a power of two in [2, 1024] (half-length time
- *         transforms), or any other nt in [3, 2048] with FP64 (Bluestein time
- *         DFTs; the paper's meshes have N_t = N + 1).
+ *         transforms), or any other nt in [3, 2048] (Bluestein time DFTs over
+ *         every frequency, FP64 or FP32; the paper's meshes have N_t = N + 1).
  * form    QBVM_FORM_PQ or QBVM_FORM_PM.
  * alpha   regularisation parameter > 0, or <= 0 for the a-priori rule of
  *         Section 5 from `delta`: alpha = delta (PQ), alpha = tau*delta (PM).

@@ -51,6 +51,8 @@ struct Tables {
     double2* gpw_full = nullptr;     // scale * gamma^t, t < nt
     double2* gip_full = nullptr;     // gamma^{-t}, t < nt
     double2* dk_full = nullptr;      // d_k = 1 - gamma theta^k, k < nt
+    float2 *tw_L32 = nullptr, *chirp32 = nullptr, *bs_fwd32 = nullptr, *bs_inv32 = nullptr;   // FP32 roundings
+    float2 *gpw_full32 = nullptr, *gip_full32 = nullptr, *dk_full32 = nullptr;
 };
 
 // DST-I (unnormalised, S_{jk} = sin(pi j k /(n+1))) along one axis of an
@@ -118,6 +120,10 @@ cudaError_t launch_mul_modes(const double* x, const double* fac, double* y, long
 // 2 = Step (c) (complex in, real out).  N columns, in place not allowed.
 cudaError_t launch_bluestein(int mode, const void* in, void* out, long long N, const Tables& tb, double cnorm,
                              int delta_rhs, int n0_only, cudaStream_t s);
+// The same three modes in FP32 (the FP32 roundings of the tables; in and out
+// FP32 / complex FP32): the FP32 solve of the refinement for nt not a power of two.
+cudaError_t launch_bluestein32(int mode, const void* in, void* out, long long N, const Tables& tb, float cnorm,
+                               int delta_rhs, int n0_only, cudaStream_t s);
 cudaError_t launch_thomas_1d_n(double2* wk, double2* cp, int nsys, const Tables& tb, cudaStream_t s);
 
 // tb.qinv[m][l] = cnorm / (d_{2m} + tau Lambda_l) (IEEE FP64 division), built

@@ -1049,41 +1049,41 @@ cudaError_t launch_time_inv_1d(const double2* wk, double* out, const Tables& tb,
 // f^0 and is written without transforming.
 enum { BS_FWD_DIV = 0, BS_FWD = 1, BS_INV = 2 };
 
-template <int S, int MODE>
+template <typename R, int S, int MODE>
 __global__ void __launch_bounds__(TILE_THREADS)
-k_bluestein(const void* in, void* out, long long N, int P, int lL, int lw, const double2* __restrict__ tw,
-            const double2* __restrict__ chirp, const double2* __restrict__ B, const double2* __restrict__ fac,
-            const double2* __restrict__ dk, const double* __restrict__ lamtau, double cnorm, int delta_rhs,
+k_bluestein(const void* in, void* out, long long N, int P, int lL, int lw, const cplx<R>* __restrict__ tw,
+            const cplx<R>* __restrict__ chirp, const cplx<R>* __restrict__ B, const cplx<R>* __restrict__ fac,
+            const cplx<R>* __restrict__ dk, const R* __restrict__ lamtau, R cnorm, int delta_rhs,
             int n0_only) {
+    using C = cplx<R>;
     extern __shared__ __align__(16) unsigned char smem_raw[];
     const int L = 1 << lL, W = 1 << lw;
-    double2* buf = reinterpret_cast<double2*>(smem_raw);
-    double2* stw = buf + ((size_t)L << lw);
+    C* buf = reinterpret_cast<C*>(smem_raw);
+    C* stw = buf + ((size_t)L << lw);
     const int tid = threadIdx.x, nth = blockDim.x;
     const long long l0 = (long long)blockIdx.x * W;
-    auto csgn = [](double2 c) { return S > 0 ? c : make_double2(c.x, -c.y); };   // c_m of sign S
-    auto epilogue = [&](int k, long long l, double2 v) {
+    auto csgn = [](C c) { return S > 0 ? c : mkc(c.x, -c.y); };   // c_m of sign S
+    auto epilogue = [&](int k, long long l, C v) {
         if (MODE == BS_FWD_DIV) {
-            const double2 a = dk[k];
-            const double zr = a.x + lamtau[l], zi = a.y;
-            const double inv = cnorm / (zr * zr + zi * zi);
-            reinterpret_cast<double2*>(out)[(long long)k * N + l] =
-                make_double2((v.x * zr + v.y * zi) * inv, (v.y * zr - v.x * zi) * inv);
+            const C a = dk[k];
+            const R zr = a.x + lamtau[l], zi = a.y;
+            const R inv = cnorm / (zr * zr + zi * zi);
+            reinterpret_cast<C*>(out)[(long long)k * N + l] = mkc((v.x * zr + v.y * zi) * inv, (v.y * zr - v.x * zi) * inv);
         } else if (MODE == BS_FWD) {
-            reinterpret_cast<double2*>(out)[(long long)k * N + l] = v;
+            reinterpret_cast<C*>(out)[(long long)k * N + l] = v;
         } else {
-            const double2 g = fac[k];
-            reinterpret_cast<double*>(out)[(long long)k * N + l] = g.x * v.x - g.y * v.y;
+            const C g = fac[k];
+            reinterpret_cast<R*>(out)[(long long)k * N + l] = g.x * v.x - g.y * v.y;
         }
     };
     if (MODE != BS_INV && delta_rhs) {
-        const double sc = MODE == BS_FWD ? cnorm : 1.0;
+        const R sc = MODE == BS_FWD ? cnorm : R(1);
         for (int e = tid; e < (P << lw); e += nth) {
             const int k = e >> lw, c = e & (W - 1);
             const long long l = l0 + c;
             if (l < N) {
-                const double f0 = sc * reinterpret_cast<const double*>(in)[l];
-                epilogue(k, l, make_double2(fac[0].x * f0, fac[0].y * f0));
+                const R f0 = sc * reinterpret_cast<const R*>(in)[l];
+                epilogue(k, l, mkc(fac[0].x * f0, fac[0].y * f0));
             }
         }
         return;
@@ -1092,13 +1092,13 @@ k_bluestein(const void* in, void* out, long long N, int P, int lL, int lw, const
     for (int e = tid; e < (L << lw); e += nth) {
         const int t = e >> lw, c = e & (W - 1);
         const long long l = l0 + c;
-        double2 v = make_double2(0.0, 0.0);
+        C v = mkc(R(0), R(0));
         if (t < P && l < N) {
             if (MODE == BS_INV) {
-                v = reinterpret_cast<const double2*>(in)[(long long)t * N + l];
+                v = reinterpret_cast<const C*>(in)[(long long)t * N + l];
             } else {
-                const double f = reinterpret_cast<const double*>(in)[(long long)t * N + l];
-                v = make_double2(fac[t].x * f, fac[t].y * f);
+                const R f = reinterpret_cast<const R*>(in)[(long long)t * N + l];
+                v = mkc(fac[t].x * f, fac[t].y * f);
             }
             v = cmul(v, csgn(chirp[t]));
         }
@@ -1117,32 +1117,49 @@ k_bluestein(const void* in, void* out, long long N, int P, int lL, int lw, const
     }
 }
 
-cudaError_t launch_bluestein(int mode, const void* in, void* out, long long N, const Tables& tb, double cnorm,
-                             int delta_rhs, int n0_only, cudaStream_t s) {
+template <typename R>
+static cudaError_t launch_bluestein_r(int mode, const void* in, void* out, long long N, const Tables& tb, R cnorm,
+                                     int delta_rhs, int n0_only, const cplx<R>* twL, const cplx<R>* chirp,
+                                     const cplx<R>* bsf, const cplx<R>* bsi, const cplx<R>* gpw,
+                                     const cplx<R>* gip, const cplx<R>* dk, const R* lamtau, cudaStream_t s) {
     const int lL = tb.lL, L = 1 << lL;
     int lw = 0;
     while ((L << (lw + 1)) <= TILE_ELEMS) ++lw;
     const long long blocks = (N + (1 << lw) - 1) >> lw;
-    const size_t smem = sizeof(double2) * (((size_t)L << lw) + L);
+    const size_t smem = sizeof(cplx<R>) * (((size_t)L << lw) + L);
     cudaError_t e = cudaSuccess;
     const int P = tb.nt;
     if (mode == BS_FWD_DIV) {
-        auto kern = k_bluestein<+1, BS_FWD_DIV>;
+        auto kern = k_bluestein<R, +1, BS_FWD_DIV>;
         if ((e = set_smem(kern, smem)) != cudaSuccess) return e;
-        kern<<<(unsigned)blocks, TILE_THREADS, smem, s>>>(in, out, N, P, lL, lw, tb.tw_L, tb.chirp, tb.bs_fwd,
-                                                          tb.gpw_full, tb.dk_full, tb.lamtau, cnorm, delta_rhs, 0);
+        kern<<<(unsigned)blocks, TILE_THREADS, smem, s>>>(in, out, N, P, lL, lw, twL, chirp, bsf, gpw, dk, lamtau,
+                                                          cnorm, delta_rhs, 0);
     } else if (mode == BS_FWD) {
-        auto kern = k_bluestein<+1, BS_FWD>;
+        auto kern = k_bluestein<R, +1, BS_FWD>;
         if ((e = set_smem(kern, smem)) != cudaSuccess) return e;
-        kern<<<(unsigned)blocks, TILE_THREADS, smem, s>>>(in, out, N, P, lL, lw, tb.tw_L, tb.chirp, tb.bs_fwd,
-                                                          tb.gpw_full, nullptr, nullptr, cnorm, delta_rhs, 0);
+        kern<<<(unsigned)blocks, TILE_THREADS, smem, s>>>(in, out, N, P, lL, lw, twL, chirp, bsf, gpw, nullptr,
+                                                          nullptr, cnorm, delta_rhs, 0);
     } else {
-        auto kern = k_bluestein<-1, BS_INV>;
+        auto kern = k_bluestein<R, -1, BS_INV>;
         if ((e = set_smem(kern, smem)) != cudaSuccess) return e;
-        kern<<<(unsigned)blocks, TILE_THREADS, smem, s>>>(in, out, N, P, lL, lw, tb.tw_L, tb.chirp, tb.bs_inv,
-                                                          tb.gip_full, nullptr, nullptr, 0.0, 0, n0_only);
+        kern<<<(unsigned)blocks, TILE_THREADS, smem, s>>>(in, out, N, P, lL, lw, twL, chirp, bsi, gip, nullptr,
+                                                          nullptr, R(0), 0, n0_only);
     }
     return cudaGetLastError();
+}
+
+cudaError_t launch_bluestein(int mode, const void* in, void* out, long long N, const Tables& tb, double cnorm,
+                             int delta_rhs, int n0_only, cudaStream_t s) {
+    return launch_bluestein_r<double>(mode, in, out, N, tb, cnorm, delta_rhs, n0_only, tb.tw_L, tb.chirp, tb.bs_fwd,
+                                      tb.bs_inv, tb.gpw_full, tb.gip_full, tb.dk_full, tb.lamtau, s);
+}
+
+cudaError_t launch_bluestein32(int mode, const void* in, void* out, long long N, const Tables& tb, float cnorm,
+                               int delta_rhs, int n0_only, cudaStream_t s) {
+    if (!tb.tw_L32) return cudaErrorInvalidValue;              // built by FP32-refinement plans only
+    return launch_bluestein_r<float>(mode, in, out, N, tb, cnorm, delta_rhs, n0_only, tb.tw_L32, tb.chirp32,
+                                     tb.bs_fwd32, tb.bs_inv32, tb.gpw_full32, tb.gip_full32, tb.dk_full32,
+                                     tb.lamtau32, s);
 }
 
 cudaError_t launch_thomas_1d_n(double2* wk, double2* cp, int nsys, const Tables& tb, cudaStream_t s) {
@@ -1214,6 +1231,50 @@ k_residual(const double* __restrict__ y, const double* __restrict__ f, int delta
             rr = fma(r, r, rr);
             ff = fma(fv, fv, ff);
         }
+    }
+    rr = block_sum(rr, sh);
+    ff = block_sum(ff, sh);
+    if (threadIdx.x == 0) {
+        partials[2 * blockIdx.x] = rr;
+        partials[2 * blockIdx.x + 1] = ff;
+    }
+}
+
+// The refinement residual of 1D plans in FP64 arithmetic: y is the
+// double-float iterate, each value joined exactly into FP64 (the bit-built
+// widenings and one FP64 add, qbvm_join_df_dadd), the stencil as in
+// k_residual, r rounded once to FP32 (r.hi of the correction), norms in FP64.
+// Its error, O(2^-53) of the terms against O(2^-48) for the double-float
+// stencil, sets the floor the refinement stalls at (about kappa(A) times it);
+// 1D plans hold at most 2047 x 2048 unknowns, so the FP64 pipe's cost stays
+// small (tens of microseconds).
+__global__ void __launch_bounds__(RES_THREADS)
+k_residual_1d_dd(const float2* __restrict__ y, const double* __restrict__ f, int delta_rhs, int fnorm, int nt,
+                 int nx, double inv_tau, double omega, double hx2, float* __restrict__ r_out, double* partials) {
+    pdl_trigger();
+    pdl_wait();
+    __shared__ double sh[32];
+    const long long N = (long long)nt * nx;
+    auto ld = [&](long long i) {
+        const float2 v = y[i];
+        return qbvm_join_df_dadd(v.x, v.y);
+    };
+    double rr = 0.0, ff = 0.0;
+    for (long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x; i < N; i += (long long)gridDim.x * blockDim.x) {
+        const int t = (int)(i / nx), ix = (int)(i - (long long)t * nx);
+        const double yv = ld(i);
+        double lap = -2.0 * yv;
+        if (ix > 0) lap += ld(i - 1);
+        if (ix < nx - 1) lap += ld(i + 1);
+        const double prev = t > 0 ? ld(i - nx) : omega * ld((long long)(nt - 1) * nx + ix);
+        const double Ay = (yv - prev) * inv_tau - lap * hx2;
+        double fv;
+        if (delta_rhs) fv = t == 0 ? -omega * inv_tau * f[ix] : 0.0;
+        else fv = f[i];
+        const double r = fv - Ay;
+        r_out[i] = __double2float_rn(r);
+        rr = fma(r, r, rr);
+        if (fnorm) ff = fma(fv, fv, ff);
     }
     rr = block_sum(rr, sh);
     ff = block_sum(ff, sh);
@@ -1672,6 +1733,17 @@ cudaError_t launch_residual_df(const void* y_df, const double* f, int delta_rhs,
     const bool eq = (tb.dim < 2 || h2inv[1] == h2inv[0]) && (tb.dim < 3 || h2inv[2] == h2inv[0]);
     const bool aligned = ((reinterpret_cast<uintptr_t>(y_df) | reinterpret_cast<uintptr_t>(f) |
                            reinterpret_cast<uintptr_t>(r_out)) & 15) == 0;
+    if (tb.dim == 1) {
+        const long long n = (long long)tb.nt * tb.Nx;
+        long long nb = (n + RES_THREADS - 1) / RES_THREADS;
+        if (nb > nblocks) nb = nblocks;
+        QBVM_PDL(k_residual_1d_dd, (unsigned)nb, RES_THREADS, 0, s, reinterpret_cast<const float2*>(y_df), f,
+                 delta_rhs, fnorm, tb.nt, tb.n[0], it, tb.omega, h2inv[0], r_out, partials);
+        cudaError_t e = cudaGetLastError();
+        if (e != cudaSuccess) return e;
+        QBVM_PDL(k_reduce_pairs, 1, 1024, 0, s, partials, (int)nb, sums);
+        return cudaGetLastError();
+    }
     if (aligned) {
         const long long groups = ((long long)tb.nt * tb.Nx + 3) / 4;
         long long nb = (groups + RES_THREADS - 1) / RES_THREADS;

@@ -91,8 +91,8 @@ int validate(const qbvm_desc* d) {
     if (is_pow2(d->nt)) {
         if (d->nt > 1024) return QBVM_ERR_UNSUPPORTED;
     } else {
-        // other lengths: FP64, Bluestein time DFTs of power-of-two length L >= 2 nt - 1 <= 4096
-        if (d->precision != QBVM_FP64 || d->nt > 2048) return QBVM_ERR_UNSUPPORTED;
+        // other lengths: Bluestein time DFTs of power-of-two length L >= 2 nt - 1 <= 4096
+        if (d->nt > 2048) return QBVM_ERR_UNSUPPORTED;
     }
     if (d->order < QBVM_ORDER_AUTO || d->order > QBVM_ORDER_SPACE_FIRST) return QBVM_ERR_BAD_ARG;
     if (d->order == QBVM_ORDER_TIME_FIRST && d->dim != 1) return QBVM_ERR_BAD_ARG;
@@ -203,6 +203,20 @@ int bluestein_tables(qbvm_plan_t* p, double mag, double scale1d) {
     if (!rc) rc = upload(p, &tb.gpw_full, gp);
     if (!rc) rc = upload(p, &tb.gip_full, gi);
     if (!rc) rc = upload(p, &tb.dk_full, dk);
+    if (!rc && p->d.precision == QBVM_FP32_REFINE) {
+        auto to32 = [](const std::vector<double2>& v) {
+            std::vector<float2> o(v.size());
+            for (size_t i = 0; i < v.size(); ++i) o[i] = make_float2((float)v[i].x, (float)v[i].y);
+            return o;
+        };
+        rc = upload(p, &tb.tw_L32, tw32);
+        if (!rc) rc = upload(p, &tb.chirp32, to32(chirp));
+        if (!rc) rc = upload(p, &tb.bs_fwd32, to32(bf));
+        if (!rc) rc = upload(p, &tb.bs_inv32, to32(bi));
+        if (!rc) rc = upload(p, &tb.gpw_full32, to32(gp));
+        if (!rc) rc = upload(p, &tb.gip_full32, to32(gi));
+        if (!rc) rc = upload(p, &tb.dk_full32, to32(dk));
+    }
     return rc;
 }
 
@@ -390,13 +404,26 @@ int fp32_solve(qbvm_plan_t* p, const void* rhs, int rhs_fp64, int delta, void* y
         { Span sp_(p, "dst_x", s); CK(qbvm::launch_dst<float, double, 0>((const double*)rhs, p->g32, tb.n[0], p->lp[0], ny * nz, 1, tb.tw_s32[0], tb.sn_s32[0], s)); }
         if (tb.dim >= 2) { Span sp_(p, "dst_y", s); CK(qbvm::launch_dst<float, float, 0>(p->g32, p->g32, tb.n[1], p->lp[1], nz, nx, tb.tw_s32[1], tb.sn_s32[1], s)); }
         if (tb.dim == 3) { Span sp_(p, "dst_z", s); CK(qbvm::launch_dst<float, float, 0>(p->g32, p->g32, tb.n[2], p->lp[2], 1, nx * ny, tb.tw_s32[2], tb.sn_s32[2], s)); }
-        { Span sp_(p, "time_solve", s); CK(qbvm::launch_time_solve<float>(p->g32, w, tb, -tb.omega * cn, 1, 0, s)); }
+        if (tb.gen) {
+            // nt not a power of two: Bluestein time DFTs (every frequency) in FP32
+            { Span sp_(p, "time_fwd", s); CK(qbvm::launch_bluestein32(0, p->g32, p->wk, tb.Nx, tb, (float)(-tb.omega * cn), 1, 0, s)); }
+            { Span sp_(p, "time_inv", s); CK(qbvm::launch_bluestein32(2, p->wk, w, tb.Nx, tb, 0.f, 0, 0, s)); }
+        } else {
+            Span sp_(p, "time_solve", s);
+            CK(qbvm::launch_time_solve<float>(p->g32, w, tb, -tb.omega * cn, 1, 0, s));
+        }
     } else {
         if (rhs_fp64) { Span sp_(p, "dst_x", s); CK(qbvm::launch_dst<float, double, 0>((const double*)rhs, w, tb.n[0], p->lp[0], nt * ny * nz, 1, tb.tw_s32[0], tb.sn_s32[0], s)); }
         else { Span sp_(p, "dst_x", s); CK(qbvm::launch_dst<float, float, 0>((const float*)rhs, w, tb.n[0], p->lp[0], nt * ny * nz, 1, tb.tw_s32[0], tb.sn_s32[0], s)); }
         if (tb.dim >= 2) { Span sp_(p, "dst_y", s); CK(qbvm::launch_dst<float, float, 0>(w, w, tb.n[1], p->lp[1], nt * nz, nx, tb.tw_s32[1], tb.sn_s32[1], s)); }
         if (tb.dim == 3) { Span sp_(p, "dst_z", s); CK(qbvm::launch_dst<float, float, 0>(w, w, tb.n[2], p->lp[2], nt, nx * ny, tb.tw_s32[2], tb.sn_s32[2], s)); }
-        { Span sp_(p, "time_solve", s); CK(qbvm::launch_time_solve<float>(w, w, tb, tb.tau * cn, 0, 0, s)); }
+        if (tb.gen) {
+            { Span sp_(p, "time_fwd", s); CK(qbvm::launch_bluestein32(0, w, p->wk, tb.Nx, tb, (float)(tb.tau * cn), 0, 0, s)); }
+            { Span sp_(p, "time_inv", s); CK(qbvm::launch_bluestein32(2, p->wk, w, tb.Nx, tb, 0.f, 0, 0, s)); }
+        } else {
+            Span sp_(p, "time_solve", s);
+            CK(qbvm::launch_time_solve<float>(w, w, tb, tb.tau * cn, 0, 0, s));
+        }
     }
     if (tb.dim == 3) { Span sp_(p, "dst_z", s); CK(qbvm::launch_dst<float, float, 0>(w, w, tb.n[2], p->lp[2], nt, nx * ny, tb.tw_s32[2], tb.sn_s32[2], s)); }
     if (tb.dim >= 2) { Span sp_(p, "dst_y", s); CK(qbvm::launch_dst<float, float, 0>(w, w, tb.n[1], p->lp[1], nt * nz, nx, tb.tw_s32[1], tb.sn_s32[1], s)); }
@@ -440,7 +467,7 @@ int solve_fp32r_dev(qbvm_plan_t* p, const double* in, double* y, int n0_only, cu
     const int maxit = p->d.refine_max_iters > 0 ? p->d.refine_max_iters : 10;
     int rc = fp32_solve(p, in, 1, delta, yfull, 0, s);
     if (rc) return rc;
-    const int launches_solve = 2 * tb.dim + 1;
+    const int launches_solve = 2 * tb.dim + (tb.gen ? 2 : 1);
     int launches = launches_solve;
     double rel = 0.0, prev = INFINITY;
     int it = 0;

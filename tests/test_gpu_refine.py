@@ -264,3 +264,27 @@ def test_zero_input_gives_zero():
     grid = bi.Grid(2, (64, 64), 1.0, 0.1, 64)
     got, _, rel = refine_solve(grid, Q.FORM_PQ, 1e-3, np.zeros(grid.shape), Q.RHS_DELTA)
     assert not got.any() and rel == 0.0
+
+
+# nt not a power of two: FP32 Bluestein time DFTs inside the refinement
+GENERAL_NT = [
+    bi.Grid(2, (16, 16), 3.141592653589793, 1.0, 17),     # Table 2 mesh (16^2, 16)
+    bi.Grid(2, (32, 24), 1.0, 0.1, 100),
+    bi.Grid(3, (8, 8, 8), 1.0, 0.05, 9),
+    bi.Grid(1, (256,), 3.141592653589793, 1.0, 257),      # Table 1 mesh (256, 256)
+    bi.Grid(2, (8, 8), 1.0, 0.1, 2047),                   # longest Bluestein length
+]
+
+
+@pytest.mark.parametrize("grid", GENERAL_NT, ids=lambda g: f"d{g.dim}-M{'x'.join(map(str, g.M))}-nt{g.nt}")
+@pytest.mark.parametrize("form", [Q.FORM_PQ, Q.FORM_PM])
+@pytest.mark.parametrize("rhs_kind", [Q.RHS_DELTA, Q.RHS_GENERAL])
+def test_refined_general_nt_matches_oracle(grid, form, rhs_kind):
+    alpha = 1e-3 if form == Q.FORM_PQ else 1e-3 * grid.tau
+    F = bi.random_general_rhs(grid, seed=51)
+    rhs = F[0] if rhs_kind == Q.RHS_DELTA else F
+    Ff = O.delta_rhs(grid, form, alpha, F[0]) if rhs_kind == Q.RHS_DELTA else F
+    want = O.solve_spectral(grid, form, alpha, Ff)
+    got, iters, rel = refine_solve(grid, form, alpha, rhs, rhs_kind)
+    assert rel <= 1e-10 and iters >= 1
+    assert O.rel_l2(got, want) <= TOL
