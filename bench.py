@@ -547,6 +547,8 @@ def our_arm(args, rank, world, device):
     if not args.no_extra and not args.refine_only:
         extra["c3_3d"] = c3_leg(args, device, stream, flush, rank == 0 and world == 1 and not args.no_cpu_baseline)
         extra["c4_sweep"] = c4_leg(args, device, stream)
+        extra["c4_full_multi"] = c4_full_leg(args, device, stream,
+                                             with_oracle=rank == 0 and world == 1 and not args.no_cpu_baseline)
         extra["c1_batched"] = c1_batched_leg(args, device, stream, flush,
                                              with_oracle=rank == 0 and world == 1 and not args.no_cpu_baseline)
         extra["batched_2d"] = batched_2d_leg(args, device, stream, flush,
@@ -681,6 +683,81 @@ def c4_leg(args, device, stream):
                          "config": {"modes_per_thread": cfg.modes_per_thread, "ctas_per_sm": cfg.ctas_per_sm,
                                     "grid": cfg.grid},
                          "graph_launches_per_run": 1, "kernel_launches_per_run": 1}
+    return out
+
+
+def c4_full_leg(args, device, stream, with_oracle=True):
+    """Full solves (every level, FP64) of the 512 uneven instances of the sweep
+    workload (1D n in {63..2047}, 2D {63,127,255}^2, nt in {32..512}), alpha =
+    each instance's noise level: one persistent launch from a captured CUDA
+    graph (qbvm_multi_run) against the same instances as 512 single-plan
+    solves one after another; sampled small instances against the oracle."""
+    import numpy as np
+    import torch
+    import bhcp_inputs as bi
+    import paper_2107_06381_gb300 as Q
+    specs = bi.batch_specs_c4()
+    insts, plans, meta = [], [], []
+    for s_ in specs:
+        grid = bi.Grid(s_["dim"], tuple(s_["M"]), 1.0, 0.1, s_["nt"])
+        rng = np.random.default_rng(s_["seed"])
+        modes = [(1,), (2,), (3,)] if grid.dim == 1 else [(1, 1), (2, 1), (1, 2)]
+        z0 = bi.sine_field(grid, modes, rng.uniform(0.3, 1.0, 3))
+        gd, delta = bi.add_noise_gaussian(grid, bi.forward_discrete(grid, z0), s_["rel_noise"], rng)
+        g = torch.as_tensor(gd.ravel(), dtype=torch.float64, device=device)
+        y = torch.empty(grid.unknowns, dtype=torch.float64, device=device)
+        insts.append(dict(dim=grid.dim, m=grid.M, L=1.0, T=0.1, nt=grid.nt, form=Q.FORM_PQ, alpha=delta,
+                          rhs_kind=Q.RHS_DELTA, g_or_F=g, y=y))
+        plans.append((Q.Plan(grid.dim, grid.M, 1.0, 0.1, grid.nt, Q.FORM_PQ, delta, 0.0, Q.FP64, Q.RHS_DELTA), g, y))
+        meta.append((grid, delta, gd))
+    unknowns = sum(g.unknowns for g, _, _ in meta)
+    out = {"workload": "c4_full_solves_512_uneven", "instances": len(specs), "unknowns_per_run": unknowns,
+           "output": "every level of every instance (FP64)"}
+    steps = max(3, args.steps // 5)
+    with Q.Multi(insts) as mp:
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        with torch.cuda.stream(stream):
+            mp.run(stream)
+            e0.record(stream)
+            for _ in range(steps):
+                mp.run(stream)
+            e1.record(stream)
+        torch.cuda.synchronize()
+        mp.check(stream)
+        ms = e0.elapsed_time(e1) / steps
+        info = mp.info
+        ys = [y.clone() for _, _, y in plans] if with_oracle else None
+        with torch.cuda.stream(stream):
+            for pl, g, y in plans:
+                pl.solve(g, y, stream=stream)
+            e0.record(stream)
+            for _ in range(steps):
+                for pl, g, y in plans:
+                    pl.solve(g, y, stream=stream)
+            e1.record(stream)
+        torch.cuda.synchronize()
+        ms_single = e0.elapsed_time(e1) / steps
+        out.update({"ms_per_run": ms, "value": unknowns / (ms / 1e3), "unit": UNIT,
+                    "solves_per_s": len(specs) / (ms / 1e3), "kernel_launches_per_run": 1,
+                    "graph_launches_per_run": 1, "work_items": info["work_items"], "grid": info["grid"],
+                    "single_plans_ms_per_run": ms_single,
+                    "single_plans_kernel_launches_per_run": sum(p.info.kernels_per_solve for p, _, _ in plans)})
+        if with_oracle:
+            import oracle as O
+            small = sorted(range(len(specs)), key=lambda i: meta[i][0].unknowns)[:4]
+            errs, diffs = [], []
+            for i in small:
+                grid, delta, gd = meta[i]
+                want = O.solve_spectral(grid, O.PQ, delta, O.delta_rhs(grid, O.PQ, delta, gd))
+                errs.append(O.rel_l2(ys[i].cpu().numpy(), want))
+            for i in range(0, len(specs), 64):
+                a, b = ys[i], plans[i][2]
+                diffs.append(float((a - b).norm() / b.norm()))
+            out["rel_err_vs_oracle"] = max(errs)
+            out["rel_err_sample"] = "the four smallest instances"
+            out["rel_diff_vs_single_plans"] = max(diffs)
+    for pl, _, _ in plans:
+        pl.close()
     return out
 
 

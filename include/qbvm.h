@@ -297,6 +297,38 @@ int qbvm_batch_refine_info(const qbvm_batch_t* batch, int* iters, double* max_re
 int qbvm_batch_destroy(qbvm_batch_t* batch);
 
 /* ------------------------------------------------------------------------
+ * Uneven batch of full solves: `count` instances of DIFFERENT shapes (dim,
+ * m, nt), each with its own form, alpha, right-hand-side kind and arrays,
+ * solved for every time level in ONE persistent kernel launch replayed from
+ * a CUDA graph captured on the first run.  Each instance is planned as an
+ * ordinary FP64 space-first plan (its tables of Section 3.3); the kernel then
+ * runs the three steps of eq. 3.8 of every instance -- forward DST-I along
+ * each axis, the time solve per tile of spatial modes (Steps (a)-(c)), the
+ * inverse DST-I -- as one queue of tiles in which a stage of an instance
+ * waits (bounded) for all tiles of the instance's previous stage.  Results
+ * equal the single plans' (the same tiles).
+ * Supported: FP64, space-first, nt a power of two in [2, 1024], every m a
+ * power of two in [4, 2048].  g_or_F ([Nx] for the delta right-hand side,
+ * else [nt][Nx]) and y ([nt][Nx]) are caller-owned DEVICE arrays of the
+ * current device that must stay valid while the plan is used.
+ * qbvm_multi_run enqueues one solve of every instance on `stream`
+ * (asynchronous); qbvm_multi_check synchronises `stream` and returns
+ * QBVM_ERR_TIMEOUT if a bounded wait inside the kernel gave up (then no
+ * result is valid).  Errors: BAD_ARG, UNSUPPORTED, OOM, CUDA. */
+typedef struct qbvm_multi_instance {
+    qbvm_desc desc;              /* shape, form, alpha (or delta), rhs_kind; precision QBVM_FP64 */
+    const double* g_or_F;        /* device input */
+    double* y;                   /* device output [nt][Nx] */
+} qbvm_multi_instance;
+typedef struct qbvm_multi qbvm_multi_t;
+int qbvm_multi_plan(const qbvm_multi_instance* inst, int count, qbvm_multi_t** out);
+int qbvm_multi_run(qbvm_multi_t* multi, void* stream);
+int qbvm_multi_check(qbvm_multi_t* multi, void* stream);
+/* total unknowns (sum of nt * Nx), queue length and persistent grid; NULL outputs allowed */
+int qbvm_multi_info(const qbvm_multi_t* multi, long long* unknowns, int* work_items, int* grid);
+int qbvm_multi_destroy(qbvm_multi_t* multi);
+
+/* ------------------------------------------------------------------------
  * Batched regularisation-parameter sweep.  Many PinT-QBVM / PinT-MQBVM
  * instances of uneven size (1D or 2D, delta right-hand side f^0 = -omega g/tau),
  * each solved for n_alpha values of alpha log-spaced around the a-priori rule

@@ -19,7 +19,7 @@ __all__ = [
     "qbvm_profile_enable", "qbvm_profile_read", "qbvm_residual_noalloc", "qbvm_measure_peak",
     "qbvm_strerror", "qbvm_version", "Plan", "Sweep", "QbvmSweepInstance", "QbvmSweepDesc", "QbvmSweepConfig",
     "qbvm_sweep_plan", "qbvm_sweep_run", "qbvm_sweep_read", "qbvm_sweep_autotune", "qbvm_sweep_set_config",
-    "qbvm_sweep_get_config", "qbvm_sweep_destroy", "MLP", "Features", "Batch", "GMRES",
+    "qbvm_sweep_get_config", "qbvm_sweep_destroy", "MLP", "Features", "Batch", "GMRES", "Multi",
     "FORM_PQ", "FORM_PM", "FP64", "FP32_REFINE", "RHS_DELTA", "RHS_GENERAL",
 ]
 
@@ -73,6 +73,10 @@ class QbvmSweepDesc(ctypes.Structure):
 class QbvmSweepConfig(ctypes.Structure):
     _fields_ = [("modes_per_thread", ctypes.c_int), ("ctas_per_sm", ctypes.c_int), ("grid", ctypes.c_int),
                 ("ms", ctypes.c_float)]
+
+
+class QbvmMultiInstance(ctypes.Structure):
+    _fields_ = [("desc", QbvmDesc), ("g_or_F", ctypes.c_void_p), ("y", ctypes.c_void_p)]
 
 
 class QbvmError(RuntimeError):
@@ -171,6 +175,16 @@ def load_library(path: str | None = None) -> ctypes.CDLL:
     lib.qbvm_features_run.restype = ip
     lib.qbvm_features_destroy.argtypes = [vp]
     lib.qbvm_features_destroy.restype = ip
+    lib.qbvm_multi_plan.argtypes = [ctypes.POINTER(QbvmMultiInstance), ip, ctypes.POINTER(vp)]
+    lib.qbvm_multi_plan.restype = ip
+    lib.qbvm_multi_run.argtypes = [vp, vp]
+    lib.qbvm_multi_run.restype = ip
+    lib.qbvm_multi_check.argtypes = [vp, vp]
+    lib.qbvm_multi_check.restype = ip
+    lib.qbvm_multi_info.argtypes = [vp, ctypes.POINTER(ctypes.c_longlong), ctypes.POINTER(ip), ctypes.POINTER(ip)]
+    lib.qbvm_multi_info.restype = ip
+    lib.qbvm_multi_destroy.argtypes = [vp]
+    lib.qbvm_multi_destroy.restype = ip
     lib.qbvm_measure_peak.argtypes = [ip, ctypes.POINTER(dp), vp]
     lib.qbvm_measure_peak.restype = ip
     lib.qbvm_version.argtypes = []
@@ -628,6 +642,53 @@ class Batch:
     def close(self):
         if self.handle:
             load_library().qbvm_batch_destroy(self.handle)
+            self.handle = None
+
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *exc):
+        self.close()
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+
+class Multi:
+    """Full solves of uneven instances in one persistent launch (qbvm_multi_*).
+    `instances`: dicts with dim, m, L, T, nt, form, alpha (or delta), rhs_kind
+    and the device arrays g_or_F, y (float64 tensors or addresses)."""
+
+    def __init__(self, instances):
+        self._keep = instances
+        arr = (QbvmMultiInstance * len(instances))()
+        for i, d in enumerate(instances):
+            desc = make_desc(d["dim"], d["m"], d.get("L", 1.0), d["T"], d["nt"], d.get("form", FORM_PQ),
+                             d.get("alpha", 0.0), d.get("delta", 0.0), FP64, d.get("rhs_kind", RHS_DELTA))
+            arr[i] = QbvmMultiInstance(desc, _ptr(d["g_or_F"]), _ptr(d["y"]))
+        h = ctypes.c_void_p()
+        _check(load_library().qbvm_multi_plan(arr, len(instances), ctypes.byref(h)), "qbvm_multi_plan")
+        self.handle = h.value
+
+    def run(self, stream=None):
+        _check(load_library().qbvm_multi_run(self.handle, _stream(stream)), "qbvm_multi_run")
+
+    def check(self, stream=None):
+        _check(load_library().qbvm_multi_check(self.handle, _stream(stream)), "qbvm_multi_check")
+
+    @property
+    def info(self):
+        u, n, g = ctypes.c_longlong(), ctypes.c_int(), ctypes.c_int()
+        _check(load_library().qbvm_multi_info(self.handle, ctypes.byref(u), ctypes.byref(n), ctypes.byref(g)),
+               "qbvm_multi_info")
+        return {"unknowns": u.value, "work_items": n.value, "grid": g.value}
+
+    def close(self):
+        if self.handle:
+            load_library().qbvm_multi_destroy(self.handle)
             self.handle = None
 
     def __enter__(self):

@@ -184,6 +184,7 @@ struct PlanView {
     int form, precision, rhs_kind, dim;
     int dev;                       // the device the plan was made on (its tables live there)
     double alpha, tau, h2inv[3];
+    double* ghat;                  // FP64 space-first plans: one level of workspace (the DST of g)
 };
 int plan_view(const struct ::qbvm_plan* p, PlanView* out);
 

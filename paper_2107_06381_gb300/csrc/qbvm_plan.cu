@@ -553,6 +553,7 @@ int qbvm::plan_view(const struct ::qbvm_plan* p, PlanView* out) {
     out->rhs_kind = p->d.rhs_kind;
     out->dim = p->d.dim;
     out->dev = p->dev;
+    out->ghat = p->ghat;
     out->alpha = p->alpha;
     out->tau = p->tau;
     for (int i = 0; i < 3; ++i) out->h2inv[i] = p->h2inv[i];
