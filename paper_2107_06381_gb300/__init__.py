@@ -132,6 +132,8 @@ def load_library(path: str | None = None) -> ctypes.CDLL:
     lib.qbvm_batch_refine_info.restype = ip
     lib.qbvm_batch_destroy.argtypes = [vp]
     lib.qbvm_batch_destroy.restype = ip
+    lib.qbvm_selftest_newton_rcp.argtypes = [vp, ctypes.c_longlong, ctypes.POINTER(dp), vp]
+    lib.qbvm_selftest_newton_rcp.restype = ip
     lib.qbvm_selftest_bounded_wait.argtypes = [ip, ctypes.POINTER(dp), vp]
     lib.qbvm_selftest_bounded_wait.restype = ip
     lib.qbvm_sweep_plan.argtypes = [ctypes.POINTER(QbvmSweepDesc), ctypes.POINTER(vp)]

@@ -113,6 +113,44 @@ __device__ double block_sum_d(double v, double* sh) {
     return v;
 }
 
+// 1/d for a positive normal FP64 d, from an FP32 seed and two FP64 Newton
+// steps (Newton-Raphson on f(x) = 1/x - d: x <- x + x (1 - d x), each step
+// squaring the relative error).  The seed is the approximate FP32 reciprocal
+// of d truncated to FP32 -- the exponent rebased and the top 23 significand
+// bits kept, on the integer pipes -- widened back to FP64 exactly from its
+// bits: relative error below 2^-21, so two steps leave the rounding of the
+// last fused multiply-add (a few units in the last place).  Four FP64
+// operations instead of a division; d outside FP32's normal range (never
+// for the scan's |d_{2m} + tau Lambda|^2) takes the division.
+__device__ __forceinline__ double rcp_newton(double d) {
+    const unsigned int H = (unsigned int)__double2hiint(d);
+    const int fe = (int)((H >> 20) & 0x7FFu) - 1023 + 127;
+    if (fe < 2 || fe > 252 || (H >> 31)) return 1.0 / d;
+    const float f = __uint_as_float(((unsigned int)fe << 23) | ((H & 0xFFFFFu) << 3) |
+                                    ((unsigned int)__double2loint(d) >> 29));
+    float r;
+    asm("rcp.approx.ftz.f32 %0, %1;" : "=f"(r) : "f"(f));
+    const unsigned int rb = __float_as_uint(r);
+    double x = __hiloint2double((int)((((rb >> 23) & 0xFFu) + 896u) << 20 | ((rb & 0x7FFFFFu) >> 3)), (int)(rb << 29));
+    double e = fma(-d, x, 1.0);
+    x = fma(x, e, x);
+    e = fma(-d, x, 1.0);
+    return fma(x, e, x);
+}
+
+// Diagnostic: the largest relative difference of rcp_newton from the IEEE
+// quotient 1/d over n values (one FP64 atomic max through its bits: the
+// values are positive).
+__global__ void k_rcp_check(const double* d, long long n, unsigned long long* maxbits) {
+    double worst = 0.0;
+    for (long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (long long)gridDim.x * blockDim.x) {
+        const double q = __drcp_rn(d[i]);
+        const double a = rcp_newton(d[i]);
+        worst = fmax(worst, fabs(a - q) / fabs(q));
+    }
+    atomicMax(maxbits, (unsigned long long)__double_as_longlong(worst));
+}
+
 // Stage B: one tile of SW_THREADS * MPT modes, every alpha, precision R.
 template <typename R, int MPT>
 __device__ void spectral_tile(const SwInst& I, int tile, unsigned char* smem) {
@@ -150,8 +188,8 @@ __device__ void spectral_tile(const SwInst& I, int tile, unsigned char* smem) {
                 R zr = d.x + lam[q];
                 if (std::is_same<R, float>::value)      // the FP32 scan: the 2-ulp fast division
                     s[q] += __fdividef((float)zr, fmaf((float)zr, (float)zr, (float)(d.y * d.y)));
-                else
-                    s[q] += zr / (zr * zr + d.y * d.y);
+                else                                    // FP64: Newton reciprocal (4 FP64 operations)
+                    s[q] = fma((double)zr, rcp_newton(fma((double)zr, (double)zr, (double)(d.y * d.y))), (double)s[q]);
             }
         }
         const R cna = R(I.cn[a]);
@@ -224,7 +262,7 @@ __device__ void final_tile(const SwInst& I, int tile) {
         for (int m = 0; m < I.H; ++m) {
             double2 d = dt[m];
             double zr = d.x + lt;
-            s += zr / fma(zr, zr, d.y * d.y);
+            s = fma(zr, rcp_newton(fma(zr, zr, d.y * d.y)), s);
         }
     } else {
         const float4* dt = I.dtabdf + (long long)a * I.H;
@@ -844,6 +882,37 @@ int qbvm_sweep_get_config(const qbvm_sweep_t* p, qbvm_sweep_config* cfg) {
 
 int qbvm_sweep_destroy(qbvm_sweep_t* p) {
     sw_destroy(p);
+    return QBVM_OK;
+}
+
+int qbvm_selftest_newton_rcp(const double* d, long long n, double* max_rel_diff, void* stream) {
+    if (!d || n < 1 || !max_rel_diff) return QBVM_ERR_BAD_ARG;
+    cudaStream_t s = static_cast<cudaStream_t>(stream);
+    unsigned long long* buf = nullptr;
+    if (cudaMalloc(&buf, sizeof(unsigned long long)) != cudaSuccess) {
+        cudaGetLastError();
+        return QBVM_ERR_OOM;
+    }
+    unsigned long long h = 0;
+    int rc = QBVM_OK;
+    if (cudaMemsetAsync(buf, 0, sizeof(h), s) != cudaSuccess) rc = QBVM_ERR_CUDA;
+    if (!rc) {
+        long long blocks = (n + 255) / 256;
+        if (blocks > 152 * 16) blocks = 152 * 16;
+        k_rcp_check<<<(unsigned)blocks, 256, 0, s>>>(d, n, buf);
+        if (cudaGetLastError() != cudaSuccess ||
+            cudaMemcpyAsync(&h, buf, sizeof(h), cudaMemcpyDeviceToHost, s) != cudaSuccess ||
+            cudaStreamSynchronize(s) != cudaSuccess)
+            rc = QBVM_ERR_CUDA;
+    }
+    cudaFree(buf);
+    if (rc) {
+        cudaGetLastError();
+        return rc;
+    }
+    double v;
+    std::memcpy(&v, &h, sizeof(v));
+    *max_rel_diff = v;
     return QBVM_OK;
 }
 

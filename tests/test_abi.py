@@ -173,3 +173,24 @@ def test_every_status_code_has_its_own_message(lib):
     assert codes == set(range(-7, 0))
     msgs = [Q.qbvm_strerror(c) for c in sorted(codes)]
     assert len(set(msgs)) == len(msgs) and "unknown status code" not in msgs
+
+
+@pytest.mark.parametrize("change,code", [
+    (dict(precision=1), -7), (dict(nt=24), -7), (dict(m=(24, 16, 1)), -7), (dict(m=(4096, 16, 1)), -7),
+    (dict(order=1, dim=1, m=(64, 1, 1)), -7), (dict(dim=0), -1), (dict(null=True), -1), (dict(count=0), -1)],
+    ids=["fp32", "nt24", "m24", "m4096", "time-first", "dim0", "null-array", "count0"])
+def test_multi_plan_rejects_before_a_gpu(lib, change, code):
+    """qbvm_multi_plan: FP64 space-first instances with power-of-two nt and m;
+    everything else is refused on the host."""
+    import ctypes
+    a = dict(dim=2, m=(16, 16, 1), nt=16, precision=0, order=0, count=2, null=False)
+    a.update(change)
+    desc = Q.make_desc(a["dim"], a["m"], 1.0, 0.1, a["nt"], 0, 1e-3, 0.0, a["precision"], 1, order=a["order"])
+    buf = (ctypes.c_double * 8)()
+    arr = (Q.QbvmMultiInstance * 2)()
+    for i in range(2):
+        arr[i] = Q.QbvmMultiInstance(desc, None if a["null"] else ctypes.addressof(buf),
+                                     None if a["null"] else ctypes.addressof(buf))
+    h = ctypes.c_void_p()
+    assert lib.qbvm_multi_plan(arr, a["count"], ctypes.byref(h)) == code
+    assert not h.value

@@ -189,3 +189,19 @@ def test_sweep_is_scale_invariant(precision):
                 np.testing.assert_allclose(u / scale, v, rtol=0, atol=1e-10 * np.abs(v).max())
         finally:
             sw2.close()
+
+
+def test_newton_reciprocal_against_ieee_division():
+    """The FP64 scan's reciprocal (FP32 seed, two FP64 Newton steps) against the
+    correctly rounded 1/d over magnitudes the scan meets and far beyond:
+    within 4 ulp (2^-50 relative) of the IEEE quotient."""
+    import ctypes
+    rng = np.random.default_rng(61)
+    d = np.concatenate([10.0 ** rng.uniform(-30, 30, 200_000), 1.0 + rng.uniform(0, 1e-9, 1000),
+                        [1.0, 2.0, 0.5, 3.0, 1e-300, 1e300, 7.0 / 3.0]])
+    dd = torch.as_tensor(d, dtype=torch.float64).cuda()
+    out = ctypes.c_double(-1.0)
+    rc = Q.load_library().qbvm_selftest_newton_rcp(dd.data_ptr(), dd.numel(), ctypes.byref(out),
+                                                   torch.cuda.current_stream().cuda_stream)
+    assert rc == 0
+    assert 0.0 <= out.value <= 2.0 ** -50, out.value
