@@ -53,25 +53,6 @@ __global__ void k_spectrum_bins(const float* __restrict__ ghat, long long Nx, co
 // ------------------------------------------------------------------ MLP
 __device__ __forceinline__ float bf(const __nv_bfloat16* w, long long i) { return __bfloat162float(w[i]); }
 
-// Z = A W^T + b (A: B x K, W: N x K bf16), H = relu(Z); optional input standardisation.
-__global__ void k_dense_relu(const float* __restrict__ A, const __nv_bfloat16* __restrict__ W, const float* __restrict__ bias,
-                             int B, int K, int N, const float* __restrict__ mu, const float* __restrict__ inv_sd,
-                             float* __restrict__ Z, float* __restrict__ H) {
-    long long idx = (long long)blockIdx.x * blockDim.x + threadIdx.x;
-    if (idx >= (long long)B * N) return;
-    int b = (int)(idx / N), n = (int)(idx - (long long)b * N);
-    const float* a = A + (long long)b * K;
-    const __nv_bfloat16* w = W + (long long)n * K;
-    float s = bias[n];
-    if (mu) {
-        for (int k = 0; k < K; ++k) s = fmaf((a[k] - mu[k]) * inv_sd[k], bf(w, k), s);
-    } else {
-        for (int k = 0; k < K; ++k) s = fmaf(a[k], bf(w, k), s);
-    }
-    Z[idx] = s;
-    H[idx] = fmaxf(s, 0.f);
-}
-
 // y = H w3 + b3 (one warp per row).
 __global__ void k_dense_out(const float* __restrict__ H, const __nv_bfloat16* __restrict__ w3, const float* __restrict__ b3,
                             int B, int N, float* __restrict__ y) {
@@ -107,22 +88,6 @@ __global__ void k_back_out(const float* __restrict__ dy, const __nv_bfloat16* __
     dZ2[idx] = Z2[idx] > 0.f ? dy[b] * bf(w3, n) : 0.f;
 }
 
-// dZ1 = (dZ2 W2) masked by Z1 > 0 (W2: N x K).
-__global__ void k_back_hidden(const float* __restrict__ dZ2, const __nv_bfloat16* __restrict__ W2, const float* __restrict__ Z1,
-                              int B, int N, int K, float* __restrict__ dZ1) {
-    long long idx = (long long)blockIdx.x * blockDim.x + threadIdx.x;
-    if (idx >= (long long)B * K) return;
-    int b = (int)(idx / K), k = (int)(idx - (long long)b * K);
-    if (!(Z1[idx] > 0.f)) {
-        dZ1[idx] = 0.f;
-        return;
-    }
-    const float* d = dZ2 + (long long)b * N;
-    float s = 0.f;
-    for (int n = 0; n < N; ++n) s = fmaf(d[n], bf(W2, (long long)n * K + k), s);
-    dZ1[idx] = s;
-}
-
 // dW[n][k] = sum_b D[b][n] A'[b][k] (A' standardised input when mu != null), db[n] = sum_b D[b][n].
 __global__ void k_wgrad(const float* __restrict__ D, const float* __restrict__ A, int B, int N, int K,
                         const float* __restrict__ mu, const float* __restrict__ inv_sd, float* __restrict__ dW,
@@ -140,6 +105,145 @@ __global__ void k_wgrad(const float* __restrict__ D, const float* __restrict__ A
         for (int b = 0; b < B; ++b) s = fmaf(D[(long long)b * N + n], (A[(long long)b * K + k] - m) * is, s);
         dW[(long long)n * K + k] = s;
     }
+}
+
+// ---------------------------------------------- tensor-core products (BF16)
+//
+// C[m][n] = sum_k A(m, k) B(k, n) on the tensor cores: mma.sync m16n8k16 with
+// BF16 operands and FP32 accumulation.  A is FP32 in memory (activations or
+// gradients; optionally standardised on load, (a - mu[k]) * is[k], and so may
+// be the FP32 B operand, (b - mub[n]) * isb[n]) and enters
+// as its BF16 split a = a_hi + a_lo (a_hi = bf16(a), a_lo = bf16(a - a_hi): 16
+// significant bits); B is either a BF16 weight matrix (one MMA per split part:
+// A_hi W + A_lo W) or FP32 (split too: A_hi B_hi + A_hi B_lo + A_lo B_hi, the
+// dropped A_lo B_lo below 2^-16 relative).  So the products keep the accuracy
+// of the FP32-activation / BF16-weight arithmetic the network is defined with.
+// Operand (m, k) of A sits at a[m * sam + k * sak], (k, n) of B at
+// b[k * sbk + n * sbn]; rows and columns past M, N, K read as zero.
+// One warp owns a 16 x 32 tile of C (four 16 x 8 MMA tiles); a CTA of four
+// warps a 16 x 128 strip.  Fragments are gathered straight from global memory
+// (the operands are a few hundred kilobytes and stay in L1/L2).
+// Epilogue: EPI_BIAS_RELU  Z = C + bias[n], H = relu(Z);
+//           EPI_MASK       C = (mask(m, n) > 0) ? C : 0 (mask row stride N);
+//           EPI_STORE      C.
+enum { EPI_BIAS_RELU = 0, EPI_MASK = 1, EPI_STORE = 2 };
+constexpr int MMA_WARPS = 4;
+
+__device__ __forceinline__ unsigned pack_bf16(__nv_bfloat16 lo_col, __nv_bfloat16 hi_col) {
+    return (unsigned)__bfloat16_as_ushort(lo_col) | ((unsigned)__bfloat16_as_ushort(hi_col) << 16);
+}
+__device__ __forceinline__ void split_bf16(float x, __nv_bfloat16& hi, __nv_bfloat16& lo) {
+    hi = __float2bfloat16_rn(x);
+    lo = __float2bfloat16_rn(x - __bfloat162float(hi));
+}
+__device__ __forceinline__ void mma_bf16(float (&d)[4], const unsigned (&a)[4], unsigned b0, unsigned b1) {
+    asm volatile(
+        "mma.sync.aligned.m16n8k16.row.col.f32.bf16.bf16.f32 {%0,%1,%2,%3}, {%4,%5,%6,%7}, {%8,%9}, {%0,%1,%2,%3};"
+        : "+f"(d[0]), "+f"(d[1]), "+f"(d[2]), "+f"(d[3])
+        : "r"(a[0]), "r"(a[1]), "r"(a[2]), "r"(a[3]), "r"(b0), "r"(b1));
+}
+
+template <bool BW, int EPI>
+__global__ void __launch_bounds__(32 * MMA_WARPS)
+k_mma_gemm(int M, int N, int K, const float* __restrict__ a, long long sam, long long sak,
+           const float* __restrict__ mu, const float* __restrict__ is, const void* __restrict__ b, long long sbk,
+           long long sbn, const float* __restrict__ mub, const float* __restrict__ isb,
+           const float* __restrict__ bias, const float* __restrict__ mask, float* __restrict__ C,
+           float* __restrict__ C2) {
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    const int g = lane >> 2, tg = lane & 3;                 // fragment row group, thread in group
+    const int m0 = blockIdx.x * 16, n0 = blockIdx.y * 128 + warp * 32;
+    if (n0 >= N) return;
+    auto ldA = [&](int m, int k) -> float {
+        if (m >= M || k >= K) return 0.f;
+        const float v = a[(long long)m * sam + (long long)k * sak];
+        return mu ? (v - mu[k]) * is[k] : v;
+    };
+    auto ldB = [&](int k, int n) -> float {
+        if (k >= K || n >= N) return 0.f;
+        const long long i = (long long)k * sbk + (long long)n * sbn;
+        if (BW) return __bfloat162float(reinterpret_cast<const __nv_bfloat16*>(b)[i]);
+        const float v = reinterpret_cast<const float*>(b)[i];
+        return mub ? (v - mub[n]) * isb[n] : v;
+    };
+    float acc[4][4];
+#pragma unroll
+    for (int j = 0; j < 4; ++j)
+#pragma unroll
+        for (int e = 0; e < 4; ++e) acc[j][e] = 0.f;
+    for (int k0 = 0; k0 < K; k0 += 16) {
+        // A fragment: rows g, g + 8; columns 2 tg, 2 tg + 1 (+ 8)
+        unsigned ah[4], al[4];
+        {
+            const int r[4] = {g, g + 8, g, g + 8}, c[4] = {2 * tg, 2 * tg, 2 * tg + 8, 2 * tg + 8};
+#pragma unroll
+            for (int q = 0; q < 4; ++q) {
+                __nv_bfloat16 h0, l0, h1, l1;
+                split_bf16(ldA(m0 + r[q], k0 + c[q]), h0, l0);
+                split_bf16(ldA(m0 + r[q], k0 + c[q] + 1), h1, l1);
+                ah[q] = pack_bf16(h0, h1);
+                al[q] = pack_bf16(l0, l1);
+            }
+        }
+#pragma unroll
+        for (int j = 0; j < 4; ++j) {
+            const int n = n0 + 8 * j + g;                    // B fragment: column g; rows 2 tg, 2 tg + 1 (+ 8)
+            __nv_bfloat16 h[4], l[4];
+            const int kk[4] = {k0 + 2 * tg, k0 + 2 * tg + 1, k0 + 2 * tg + 8, k0 + 2 * tg + 9};
+#pragma unroll
+            for (int q = 0; q < 4; ++q) {
+                if (BW) {
+                    h[q] = __float2bfloat16_rn(ldB(kk[q], n));   // exact: the weights are BF16
+                    l[q] = __float2bfloat16_rn(0.f);
+                } else {
+                    split_bf16(ldB(kk[q], n), h[q], l[q]);
+                }
+            }
+            const unsigned bh0 = pack_bf16(h[0], h[1]), bh1 = pack_bf16(h[2], h[3]);
+            mma_bf16(acc[j], ah, bh0, bh1);
+            mma_bf16(acc[j], al, bh0, bh1);
+            if (!BW) mma_bf16(acc[j], ah, pack_bf16(l[0], l[1]), pack_bf16(l[2], l[3]));
+        }
+    }
+    // D fragment: rows g, g + 8; columns 2 tg, 2 tg + 1 of each n-tile
+#pragma unroll
+    for (int j = 0; j < 4; ++j) {
+#pragma unroll
+        for (int e = 0; e < 4; ++e) {
+            const int m = m0 + g + (e >= 2 ? 8 : 0), n = n0 + 8 * j + 2 * tg + (e & 1);
+            if (m >= M || n >= N) continue;
+            const long long o = (long long)m * N + n;
+            float v = acc[j][e];
+            if (EPI == EPI_BIAS_RELU) {
+                v += bias[n];
+                C[o] = v;
+                C2[o] = fmaxf(v, 0.f);
+            } else if (EPI == EPI_MASK) {
+                C[o] = mask[o] > 0.f ? v : 0.f;
+            } else {
+                C[o] = v;
+            }
+        }
+    }
+}
+
+template <bool BW, int EPI>
+cudaError_t launch_mma(int M, int N, int K, const float* a, long long sam, long long sak, const float* mu,
+                       const float* is, const void* b, long long sbk, long long sbn, const float* mub,
+                       const float* isb, const float* bias, const float* mask, float* C, float* C2, cudaStream_t s) {
+    const dim3 grid((unsigned)((M + 15) / 16), (unsigned)((N + 127) / 128));
+    k_mma_gemm<BW, EPI><<<grid, 32 * MMA_WARPS, 0, s>>>(M, N, K, a, sam, sak, mu, is, b, sbk, sbn, mub, isb, bias,
+                                                        mask, C, C2);
+    return cudaGetLastError();
+}
+
+// db[n] = sum_b D[b][n] (the bias gradients).
+__global__ void k_colsum(const float* __restrict__ D, int B, int N, float* __restrict__ db) {
+    const int n = blockIdx.x * blockDim.x + threadIdx.x;
+    if (n >= N) return;
+    float s = 0.f;
+    for (int b = 0; b < B; ++b) s += D[(long long)b * N + n];
+    db[n] = s;
 }
 
 // Adam (Kingma & Ba): FP32 master weights, bfloat16 copy for the products.
@@ -224,25 +328,45 @@ unsigned long long splitmix(unsigned long long& s) {
     return z ^ (z >> 31);
 }
 
+// The two hidden layers on the tensor cores: Z1 = A' W1^T + b1 (A' the
+// standardised input), H1 = relu(Z1); Z2 = H1 W2^T + b2, H2 = relu(Z2).
+cudaError_t mlp_hidden_layers(qbvm_mlp_t* h, const float* x, int B, cudaStream_t s) {
+    const int K = h->in_dim, N = h->width;
+    const float* mu = h->has_norm ? h->mu : nullptr;
+    const float* is = h->has_norm ? h->inv_sd : nullptr;
+    cudaError_t e = launch_mma<true, EPI_BIAS_RELU>(B, N, K, x, K, 1, mu, is, h->pb + h->oW1, 1, K, nullptr, nullptr,
+                                                    h->p + h->ob1, nullptr, h->Z1, h->H1, s);
+    if (e != cudaSuccess) return e;
+    return launch_mma<true, EPI_BIAS_RELU>(B, N, N, h->H1, N, 1, nullptr, nullptr, h->pb + h->oW2, 1, N, nullptr,
+                                           nullptr, h->p + h->ob2, nullptr, h->Z2, h->H2, s);
+}
+
 int mlp_grads(qbvm_mlp_t* h, const float* x, const float* t, int B, cudaStream_t s) {
     const int K = h->in_dim, N = h->width;
     const float* mu = h->has_norm ? h->mu : nullptr;
     const float* is = h->has_norm ? h->inv_sd : nullptr;
     if (cudaMemsetAsync(h->loss, 0, sizeof(double), s) != cudaSuccess) return QBVM_ERR_CUDA;
-    k_dense_relu<<<nblk((long long)B * N), MLP_THREADS, 0, s>>>(x, h->pb + h->oW1, h->p + h->ob1, B, K, N, mu, is, h->Z1, h->H1);
-    k_dense_relu<<<nblk((long long)B * N), MLP_THREADS, 0, s>>>(h->H1, h->pb + h->oW2, h->p + h->ob2, B, N, N, nullptr,
-                                                                 nullptr, h->Z2, h->H2);
+    if (mlp_hidden_layers(h, x, B, s) != cudaSuccess) return QBVM_ERR_CUDA;
     k_dense_out<<<nblk((long long)B * 32), MLP_THREADS, 0, s>>>(h->H2, h->pb + h->ow3, h->p + h->ob3, B, N, h->y);
     k_mse<<<nblk(B), MLP_THREADS, 0, s>>>(h->y, t, B, h->dy, h->loss);
     // w3, b3: dW = dy^T H2 (one output row)
     k_wgrad<<<nblk((long long)(N + 1)), MLP_THREADS, 0, s>>>(h->dy, h->H2, B, 1, N, nullptr, nullptr, h->g + h->ow3,
                                                             h->g + h->ob3);
     k_back_out<<<nblk((long long)B * N), MLP_THREADS, 0, s>>>(h->dy, h->pb + h->ow3, h->Z2, B, N, h->dZ2);
-    k_wgrad<<<nblk((long long)N * (N + 1)), MLP_THREADS, 0, s>>>(h->dZ2, h->H1, B, N, N, nullptr, nullptr,
-                                                                h->g + h->oW2, h->g + h->ob2);
-    k_back_hidden<<<nblk((long long)B * N), MLP_THREADS, 0, s>>>(h->dZ2, h->pb + h->oW2, h->Z1, B, N, N, h->dZ1);
-    k_wgrad<<<nblk((long long)N * (K + 1)), MLP_THREADS, 0, s>>>(h->dZ1, x, B, N, K, mu, is, h->g + h->oW1,
-                                                                h->g + h->ob1);
+    // dW2 = dZ2^T H1 (N x N, reduction over the batch), db2 = column sums of dZ2
+    if (launch_mma<false, EPI_STORE>(N, N, B, h->dZ2, 1, N, nullptr, nullptr, h->H1, N, 1, nullptr, nullptr,
+                                     nullptr, nullptr, h->g + h->oW2, nullptr, s) != cudaSuccess)
+        return QBVM_ERR_CUDA;
+    k_colsum<<<nblk(N), MLP_THREADS, 0, s>>>(h->dZ2, B, N, h->g + h->ob2);
+    // dZ1 = (dZ2 W2) masked by Z1 > 0
+    if (launch_mma<true, EPI_MASK>(B, N, N, h->dZ2, N, 1, nullptr, nullptr, h->pb + h->oW2, N, 1, nullptr, nullptr,
+                                   nullptr, h->Z1, h->dZ1, nullptr, s) != cudaSuccess)
+        return QBVM_ERR_CUDA;
+    // dW1 = dZ1^T A' (N x K, A' the standardised input, standardised on load), db1
+    if (launch_mma<false, EPI_STORE>(N, K, B, h->dZ1, 1, N, nullptr, nullptr, x, K, 1, mu, is, nullptr, nullptr,
+                                     h->g + h->oW1, nullptr, s) != cudaSuccess)
+        return QBVM_ERR_CUDA;
+    k_colsum<<<nblk(N), MLP_THREADS, 0, s>>>(h->dZ1, B, N, h->g + h->ob1);
     return cudaGetLastError() == cudaSuccess ? QBVM_OK : QBVM_ERR_CUDA;
 }
 
@@ -344,12 +468,8 @@ int qbvm_mlp_set_params(qbvm_mlp_t* h, const float* params, const float* adam_m,
 int qbvm_mlp_forward(qbvm_mlp_t* h, const float* x, int B, float* y, void* stream) {
     if (!h || !x || !y || B < 1 || B > h->bmax) return QBVM_ERR_BAD_ARG;
     cudaStream_t s = static_cast<cudaStream_t>(stream);
-    const int K = h->in_dim, N = h->width;
-    k_dense_relu<<<nblk((long long)B * N), MLP_THREADS, 0, s>>>(x, h->pb + h->oW1, h->p + h->ob1, B, K, N,
-                                                                 h->has_norm ? h->mu : nullptr,
-                                                                 h->has_norm ? h->inv_sd : nullptr, h->Z1, h->H1);
-    k_dense_relu<<<nblk((long long)B * N), MLP_THREADS, 0, s>>>(h->H1, h->pb + h->oW2, h->p + h->ob2, B, N, N, nullptr,
-                                                                 nullptr, h->Z2, h->H2);
+    const int N = h->width;
+    if (mlp_hidden_layers(h, x, B, s) != cudaSuccess) return QBVM_ERR_CUDA;
     k_dense_out<<<nblk((long long)B * 32), MLP_THREADS, 0, s>>>(h->H2, h->pb + h->ow3, h->p + h->ob3, B, N, y);
     return cudaGetLastError() == cudaSuccess ? QBVM_OK : QBVM_ERR_CUDA;
 }
