@@ -294,6 +294,15 @@ int qbvm_batch_info(const qbvm_batch_t* batch, double* alphas, long long* unknow
  * ||f_b - A_b y_b|| / ||f_b|| over the instances after the last solve (NaN
  * after an FP64 fallback).  Either output may be NULL. */
 int qbvm_batch_refine_info(const qbvm_batch_t* batch, int* iters, double* max_rel_residual);
+/* FP32_REFINE batches: *fused = 1 when the batch runs the whole refinement
+ * in one launch, 0 when it runs the staged passes above.  The one-launch
+ * form takes 1D space-first batches with (m, nt) in {(64, 64), (64, 128),
+ * (128, 64)}: one CTA per instance keeps the instance's double-float iterate
+ * and FP32 work array in shared memory for every step, and each instance
+ * stops on its own relative residual (<= refine_tol, or DIVERGED as above);
+ * refine_info then reports the most steps any instance took and the largest
+ * final residual.  The call synchronises `stream` once, after the launch. */
+int qbvm_batch_refine_fused(const qbvm_batch_t* batch, int* fused);
 int qbvm_batch_destroy(qbvm_batch_t* batch);
 
 /* ------------------------------------------------------------------------

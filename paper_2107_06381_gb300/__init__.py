@@ -130,6 +130,8 @@ def load_library(path: str | None = None) -> ctypes.CDLL:
     lib.qbvm_batch_info.restype = ip
     lib.qbvm_batch_refine_info.argtypes = [vp, ctypes.POINTER(ip), ctypes.POINTER(dp)]
     lib.qbvm_batch_refine_info.restype = ip
+    lib.qbvm_batch_refine_fused.argtypes = [vp, ctypes.POINTER(ip)]
+    lib.qbvm_batch_refine_fused.restype = ip
     lib.qbvm_batch_destroy.argtypes = [vp]
     lib.qbvm_batch_destroy.restype = ip
     lib.qbvm_selftest_newton_rcp.argtypes = [vp, ctypes.c_longlong, ctypes.POINTER(dp), vp]
@@ -634,6 +636,13 @@ class Batch:
         _check(load_library().qbvm_batch_refine_info(self.handle, ctypes.byref(it), ctypes.byref(rel)),
                "qbvm_batch_refine_info")
         return it.value, rel.value
+
+    @property
+    def refine_fused(self):
+        """True when the FP32_REFINE batch runs the whole refinement in one launch."""
+        f = ctypes.c_int()
+        _check(load_library().qbvm_batch_refine_fused(self.handle, ctypes.byref(f)), "qbvm_batch_refine_fused")
+        return bool(f.value)
 
     @property
     def alphas(self):

@@ -21,7 +21,7 @@ LIB_DIR = os.path.join(HERE, "_lib")
 LIB_PATH = os.path.join(LIB_DIR, "libqbvm.so")
 
 SOURCES = ["qbvm_kernels.cu", "qbvm_plan.cu", "qbvm_noalloc.cu", "qbvm_sweep.cu", "qbvm_mlp.cu",
-           "qbvm_gmres.cu", "qbvm_batch.cu", "qbvm_peak.cu", "qbvm_multi.cu"]
+           "qbvm_gmres.cu", "qbvm_batch.cu", "qbvm_peak.cu", "qbvm_multi.cu", "qbvm_refine1d.cu"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 FLAGS = ["-O3", "-lineinfo", "-std=c++17", "-Xcompiler", "-fPIC,-O2", "--expt-relaxed-constexpr",
          "-I", CSRC, "-I", INCLUDE]

@@ -81,6 +81,9 @@ struct qbvm_batch {
     double* partials = nullptr;   // residual partial sums [count][bpi][2]
     double* sums = nullptr;       // per-instance ||r||^2, ||f||^2 [count][2]
     int* flags = nullptr;         // input classification (NaN/Inf, nonzero)
+    bool r1 = false;              // 1D shapes the fused refinement kernel takes (qbvm_refine1d.cu)
+    int* r1_stat = nullptr;       // its per-instance status and steps, [count][2]
+    double* r1_rel = nullptr;     // its per-instance final relative residual, [count]
     int bpi = 1;
     int last_iters = 0;
     double last_rel = 0.0;        // largest relative residual over the instances at the end
@@ -213,6 +216,12 @@ int fp32_tables(qbvm_batch* bt) {
     if (rc) return rc;
     bt->t32_delta = {gp, gi, gr, gir, ak, pcd, prh, pri};
     bt->t32_gen = {gp, gi, gr, gir, ak, pcg, prh, pri};
+    bt->r1 = qbvm::refine1d_supported(tb) != 0;
+    if (bt->r1) {                                  // the fused kernel needs no work arrays
+        rc = balloc(bt, &bt->r1_stat, (size_t)(2 * count));
+        if (!rc) rc = balloc(bt, &bt->r1_rel, (size_t)count);
+        return rc;
+    }
     // blocks per instance: about four groups of four unknowns per thread
     // (measured on 10 000 instances of 63 x 64: one, two and four groups per
     // thread took 2.51, 2.12 and 1.93 ms per refined batch)
@@ -423,7 +432,77 @@ int fp32_solve_batched(qbvm_batch* bt, const qbvm::Tables& tb, const void* rhs, 
     return QBVM_OK;
 }
 
+// The fused 1D refinement: one launch, then the per-instance statuses.
+int solve_batched_r1(qbvm_batch* bt, const double* in, double* y, int n0_only, cudaStream_t s) {
+    qbvm::PlanView v;
+    qbvm::plan_view(bt->base, &v);
+    const qbvm::Tables& tb = *v.tb;
+    const long long B = bt->count;
+    auto df = [](double x) {
+        const float h = (float)x;
+        return make_float2(h, (float)(x - (double)h));
+    };
+    qbvm::Refine1dArgs a;
+    a.f = in;
+    a.y = y;
+    a.delta = bt->d.rhs_kind == QBVM_RHS_DELTA;
+    a.n0_only = n0_only;
+    a.tws = tb.tw_s32[0];
+    a.sns = tb.sn_s32[0];
+    a.twt = tb.tw_t32;
+    a.lamtau = tb.lamtau32;
+    a.gpow = bt->t32_gen.gpow;
+    a.gipw = bt->t32_gen.gipw;
+    a.ak = bt->t32_gen.ak;
+    a.cnorm = bt->t32_gen.cnorm;
+    a.rho_h = bt->t32_gen.rho_h;
+    a.rho_hinv = bt->t32_gen.rho_hinv;
+    a.omega_df = bt->omega_df;
+    a.omega64 = bt->omega64;
+    a.ct = df(1.0 / tb.tau);
+    a.cx = df(v.h2inv[0]);
+    a.inv_tau = 1.0 / tb.tau;
+    a.tol = bt->d.refine_tol > 0 ? bt->d.refine_tol : 1e-13;
+    a.maxit = bt->d.refine_max_iters > 0 ? bt->d.refine_max_iters : 10;
+    a.iters = bt->r1_stat + B;
+    a.rel = bt->r1_rel;
+    a.status = bt->r1_stat;
+    BCK(qbvm::launch_refine1d(tb, B, a, s));
+    std::vector<int> st((size_t)(2 * B));
+    std::vector<double> rl((size_t)B);
+    BCK(cudaMemcpyAsync(st.data(), bt->r1_stat, sizeof(int) * 2 * B, cudaMemcpyDeviceToHost, s));
+    BCK(cudaMemcpyAsync(rl.data(), bt->r1_rel, sizeof(double) * B, cudaMemcpyDeviceToHost, s));
+    BCK(cudaStreamSynchronize(s));
+    bool nonfinite_in = false, unusable = false, nonfinite = false, diverged = false;
+    int iters = 0;
+    double rel = 0.0;
+    for (long long b = 0; b < B; ++b) {
+        const int sb = st[(size_t)b];
+        if (sb == 1) nonfinite_in = true;
+        if (sb == 1 || sb == 2) unusable = true;
+        if (sb == 3) diverged = true;
+        if (sb == 4) nonfinite = true;
+        iters = std::max(iters, st[(size_t)(B + b)]);
+        rel = std::max(rel, rl[(size_t)b]);
+    }
+    if (unusable) {
+        // NaN / Inf, or data outside the FP32 range, in some instance: the FP64
+        // pipeline solves the batch, as in the staged refinement
+        int rc = fp64_tables(bt);
+        if (rc) return rc;
+        rc = solve_batched_fp64(bt, in, y, n0_only, s);
+        bt->last_iters = 0;
+        bt->last_rel = NAN;
+        return rc ? rc : (nonfinite_in ? QBVM_ERR_NONFINITE : QBVM_OK);
+    }
+    bt->last_iters = iters;
+    bt->last_rel = rel;
+    if (nonfinite) return QBVM_ERR_NONFINITE;
+    return diverged ? QBVM_ERR_DIVERGED : QBVM_OK;
+}
+
 int solve_batched_fp32r(qbvm_batch* bt, const double* in, double* y, int n0_only, cudaStream_t s) {
+    if (bt->r1) return solve_batched_r1(bt, in, y, n0_only, s);
     qbvm::PlanView v;
     qbvm::plan_view(bt->base, &v);
     const qbvm::Tables& tb = *v.tb;
@@ -571,6 +650,12 @@ int qbvm_batch_refine_info(const qbvm_batch_t* bt, int* iters, double* max_rel_r
     if (!bt) return QBVM_ERR_BAD_ARG;
     if (iters) *iters = bt->last_iters;
     if (max_rel_residual) *max_rel_residual = bt->last_rel;
+    return QBVM_OK;
+}
+
+int qbvm_batch_refine_fused(const qbvm_batch_t* bt, int* fused) {
+    if (!bt || !fused) return QBVM_ERR_BAD_ARG;
+    *fused = bt->r1 ? 1 : 0;
     return QBVM_OK;
 }
 

@@ -112,6 +112,40 @@ cudaError_t launch_residual_df_batched(const void* y_df, const double* f, int de
                                        const double* omega64, float* r_out, double* partials, double* sums,
                                        int fnorm, int bpi, cudaStream_t s);
 int residual_blocks_per_instance(const Tables& tb);
+
+// FP32 + double-float refinement of `count` 1D instances of one shape in one
+// launch (qbvm_refine1d.cu): one CTA per instance holds its iterate and work
+// array in shared memory for the whole loop and stops on its own residual.
+// f: [count][n] (delta: g) or [count][nt][n]; y: [count][nt][n] or
+// [count][n] (n0_only).  Per-instance tables as BatchTables32 (the general
+// cnorm), omega as a double-float pair and in FP64; ct = 1/tau and
+// cx = 1/h^2 as double-float pairs.  Outputs per instance: refinement steps,
+// final relative residual and a status (0 ok, 1 NaN / Inf in f, 2 f outside
+// the FP32 range, 3 no contraction above 1e-10 or the step cap, 4 NaN / Inf
+// residual); instances with status 1 or 2 write no y.
+struct Refine1dArgs {
+    const double* f = nullptr;
+    double* y = nullptr;
+    int delta = 0, n0_only = 0;
+    const float2* tws = nullptr;   // DST roots exp(-2 pi i m / M), m < M
+    const float* sns = nullptr;    // sin(j pi / M), j <= M/2
+    const float2* twt = nullptr;   // time roots exp(-2 pi i m / H), m < H
+    const float* lamtau = nullptr; // tau Lambda_l, l < n
+    const float2 *gpow = nullptr, *gipw = nullptr, *ak = nullptr;       // [count][H]
+    const float *cnorm = nullptr, *rho_h = nullptr, *rho_hinv = nullptr; // [count]
+    const float2* omega_df = nullptr;
+    const double* omega64 = nullptr;
+    float2 ct{}, cx{};
+    double inv_tau = 0, tol = 0;
+    int maxit = 0;
+    int* iters = nullptr;
+    double* rel = nullptr;
+    int* status = nullptr;
+};
+// 1 when the fused kernel takes tb's shape (1D space-first, power-of-two nt,
+// (m, nt) in {(64, 64), (64, 128), (128, 64)}, within the device's shared memory).
+int refine1d_supported(const Tables& tb);
+cudaError_t launch_refine1d(const Tables& tb, long long count, const Refine1dArgs& a, cudaStream_t s);
 // y[l] = fac[l] * x[l], l < n
 cudaError_t launch_mul_modes(const double* x, const double* fac, double* y, long long n, cudaStream_t s);
 

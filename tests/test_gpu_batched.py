@@ -125,8 +125,9 @@ def _batched32(grid, form, alphas, rhs, rhs_kind, n0_only, tol=0.0):
 
 
 GRIDS32 = [
-    bi.Grid(1, (64,), 1.0, 0.1, 64),              # the 1D 63 x 64 shape (register time solve, H = 32)
+    bi.Grid(1, (64,), 1.0, 0.1, 64),              # the 1D 63 x 64 shape (one-launch refinement)
     bi.Grid(2, (32, 16), 1.0, 0.1, 16),           # generic FP32 time tile (H = 8)
+    bi.Grid(1, (32,), 1.0, 0.1, 64),              # 1D through the staged passes (register time solve)
     bi.Grid(3, (8, 8, 4), 1.0, 0.05, 128),
     bi.Grid(2, (10, 100), 1.0, 0.1, 256),         # mixed-radix DST lengths
 ]
