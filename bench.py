@@ -100,6 +100,9 @@ def parse():
     ap.add_argument("--c5", action="store_true",
                     help="only the learned-alpha workload at its full size (200k labelled 2D 127^2 x 128 "
                          "instances, 4096 held out); several minutes")
+    ap.add_argument("--leg", choices=["c3_3d", "c4_sweep", "c4_full_multi", "c1_batched", "batched_2d",
+                                      "learned_alpha"],
+                    help="run one of the secondary workloads alone (its JSON object only, no headline)")
     ap.add_argument("--no-extra", action="store_true",
                     help="skip the 3D (127^3 x 128) and batched-sweep (512 instances) measurements")
     return ap.parse_args()
@@ -550,15 +553,8 @@ def our_arm(args, rank, world, device):
 
     extra = {}
     if not args.no_extra and not args.refine_only:
-        extra["c3_3d"] = c3_leg(args, device, stream, flush, rank == 0 and world == 1 and not args.no_cpu_baseline)
-        extra["c4_sweep"] = c4_leg(args, device, stream)
-        extra["c4_full_multi"] = c4_full_leg(args, device, stream,
-                                             with_oracle=rank == 0 and world == 1 and not args.no_cpu_baseline)
-        extra["c1_batched"] = c1_batched_leg(args, device, stream, flush,
-                                             with_oracle=rank == 0 and world == 1 and not args.no_cpu_baseline)
-        extra["batched_2d"] = batched_2d_leg(args, device, stream, flush,
-                                             with_oracle=rank == 0 and world == 1 and not args.no_cpu_baseline)
-        extra["learned_alpha"] = learned_alpha_leg(with_oracle=rank == 0 and world == 1 and not args.no_cpu_baseline)
+        extra = run_legs(args, device, stream, flush, rank == 0 and world == 1 and not args.no_cpu_baseline)
+
 
     out = {
         "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
@@ -772,9 +768,9 @@ def c1_batched_leg(args, device, stream, flush, count=10_000, with_oracle=True):
     `count` instances with their own noise draw and alpha = their own delta
     (PinT-QBVM, Section 5), full y of every instance, one qbvm_solve_batched
     call per batch: FP64 (3 kernel launches for the whole batch) and FP32
-    transforms + double-float refinement (about 20 launches and one
-    synchronisation per refinement step), each with its error against the
-    FP64 oracle on sampled instances."""
+    transforms + double-float refinement (one launch: a CTA per instance runs
+    the whole refinement in shared memory; one synchronisation per batch),
+    each with its error against the FP64 oracle on sampled instances."""
     import numpy as np
     import torch
     import bhcp_inputs as bi
@@ -811,7 +807,9 @@ def c1_batched_leg(args, device, stream, flush, count=10_000, with_oracle=True):
             else:
                 it, rel = bt.refine_info
                 leg.update({"refine_steps": it, "max_rel_residual": rel,
-                            "dtype": "f32 transforms + double-float residual/update"})
+                            "dtype": "f32 transforms + double-float residual/update",
+                            "one_launch": bt.refine_fused,
+                            "kernel_launches_per_batch": 1 if bt.refine_fused else None})
             if with_oracle:
                 import oracle as O
                 errs = []
@@ -1024,8 +1022,33 @@ def c5_leg(n_train=200_000, n_eval=4096, seed=5):
             "data": "synthetic"}
 
 
+def run_legs(args, device, stream, flush, with_oracle, only=None):
+    """The secondary workloads (3D, the sweeps, the batches, learned alpha),
+    all of them or the one named."""
+    legs = {
+        "c3_3d": lambda: c3_leg(args, device, stream, flush, with_oracle),
+        "c4_sweep": lambda: c4_leg(args, device, stream),
+        "c4_full_multi": lambda: c4_full_leg(args, device, stream, with_oracle=with_oracle),
+        "c1_batched": lambda: c1_batched_leg(args, device, stream, flush, with_oracle=with_oracle),
+        "batched_2d": lambda: batched_2d_leg(args, device, stream, flush, with_oracle=with_oracle),
+        "learned_alpha": lambda: learned_alpha_leg(with_oracle=with_oracle),
+    }
+    return {k: f() for k, f in legs.items() if only is None or k == only}
+
+
 def main():
     args = parse()
+    if args.leg:
+        import torch
+        import paper_2107_06381_gb300 as Q
+        device = torch.device("cuda", 0)
+        torch.cuda.set_device(device)
+        Q.build_library()
+        Q.load_library()
+        stream = torch.cuda.Stream(device)
+        flush = torch.empty(64 * 1024 * 1024, dtype=torch.float32, device=device)      # 256 MB > L2
+        print(json.dumps(run_legs(args, device, stream, flush, not args.no_cpu_baseline, only=args.leg)), flush=True)
+        return 0
     if args.c5:
         import torch
         torch.cuda.set_device(0)
