@@ -642,10 +642,14 @@ def c3_leg(args, device, stream, flush, with_oracle):
     return out
 
 
-def c4_leg(args, device, stream):
+def c4_leg(args, device, stream, with_oracle=True):
     """512 uneven instances (1D n in {63..2047}, 2D {63,127,255}^2, nt in {32..512},
     relative noise log-uniform in [1e-4, 1e-2]) x 16 alphas, one persistent
-    launch per run from a captured CUDA graph, launch shape autotuned."""
+    launch per run from a captured CUDA graph, launch shape autotuned.  The
+    FP32 mode scans alpha in FP32 and sums y^0 at the picked alpha in
+    double-float; the FP64 mode does both in FP64.  With the oracle: the
+    discrepancies of the four smallest instances at all 16 alphas, the pick,
+    and y^0 at the pick, against the oracle's full solves."""
     import numpy as np
     import torch
     import bhcp_inputs as bi
@@ -661,7 +665,7 @@ def c4_leg(args, device, stream):
         gd, delta = bi.add_noise_gaussian(grid, bi.forward_discrete(grid, z0), s["rel_noise"], rng)
         g = torch.as_tensor(gd.ravel(), dtype=torch.float64, device=device)
         y0 = torch.empty(grid.Nx, dtype=torch.float64, device=device)
-        keep.append((g, y0))
+        keep.append((g, y0, grid, gd, delta))
         insts.append(dict(dim=grid.dim, m=grid.M, L=1.0, T=0.1, nt=grid.nt, form=Q.FORM_PQ, delta=delta, g=g, y0=y0))
         alpha_solves_unknowns += grid.unknowns
     out = {"workload": "c4_batch_512_uneven_x16_alpha", "instances": len(specs), "n_alpha": 16}
@@ -684,7 +688,37 @@ def c4_leg(args, device, stream):
                          "config": {"modes_per_thread": cfg.modes_per_thread, "ctas_per_sm": cfg.ctas_per_sm,
                                     "grid": cfg.grid},
                          "graph_launches_per_run": 1, "kernel_launches_per_run": 1}
+            if with_oracle:
+                out[name].update(_c4_oracle_check(keep, al, disc, pick))
+    out["fp32_scan"]["mode"] = "alpha scan in FP32, y0 at the pick summed in double-float"
+    out["fp64_scan"]["mode"] = "alpha scan and y0 at the pick in FP64"
     return out
+
+
+def _c4_oracle_check(keep, al, disc, pick, tau_dp=1.1, count=4):
+    """Discrepancies (all alphas), pick and y^0 at the pick of the `count`
+    smallest instances against the oracle's full FP64 solves."""
+    import numpy as np
+    import bhcp_inputs as bi
+    import oracle as O
+    order = sorted(range(len(keep)), key=lambda i: keep[i][2].unknowns)[:count]
+    dmax, ymax, same = 0.0, 0.0, 0
+    for i in order:
+        _, y0, grid, gd, delta = keep[i]
+        od, oy = [], []
+        for a in al[i]:
+            y = O.solve_spectral(grid, O.PQ, float(a), O.delta_rhs(grid, O.PQ, float(a), gd))
+            od.append(bi.discrete_l2(y[-1] - gd, grid))
+            oy.append(y[0])
+        od = np.array(od)
+        dmax = max(dmax, float(np.max(np.abs(np.asarray(disc[i]) / od - 1.0))))
+        ok = np.nonzero(od <= tau_dp * delta)[0]
+        opick = int(ok[np.argmax(np.asarray(al[i])[ok])]) if len(ok) else int(np.argmin(od))
+        same += int(int(pick[i, 0]) == opick)
+        ymax = max(ymax, O.rel_l2(y0.cpu().numpy(), oy[int(pick[i, 0])].ravel()))
+    return {"disc_rel_err_vs_oracle": dmax, "y0_at_pick_rel_err_vs_oracle": ymax,
+            "picks_equal_to_oracle": f"{same}/{len(order)}",
+            "oracle_sample": f"the {len(order)} smallest instances, all 16 alphas"}
 
 
 def c4_full_leg(args, device, stream, with_oracle=True):
@@ -1027,7 +1061,7 @@ def run_legs(args, device, stream, flush, with_oracle, only=None):
     all of them or the one named."""
     legs = {
         "c3_3d": lambda: c3_leg(args, device, stream, flush, with_oracle),
-        "c4_sweep": lambda: c4_leg(args, device, stream),
+        "c4_sweep": lambda: c4_leg(args, device, stream, with_oracle=with_oracle),
         "c4_full_multi": lambda: c4_full_leg(args, device, stream, with_oracle=with_oracle),
         "c1_batched": lambda: c1_batched_leg(args, device, stream, flush, with_oracle=with_oracle),
         "batched_2d": lambda: batched_2d_leg(args, device, stream, flush, with_oracle=with_oracle),

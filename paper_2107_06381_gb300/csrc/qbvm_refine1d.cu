@@ -340,6 +340,19 @@ __device__ __forceinline__ void time_modes(float* W, int WS, int nmodes, float2*
 // Per-instance status written by the kernel (the host maps it to the batch's).
 enum : int { ST_OK = 0, ST_NONFINITE_IN = 1, ST_RANGE = 2, ST_DIVERGED = 3, ST_NONFINITE = 4 };
 
+// FP32 sum over the CTA, returned in thread 0 (warp shuffles, then one thread
+// over the warps' sums).
+__device__ __forceinline__ float fsum0(float v, float* shf) {
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+    if ((threadIdx.x & 31) == 0) shf[threadIdx.x >> 5] = v;
+    __syncthreads();
+    float s = 0.f;
+    if (threadIdx.x == 0)
+        for (int i = 0; i < NTH / 32; ++i) s += shf[i];
+    return s;
+}
+
 // Sum of the CTA's ScaledSsq partials, returned in thread 0: within a warp the
 // partials are rescaled to the warp's largest exponent and added in FP32 (a
 // stopping test needs no more), the warps' sums are combined in FP64 by one
@@ -388,6 +401,7 @@ __global__ void __launch_bounds__(NTH, 2) k_refine1d(Refine1dArgs a) {
     __shared__ float s_f[NTH / 32];
     __shared__ int s_e[NTH / 32];
     __shared__ int s_go;
+    __shared__ float s_scale;
     const int tid = threadIdx.x;
     const long long b = blockIdx.x;
 
@@ -446,6 +460,9 @@ __global__ void __launch_bounds__(NTH, 2) k_refine1d(Refine1dArgs a) {
         if (bad) st = ST_NONFINITE_IN;
         else if ((rms > 0 && (rms < 1e-18 || rms > 1e28)) || (f2 == 0.0 && nonzero)) st = ST_RANGE;
         s_go = st != ST_OK ? 0 : f2 > 0.0 ? 1 : 2;
+        // residual sums of squares are taken of r / 2^k, 2^k the power of two at
+        // or below the root mean square of f (in range: rms in [1e-18, 1e28])
+        s_scale = rms > 0 ? ldexpf(1.f, -(int)floorf(log2f((float)rms))) : 1.f;
         if (st != ST_OK || f2 == 0.0) {
             a.status[b] = st;
             a.iters[b] = 0;
@@ -460,6 +477,7 @@ __global__ void __launch_bounds__(NTH, 2) k_refine1d(Refine1dArgs a) {
     }
 
     double prev2 = INFINITY, r2 = f2;             // the stopping test runs in thread 0, on squares
+    const float rsc = s_scale;
     int it = 0, status = ST_OK;
     const int rj = tid % M, rc = tid / M;
     for (bool first = true;; first = false) {
@@ -474,7 +492,7 @@ __global__ void __launch_bounds__(NTH, 2) k_refine1d(Refine1dArgs a) {
         else dst_rows<LM, 2>(W, NT, bufs, tws, sns, Y);
         __syncthreads();
         // ---- r = f - A y (eq. 3.3 / 3.6) in double-float, rounded to FP32 into W
-        ScaledSsq nr;
+        float nr = 0.f;                           // sum of (r / 2^k)^2
         if (rj < n) {
             const int j = rj, t0 = rc * LC, pj = P(j), pl = j > 0 ? P(j - 1) : 0, pr = j < n - 1 ? P(j + 1) : 0;
             int e = t0 * YS;                      // row offset of level t0 + q
@@ -504,17 +522,21 @@ __global__ void __launch_bounds__(NTH, 2) k_refine1d(Refine1dArgs a) {
                 const dfloat r = df_sub_un(fv, Ay);
                 const float rh = r.hi + r.lo;
                 W[(t0 + q) * WS + pj] = rh;
-                nr.add(rh);
+                const float rs = rh * rsc;
+                nr = fmaf(rs, rs, nr);
                 pv = yc;
             }
         }
-        r2 = ssq_sum0(nr, s_f, s_e);
+        const float r2s = fsum0(nr, s_f);
         if (tid == 0) {
             // ||r|| <= tol ||f||, ||r|| > ||r_prev|| / 2 and ||r|| > 1e-10 ||f||,
             // compared as squares (no division or square root in the loop)
+            r2 = (double)r2s / ((double)rsc * (double)rsc);
             int go = 0;
-            if (!(r2 <= 1.0e300)) {               // NaN or Inf residual
+            if (r2s != r2s) {                     // NaN residual
                 status = ST_NONFINITE;
+            } else if (isinf(r2s)) {              // (r / 2^k)^2 beyond the FP32 range: diverging
+                status = ST_DIVERGED;
             } else if (r2 <= a.tol * a.tol * f2) {
             } else if (r2 > 0.25 * prev2) {       // no contraction
                 if (r2 > 1e-20 * f2) status = ST_DIVERGED;
