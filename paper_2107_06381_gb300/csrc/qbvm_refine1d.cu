@@ -114,14 +114,18 @@ __device__ __forceinline__ void dst_rows(float* W, int rows, float2* bufs, const
         float2 v[N1];
 #pragma unroll
         for (int n1 = 0; n1 < N1; ++n1) {
-            const int j = N2 * n1 + t;
-            if (j == 0) {
+            // j = N2 n1 + t (t < N2) and M - j in the padded layout, in closed form:
+            // P(N2 n1 + t - 1) = P(N2 n1) + t - 1 for t >= 1 and
+            // P(M - 1 - N2 n1 - t) = P(M - 1 - N2 n1) - t (no run boundary is crossed)
+            const int c0 = N2 * n1, cm = M - 1 - N2 * n1;
+            const int pj = t ? Pad<LM>::col(c0) + t - 1 : (n1 ? Pad<LM>::col(c0 - 1) : 0);
+            const int pm = Pad<LM>::col(cm) - t;
+            const int si = 2 * n1 < N1 ? c0 + t : M - c0 - t;          // min(j, M - j)
+            if (n1 == 0 && t == 0) {
                 v[n1] = make_float2(0.f, 0.f);
             } else {
-                const int jm = M - j;
-                const int pj = P(j - 1), pm = P(jm - 1);
                 const float xa = wa[pj], xb = wb[pj], ma = wa[pm], mb = wb[pm];
-                const float s = sns[j < jm ? j : jm];
+                const float s = sns[si];
                 v[n1] = make_float2(fmaf(s, xa + ma, 0.5f * (xa - ma)), fmaf(s, xb + mb, 0.5f * (xb - mb)));
             }
         }
@@ -180,24 +184,27 @@ __device__ __forceinline__ void dst_rows(float* W, int rows, float2* bufs, const
         }
         const float oa = sa - pa, ob = sb - pb;
         if (act) {
+            // outputs 2k - 1 and 2k, k = KP t + i, in the padded layout:
+            // P(2k) = (2 KP + 1) t + 2i, P(2k - 1) = (2 KP + 1) t + 2i - 1 (i > 0)
+            // or (2 KP + 1) t - 2 (i = 0)
+            const int ob0 = (2 * KP + 1) * t;
             if (OUT == 0) {
                 float* oa_row = W + 2 * p * WS;
                 float* ob_row = oa_row + WS;
 #pragma unroll
                 for (int i = 0; i < KP; ++i) {
-                    const int k = KP * t + i;
-                    if (k > 0) {                      // y_{2k}
-                        oa_row[P(2 * k - 1)] = ea[i];
-                        ob_row[P(2 * k - 1)] = eb[i];
+                    if (i > 0 || t > 0) {             // y_{2k}
+                        const int q = ob0 + (i ? 2 * i - 1 : -2);
+                        oa_row[q] = ea[i];
+                        ob_row[q] = eb[i];
                     }
-                    oa_row[P(2 * k)] = ra[i] + oa;    // y_{2k+1}
-                    ob_row[P(2 * k)] = rb[i] + ob;
+                    oa_row[ob0 + 2 * i] = ra[i] + oa; // y_{2k+1}
+                    ob_row[ob0 + 2 * i] = rb[i] + ob;
                 }
             } else {
                 float2* ya = Y + 2 * p * YS;
                 float2* yb = ya + YS;
-                auto put = [&](float2* row, int jp, float v) {
-                    const int q = P(jp);
+                auto put = [&](float2* row, int q, float v) {
                     if (OUT == 1) {
                         row[q] = make_float2(v, 0.f);
                     } else {
@@ -208,13 +215,13 @@ __device__ __forceinline__ void dst_rows(float* W, int rows, float2* bufs, const
                 };
 #pragma unroll
                 for (int i = 0; i < KP; ++i) {
-                    const int k = KP * t + i;
-                    if (k > 0) {
-                        put(ya, 2 * k - 1, ea[i]);
-                        put(yb, 2 * k - 1, eb[i]);
+                    if (i > 0 || t > 0) {
+                        const int q = ob0 + (i ? 2 * i - 1 : -2);
+                        put(ya, q, ea[i]);
+                        put(yb, q, eb[i]);
                     }
-                    put(ya, 2 * k, ra[i] + oa);
-                    put(yb, 2 * k, rb[i] + ob);
+                    put(ya, ob0 + 2 * i, ra[i] + oa);
+                    put(yb, ob0 + 2 * i, rb[i] + ob);
                 }
             }
         }
