@@ -88,22 +88,43 @@ __global__ void k_back_out(const float* __restrict__ dy, const __nv_bfloat16* __
     dZ2[idx] = Z2[idx] > 0.f ? dy[b] * bf(w3, n) : 0.f;
 }
 
-// dW[n][k] = sum_b D[b][n] A'[b][k] (A' standardised input when mu != null), db[n] = sum_b D[b][n].
-__global__ void k_wgrad(const float* __restrict__ D, const float* __restrict__ A, int B, int N, int K,
-                        const float* __restrict__ mu, const float* __restrict__ inv_sd, float* __restrict__ dW,
-                        float* __restrict__ db) {
-    long long idx = (long long)blockIdx.x * blockDim.x + threadIdx.x;
-    long long total = (long long)N * (K + 1);
-    if (idx >= total) return;
-    int n = (int)(idx / (K + 1)), k = (int)(idx - (long long)n * (K + 1));
-    float s = 0.f;
-    if (k == K) {
-        for (int b = 0; b < B; ++b) s += D[(long long)b * N + n];
-        db[n] = s;
-    } else {
-        const float m = mu ? mu[k] : 0.f, is = mu ? inv_sd[k] : 1.f;
-        for (int b = 0; b < B; ++b) s = fmaf(D[(long long)b * N + n], (A[(long long)b * K + k] - m) * is, s);
-        dW[(long long)n * K + k] = s;
+// Gradient of the output layer (one output): dw[k] = sum_b D[b] A[b][k],
+// db = sum_b D[b], the batch cut into WG_CHUNKS chunks.  Block c sums its
+// chunk's rows -- the 8 warps take rows b, b + 8, ..., the lanes consecutive k,
+// so every row of A is read coalesced -- into part[c][0..K]; k_wgrad1_sum adds
+// the chunks in a fixed order (the result does not depend on scheduling).
+constexpr int WG_CHUNKS = 64;
+__global__ void k_wgrad1_part(const float* __restrict__ D, const float* __restrict__ A, int B, int K,
+                              float* __restrict__ part) {
+    constexpr int NW = MLP_THREADS / 32;
+    __shared__ float sh[NW][33];
+    const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+    const int b0 = (int)((long long)B * blockIdx.x / gridDim.x);
+    const int b1 = (int)((long long)B * (blockIdx.x + 1) / gridDim.x);
+    for (int k0 = 0; k0 <= K; k0 += 32) {
+        const int k = k0 + lane;
+        float acc = 0.f;
+        for (int b = b0 + w; b < b1; b += NW) {
+            const float a = k < K ? A[(long long)b * K + k] : (k == K ? 1.f : 0.f);
+            acc = fmaf(D[b], a, acc);
+        }
+        sh[w][lane] = acc;
+        __syncthreads();
+        if (w == 0 && k <= K) {
+            float t = 0.f;
+            for (int i = 0; i < NW; ++i) t += sh[i][lane];
+            part[(long long)blockIdx.x * (K + 1) + k] = t;
+        }
+        __syncthreads();
+    }
+}
+__global__ void k_wgrad1_sum(const float* __restrict__ part, int G, int K, float* __restrict__ dw,
+                             float* __restrict__ db) {
+    for (int k = blockIdx.x * blockDim.x + threadIdx.x; k <= K; k += gridDim.x * blockDim.x) {
+        float t = 0.f;
+        for (int c = 0; c < G; ++c) t += part[(long long)c * (K + 1) + k];
+        if (k < K) dw[k] = t;
+        else *db = t;
     }
 }
 
@@ -286,6 +307,7 @@ struct qbvm_mlp {
     float *Z1 = nullptr, *H1 = nullptr, *Z2 = nullptr, *H2 = nullptr, *y = nullptr, *dy = nullptr, *dZ1 = nullptr,
           *dZ2 = nullptr;
     double* loss = nullptr;
+    float* wpart = nullptr;   // output-layer gradient partial sums [WG_CHUNKS][width + 1]
     long long step = 0;
     std::vector<void*> allocs;
 };
@@ -350,8 +372,9 @@ int mlp_grads(qbvm_mlp_t* h, const float* x, const float* t, int B, cudaStream_t
     k_dense_out<<<nblk((long long)B * 32), MLP_THREADS, 0, s>>>(h->H2, h->pb + h->ow3, h->p + h->ob3, B, N, h->y);
     k_mse<<<nblk(B), MLP_THREADS, 0, s>>>(h->y, t, B, h->dy, h->loss);
     // w3, b3: dW = dy^T H2 (one output row)
-    k_wgrad<<<nblk((long long)(N + 1)), MLP_THREADS, 0, s>>>(h->dy, h->H2, B, 1, N, nullptr, nullptr, h->g + h->ow3,
-                                                            h->g + h->ob3);
+    k_wgrad1_part<<<WG_CHUNKS, MLP_THREADS, 0, s>>>(h->dy, h->H2, B, N, h->wpart);
+    k_wgrad1_sum<<<nblk((long long)(N + 1)), MLP_THREADS, 0, s>>>(h->wpart, WG_CHUNKS, N, h->g + h->ow3,
+                                                                h->g + h->ob3);
     k_back_out<<<nblk((long long)B * N), MLP_THREADS, 0, s>>>(h->dy, h->pb + h->ow3, h->Z2, B, N, h->dZ2);
     // dW2 = dZ2^T H1 (N x N, reduction over the batch), db2 = column sums of dZ2
     if (launch_mma<false, EPI_STORE>(N, N, B, h->dZ2, 1, N, nullptr, nullptr, h->H1, N, 1, nullptr, nullptr,
@@ -412,6 +435,7 @@ int qbvm_mlp_create(int in_dim, int width, int max_batch, unsigned long long see
     if (!rc) rc = m_alloc(h, &h->dZ2, (size_t)max_batch * N);
     if (!rc) rc = m_alloc(h, &h->y, (size_t)max_batch);
     if (!rc) rc = m_alloc(h, &h->dy, (size_t)max_batch);
+    if (!rc) rc = m_alloc(h, &h->wpart, (size_t)WG_CHUNKS * (N + 1));
     if (!rc) rc = m_alloc(h, &h->loss, 1);
     if (!rc && cudaMemcpy(h->p, init.data(), sizeof(float) * init.size(), cudaMemcpyHostToDevice) != cudaSuccess)
         rc = QBVM_ERR_CUDA;
