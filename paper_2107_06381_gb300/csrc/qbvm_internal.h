@@ -186,9 +186,12 @@ cudaError_t launch_classify(const double* x, long long n, int* flags, cudaStream
 // f FP64 (F, or g for the delta right-hand side); writes r.hi (FP32) to r_out
 // and sums[2] = (||r||^2, ||f||^2).
 // fnorm: also sum ||f||^2 (sums[1]); otherwise sums[1] is not meaningful.
+// rscale > 0 (with fnorm 0; 2D / 3D): ||r||^2 summed as an FP32 sum of
+// (r rscale)^2, rscale a power of two near 1 / rms(f) (+Inf when that sum
+// overflows, i.e. r beyond ~1e19 rms(f)).
 cudaError_t launch_residual_df(const void* y_df, const double* f, int delta_rhs, const Tables& tb,
                                const double h2inv[3], float* r_out, double* partials, int nblocks, double* sums,
-                               int fnorm, cudaStream_t s);
+                               int fnorm, cudaStream_t s, float rscale = 0.f);
 // In place: double-float (float2) array of n values -> FP64 array.
 cudaError_t launch_df_to_double(void* buf, long long n, cudaStream_t s);
 

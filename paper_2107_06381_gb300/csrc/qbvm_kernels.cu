@@ -1289,12 +1289,17 @@ k_residual_df(const float2* __restrict__ y, const double* __restrict__ f, int de
 // split by truncation (df_from_double_trunc), 6 y is an exact product pair,
 // and ||f||^2 is summed only when `fnorm` is set (the first residual of a
 // solve).  Bounded to 64 registers (4 CTAs per SM): the 3D stencil took 97
-// and ran at a quarter of the warp slots.
-template <bool EQ, int DIMS>
+// and ran at a quarter of the warp slots.  FAST (the residuals after the
+// first, whose ||f|| is known): ||r||^2 as a plain FP32 sum of (r rscale)^2,
+// rscale the power of two near 1 / rms(f), instead of the scaled sum that
+// follows the magnitudes (about 13 instructions per term); the block's sum is
+// returned times inv_s2 = 1 / rscale^2 (exact).
+template <bool EQ, int DIMS, bool FAST = false>
 __device__ __forceinline__ void residual_df4_body(const float2* __restrict__ y, const double* __restrict__ f,
                                                   int delta_rhs, int nt, int nx, int ny, int nz, const DfCoef& k,
                                                   double f0_scale, int fnorm, float* __restrict__ r_out,
-                                                  long long blk, long long nblk, double* part2) {
+                                                  long long blk, long long nblk, double* part2,
+                                                  float rscale = 0.f, double inv_s2 = 0.0) {
     __shared__ double sh[32];
     const long long Nx = (long long)nx * ny * nz, N = (long long)nt * Nx, pl = (long long)nx * ny;
     const long long ngroups = (N + 3) >> 2;
@@ -1332,6 +1337,7 @@ __device__ __forceinline__ void residual_df4_body(const float2* __restrict__ y, 
     const float4* y4 = reinterpret_cast<const float4*>(y);
     const double2* f2 = reinterpret_cast<const double2*>(f);
     ScaledSsq nr, nf;
+    float nr2 = 0.f;
     for (long long gb = wid * 32; gb < ngroups; gb += nw * 32) {
         const long long g = gb + lane, i0 = 4 * g;
         const bool act = g < ngroups, full = act && i0 + 3 < N;
@@ -1421,8 +1427,13 @@ __device__ __forceinline__ void residual_df4_body(const float2* __restrict__ y, 
             const dfloat r = df_sub_un(fv, Ay);
             const float rh = r.hi + r.lo;
             rv[e] = rh;
-            nr.add(rh);
-            if (fnorm) nf.add(fv.hi);
+            if (FAST) {
+                const float rs = rh * rscale;
+                nr2 = fmaf(rs, rs, nr2);
+            } else {
+                nr.add(rh);
+                if (fnorm) nf.add(fv.hi);
+            }
         }
         if (full) {
             reinterpret_cast<float4*>(r_out)[g] = make_float4(rv[0], rv[1], rv[2], rv[3]);
@@ -1443,6 +1454,21 @@ __device__ __forceinline__ void residual_df4_body(const float2* __restrict__ y, 
         if (c) iz -= nz;
         t += St + c;
     }
+    if (FAST) {
+        // warp sums in FP32, the warps' sums in FP64 by one thread
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) nr2 += __shfl_xor_sync(0xffffffffu, nr2, o);
+        __shared__ float shf[RES_THREADS / 32];
+        if (lane == 0) shf[threadIdx.x >> 5] = nr2;
+        __syncthreads();
+        if (threadIdx.x == 0) {
+            double a = 0.0;
+            for (int i = 0; i < (int)(blockDim.x >> 5); ++i) a += (double)shf[i];
+            part2[0] = a * inv_s2;
+            part2[1] = 0.0;
+        }
+        return;
+    }
     double a = block_sum(nr.value(), sh);
     double b = block_sum(nf.value(), sh);
     if (threadIdx.x == 0) {
@@ -1451,14 +1477,15 @@ __device__ __forceinline__ void residual_df4_body(const float2* __restrict__ y, 
     }
 }
 
-template <bool EQ, int DIMS>
+template <bool EQ, int DIMS, bool FAST>
 __global__ void __launch_bounds__(RES_THREADS, 4)
 k_residual_df4(const float2* __restrict__ y, const double* __restrict__ f, int delta_rhs, int nt, int nx, int ny,
-               int nz, DfCoef k, double f0_scale, int fnorm, float* __restrict__ r_out, double* partials) {
+               int nz, DfCoef k, double f0_scale, int fnorm, float* __restrict__ r_out, double* partials,
+               float rscale, double inv_s2) {
     pdl_trigger();
     pdl_wait();
-    residual_df4_body<EQ, DIMS>(y, f, delta_rhs, nt, nx, ny, nz, k, f0_scale, fnorm, r_out, blockIdx.x, gridDim.x,
-                                partials + 2 * (long long)blockIdx.x);
+    residual_df4_body<EQ, DIMS, FAST>(y, f, delta_rhs, nt, nx, ny, nz, k, f0_scale, fnorm, r_out, blockIdx.x,
+                                      gridDim.x, partials + 2 * (long long)blockIdx.x, rscale, inv_s2);
 }
 
 // `count` instances back to back, bpi blocks per instance: block (b, j) runs
@@ -1549,7 +1576,7 @@ static dfloat df_const(double c) {
 
 cudaError_t launch_residual_df(const void* y_df, const double* f, int delta_rhs, const Tables& tb,
                                const double h2inv[3], float* r_out, double* partials, int nblocks, double* sums,
-                               int fnorm, cudaStream_t s) {
+                               int fnorm, cudaStream_t s, float rscale) {
     DfCoef k;
     const double it = 1.0 / tb.tau;
     k.ct = df_const(it);
@@ -1578,15 +1605,25 @@ cudaError_t launch_residual_df(const void* y_df, const double* f, int delta_rhs,
         const float2* yy = reinterpret_cast<const float2*>(y_df);
         const double fs = -tb.omega * it;
         const int nx = tb.n[0], ny = tb.n[1], nz = tb.n[2];
-        if (tb.dim == 1) {
-            QBVM_PDL(k_residual_df4<true, 1>, (unsigned)nb, RES_THREADS, 0, s, yy, f, delta_rhs, tb.nt, nx, ny, nz, k, fs, fnorm, r_out, partials);
-        } else if (tb.dim == 2) {
-            if (eq) QBVM_PDL(k_residual_df4<true, 2>, (unsigned)nb, RES_THREADS, 0, s, yy, f, delta_rhs, tb.nt, nx, ny, nz, k, fs, fnorm, r_out, partials);
-            else QBVM_PDL(k_residual_df4<false, 2>, (unsigned)nb, RES_THREADS, 0, s, yy, f, delta_rhs, tb.nt, nx, ny, nz, k, fs, fnorm, r_out, partials);
+        const bool fast = rscale > 0.f && !fnorm;
+        const double is2 = fast ? 1.0 / ((double)rscale * (double)rscale) : 0.0;
+#define QBVM_RD4(E, D)                                                                                          \
+        do {                                                                                                    \
+            if (fast)                                                                                           \
+                QBVM_PDL(k_residual_df4<E, D, true>, (unsigned)nb, RES_THREADS, 0, s, yy, f, delta_rhs, tb.nt, nx,  \
+                         ny, nz, k, fs, fnorm, r_out, partials, rscale, is2);                                  \
+            else                                                                                                \
+                QBVM_PDL(k_residual_df4<E, D, false>, (unsigned)nb, RES_THREADS, 0, s, yy, f, delta_rhs, tb.nt, nx, \
+                         ny, nz, k, fs, fnorm, r_out, partials, rscale, is2);                                  \
+        } while (0)
+        if (tb.dim == 2) {
+            if (eq) QBVM_RD4(true, 2);
+            else QBVM_RD4(false, 2);
         } else {
-            if (eq) QBVM_PDL(k_residual_df4<true, 3>, (unsigned)nb, RES_THREADS, 0, s, yy, f, delta_rhs, tb.nt, nx, ny, nz, k, fs, fnorm, r_out, partials);
-            else QBVM_PDL(k_residual_df4<false, 3>, (unsigned)nb, RES_THREADS, 0, s, yy, f, delta_rhs, tb.nt, nx, ny, nz, k, fs, fnorm, r_out, partials);
+            if (eq) QBVM_RD4(true, 3);
+            else QBVM_RD4(false, 3);
         }
+#undef QBVM_RD4
         cudaError_t e = cudaGetLastError();
         if (e != cudaSuccess) return e;
         QBVM_PDL(k_reduce_pairs, 1, 1024, 0, s, partials, (int)nb, sums);

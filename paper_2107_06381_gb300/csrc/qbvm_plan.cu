@@ -33,6 +33,7 @@ struct qbvm_plan {
     double* ghat = nullptr;       // 2D/3D delta rhs: DST of g (Nx)
     double* wreal = nullptr;      // 2D/3D general rhs with n0_only: [nt][Nx]
     double* partials = nullptr;   // residual partial sums
+    float rscale = 0.f;           // 2^-k, 2^k <= rms(f) of the solve in progress (refinement residual norms)
     double* sums = nullptr;       // residual sums (2)
     int nres = 0;
     double* stage_in = nullptr;   // host-pointer staging
@@ -443,12 +444,25 @@ int fp32_solve(qbvm_plan_t* p, const void* rhs, int rhs_fp64, int delta, void* y
 int residual_norm_df(qbvm_plan_t* p, const void* ydf, const double* in, int delta, double* rel, double* fnorm2,
                      cudaStream_t s) {
     const int want_f = *fnorm2 < 0;
-    { Span sp_(p, "residual_df", s); CK(qbvm::launch_residual_df(ydf, in, delta, p->tb, p->h2inv, p->f32, p->partials, p->nres, p->sums, want_f, s)); }
+    // after the first residual ||r||^2 is a plain FP32 sum of (r / 2^k)^2, 2^k the
+    // power of two at or below rms(f) (2D / 3D; 1D sums in FP64)
+    const float rscale = want_f ? 0.f : p->rscale;
+    { Span sp_(p, "residual_df", s); CK(qbvm::launch_residual_df(ydf, in, delta, p->tb, p->h2inv, p->f32, p->partials, p->nres, p->sums, want_f, s, rscale)); }
     double h[2] = {0, 0};
     CK(cudaMemcpyAsync(h, p->sums, sizeof(h), cudaMemcpyDeviceToHost, s));
     CK(cudaStreamSynchronize(s));
-    if (want_f) *fnorm2 = h[1];
-    else h[1] = *fnorm2;
+    if (want_f) {
+        *fnorm2 = h[1];
+        const double cnt = (double)p->tb.Nx * (delta ? 1 : p->tb.nt);
+        const double rms = std::sqrt(h[1] / cnt);
+        p->rscale = (std::isfinite(rms) && rms > 1e-30 && rms < 1e30) ? (float)std::ldexp(1.0, -(int)std::floor(std::log2(rms))) : 0.f;
+    } else {
+        h[1] = *fnorm2;
+    }
+    if (!want_f && rscale > 0.f && h[0] == INFINITY && std::isfinite(h[1])) {
+        *rel = INFINITY;                              // (r / 2^k)^2 beyond the FP32 range: the iteration diverges
+        return QBVM_OK;
+    }
     if (!std::isfinite(h[0]) || !std::isfinite(h[1])) return QBVM_ERR_NONFINITE;
     *rel = h[1] > 0 ? std::sqrt(h[0] / h[1]) : std::sqrt(h[0]);
     return QBVM_OK;
