@@ -1294,22 +1294,22 @@ k_residual_df(const float2* __restrict__ y, const double* __restrict__ f, int de
 // rscale the power of two near 1 / rms(f), instead of the scaled sum that
 // follows the magnitudes (about 13 instructions per term); the block's sum is
 // returned times inv_s2 = 1 / rscale^2 (exact).
-template <bool EQ, int DIMS, bool FAST = false>
+template <bool EQ, int DIMS, bool FAST = false, typename IT = long long>
 __device__ __forceinline__ void residual_df4_body(const float2* __restrict__ y, const double* __restrict__ f,
                                                   int delta_rhs, int nt, int nx, int ny, int nz, const DfCoef& k,
                                                   double f0_scale, int fnorm, float* __restrict__ r_out,
-                                                  long long blk, long long nblk, double* part2,
+                                                  IT blk, IT nblk, double* part2,
                                                   float rscale = 0.f, double inv_s2 = 0.0) {
     __shared__ double sh[32];
-    const long long Nx = (long long)nx * ny * nz, N = (long long)nt * Nx, pl = (long long)nx * ny;
-    const long long ngroups = (N + 3) >> 2;
+    const IT Nx = (IT)nx * ny * nz, N = (IT)nt * Nx, pl = (IT)nx * ny;
+    const IT ngroups = (N + 3) >> 2;
     const int lane = threadIdx.x & 31;
-    const long long wid = (blk * blockDim.x + threadIdx.x) >> 5;
-    const long long nw = (nblk * blockDim.x) >> 5;
+    const IT wid = (blk * blockDim.x + threadIdx.x) >> 5;
+    const IT nw = (nblk * blockDim.x) >> 5;
     // (t, z, y, x) of a flat index: 32-bit divisions when the index fits (a
     // 64-bit division is a long software sequence, and short-lived threads --
     // small instances of a batch -- pay it for few elements)
-    auto split = [&](long long i, int& t, int& z, int& yy, int& x) {
+    auto split = [&](IT i, int& t, int& z, int& yy, int& x) {
         if (i < 0x7fffffffLL && Nx < 0x7fffffffLL) {
             const unsigned ui = (unsigned)i, uN = (unsigned)Nx, up = (unsigned)pl, ux = (unsigned)nx;
             const unsigned ut = ui / uN;
@@ -1324,22 +1324,22 @@ __device__ __forceinline__ void residual_df4_body(const float2* __restrict__ y, 
             return;
         }
         t = (int)(i / Nx);
-        long long r = i - (long long)t * Nx;
+        IT r = i - (IT)t * Nx;
         z = (int)(r / pl);
-        r -= (long long)z * pl;
+        r -= (IT)z * pl;
         yy = (int)(r / nx);
-        x = (int)(r - (long long)yy * nx);
+        x = (int)(r - (IT)yy * nx);
     };
     int t, iz, iy, ix, St, Sz, Sy, Sx;
     split((wid * 32 + lane) * 4, t, iz, iy, ix);
     split(nw * 128, St, Sz, Sy, Sx);
-    auto ld = [&](long long i) { float2 v = y[i]; return dfloat{v.x, v.y}; };
+    auto ld = [&](IT i) { float2 v = y[i]; return dfloat{v.x, v.y}; };
     const float4* y4 = reinterpret_cast<const float4*>(y);
     const double2* f2 = reinterpret_cast<const double2*>(f);
     ScaledSsq nr, nf;
     float nr2 = 0.f;
-    for (long long gb = wid * 32; gb < ngroups; gb += nw * 32) {
-        const long long g = gb + lane, i0 = 4 * g;
+    for (IT gb = wid * 32; gb < ngroups; gb += nw * 32) {
+        const IT g = gb + lane, i0 = 4 * g;
         const bool act = g < ngroups, full = act && i0 + 3 < N;
         dfloat yv[4];
         if (full) {
@@ -1385,11 +1385,11 @@ __device__ __forceinline__ void residual_df4_body(const float2* __restrict__ y, 
                     }
                 }
             }
-            const long long idx = i0 + e;
+            const IT idx = i0 + e;
             rv[e] = 0.f;
             if (!(act && idx < N)) continue;
             const dfloat yc = yv[e];
-            dfloat pv = et > 0 ? ld(idx - Nx) : ld(idx + (long long)(nt - 1) * Nx);
+            dfloat pv = et > 0 ? ld(idx - Nx) : ld(idx + (IT)(nt - 1) * Nx);
             if (et == 0) pv = df_mul_un(k.omega, pv);
             dfloat Ay = df_mul_un(k.ct, df_sub_un(yc, pv));
             const dfloat L = e > 0 ? yv[e - 1] : xl, R = e < 3 ? yv[e + 1] : xr;
@@ -1418,13 +1418,15 @@ __device__ __forceinline__ void residual_df4_body(const float2* __restrict__ y, 
                 if (DIMS >= 2) Ay = df_add_un(Ay, df_mul_un(k.cy, df_sub_un(y2, df_add_un(ys, yn))));
                 if (DIMS >= 3) Ay = df_add_un(Ay, df_mul_un(k.cz, df_sub_un(y2, df_add_un(zd, zu))));
             }
-            dfloat fv = zero;
-            if (delta_rhs) {
-                if (et == 0) fv = df_from_double_trunc(f0_scale * f[((long long)ez * ny + ey) * nx + ex]);
+            // f - A y; with the delta right-hand side f is zero past level 0
+            dfloat fv = zero, r;
+            if (delta_rhs && et != 0) {
+                r = dfloat{-Ay.hi, -Ay.lo};
             } else {
-                fv = df_from_double_trunc(fd[e]);
+                if (delta_rhs) fv = df_from_double_trunc(f0_scale * f[((IT)ez * ny + ey) * nx + ex]);
+                else fv = df_from_double_trunc(fd[e]);
+                r = df_sub_un(fv, Ay);
             }
-            const dfloat r = df_sub_un(fv, Ay);
             const float rh = r.hi + r.lo;
             rv[e] = rh;
             if (FAST) {
@@ -1477,20 +1479,24 @@ __device__ __forceinline__ void residual_df4_body(const float2* __restrict__ y, 
     }
 }
 
-template <bool EQ, int DIMS, bool FAST>
+// IT: the index type, int when the array has fewer than 2^31 values (the
+// 64-bit index arithmetic had cost 22 % more instructions and 8 % more time
+// on 127^3 x 128).
+template <bool EQ, int DIMS, bool FAST, typename IT>
 __global__ void __launch_bounds__(RES_THREADS, 4)
 k_residual_df4(const float2* __restrict__ y, const double* __restrict__ f, int delta_rhs, int nt, int nx, int ny,
                int nz, DfCoef k, double f0_scale, int fnorm, float* __restrict__ r_out, double* partials,
                float rscale, double inv_s2) {
     pdl_trigger();
     pdl_wait();
-    residual_df4_body<EQ, DIMS, FAST>(y, f, delta_rhs, nt, nx, ny, nz, k, f0_scale, fnorm, r_out, blockIdx.x,
-                                      gridDim.x, partials + 2 * (long long)blockIdx.x, rscale, inv_s2);
+    residual_df4_body<EQ, DIMS, FAST, IT>(y, f, delta_rhs, nt, nx, ny, nz, k, f0_scale, fnorm, r_out,
+                                          (IT)blockIdx.x, (IT)gridDim.x, partials + 2 * (long long)blockIdx.x,
+                                          rscale, inv_s2);
 }
 
 // `count` instances back to back, bpi blocks per instance: block (b, j) runs
 // the instance's residual with its own omega (and f^0 = -omega_b g_b / tau).
-template <bool EQ, int DIMS>
+template <bool EQ, int DIMS, typename IT>
 __global__ void __launch_bounds__(RES_THREADS, 4)
 k_residual_df4_batched(const float2* __restrict__ y, const double* __restrict__ f, int delta_rhs, int nt, int nx,
                        int ny, int nz, DfCoef k, const float2* __restrict__ omega_df,
@@ -1503,9 +1509,9 @@ k_residual_df4_batched(const float2* __restrict__ y, const double* __restrict__ 
     DfCoef kb = k;
     const float2 om = omega_df[b];
     kb.omega = dfloat{om.x, om.y};
-    residual_df4_body<EQ, DIMS>(y + b * per, f + b * (delta_rhs ? Nx : per), delta_rhs, nt, nx, ny, nz, kb,
-                                -omega64[b] * inv_tau, fnorm, r_out + b * per, j, bpi,
-                                partials + 2 * (long long)blockIdx.x);
+    residual_df4_body<EQ, DIMS, false, IT>(y + b * per, f + b * (delta_rhs ? Nx : per), delta_rhs, nt, nx, ny, nz, kb,
+                                           -omega64[b] * inv_tau, fnorm, r_out + b * per, (IT)j, (IT)bpi,
+                                           partials + 2 * (long long)blockIdx.x);
 }
 
 // sums[2 b], sums[2 b + 1] = the instance's partial pairs summed (one warp each).
@@ -1607,14 +1613,20 @@ cudaError_t launch_residual_df(const void* y_df, const double* f, int delta_rhs,
         const int nx = tb.n[0], ny = tb.n[1], nz = tb.n[2];
         const bool fast = rscale > 0.f && !fnorm;
         const double is2 = fast ? 1.0 / ((double)rscale * (double)rscale) : 0.0;
-#define QBVM_RD4(E, D)                                                                                          \
+        const bool i32 = (long long)tb.nt * tb.Nx < 0x7ffff000LL;
+#define QBVM_RD4F(E, D, F)                                                                                      \
         do {                                                                                                    \
-            if (fast)                                                                                           \
-                QBVM_PDL(k_residual_df4<E, D, true>, (unsigned)nb, RES_THREADS, 0, s, yy, f, delta_rhs, tb.nt, nx,  \
+            if (i32)                                                                                            \
+                QBVM_PDL(k_residual_df4<E, D, F, int>, (unsigned)nb, RES_THREADS, 0, s, yy, f, delta_rhs, tb.nt, nx,\
                          ny, nz, k, fs, fnorm, r_out, partials, rscale, is2);                                  \
             else                                                                                                \
-                QBVM_PDL(k_residual_df4<E, D, false>, (unsigned)nb, RES_THREADS, 0, s, yy, f, delta_rhs, tb.nt, nx, \
-                         ny, nz, k, fs, fnorm, r_out, partials, rscale, is2);                                  \
+                QBVM_PDL(k_residual_df4<E, D, F, long long>, (unsigned)nb, RES_THREADS, 0, s, yy, f, delta_rhs,     \
+                         tb.nt, nx, ny, nz, k, fs, fnorm, r_out, partials, rscale, is2);                       \
+        } while (0)
+#define QBVM_RD4(E, D)                                                                                          \
+        do {                                                                                                    \
+            if (fast) QBVM_RD4F(E, D, true);                                                                    \
+            else QBVM_RD4F(E, D, false);                                                                        \
         } while (0)
         if (tb.dim == 2) {
             if (eq) QBVM_RD4(true, 2);
@@ -1624,6 +1636,7 @@ cudaError_t launch_residual_df(const void* y_df, const double* f, int delta_rhs,
             else QBVM_RD4(false, 3);
         }
 #undef QBVM_RD4
+#undef QBVM_RD4F
         cudaError_t e = cudaGetLastError();
         if (e != cudaSuccess) return e;
         QBVM_PDL(k_reduce_pairs, 1, 1024, 0, s, partials, (int)nb, sums);
@@ -1669,9 +1682,16 @@ cudaError_t launch_residual_df_batched(const void* y_df, const double* f, int de
     const float2* yy = reinterpret_cast<const float2*>(y_df);
     const int nx = tb.n[0], ny = tb.n[1], nz = tb.n[2];
     const unsigned nb = (unsigned)(count * bpi);
+    const bool i32 = (long long)tb.nt * tb.Nx < 0x7ffff000LL;       // one instance's values
 #define QBVM_RDB(E, D)                                                                                        \
-    QBVM_PDL(k_residual_df4_batched<E, D>, nb, RES_THREADS, 0, s, yy, f, delta_rhs, tb.nt, nx, ny, nz, k, omega_df, \
-             omega64, it, fnorm, bpi, r_out, partials)
+    do {                                                                                                      \
+        if (i32)                                                                                              \
+            QBVM_PDL(k_residual_df4_batched<E, D, int>, nb, RES_THREADS, 0, s, yy, f, delta_rhs, tb.nt, nx, ny, nz, \
+                     k, omega_df, omega64, it, fnorm, bpi, r_out, partials);                                   \
+        else                                                                                                  \
+            QBVM_PDL(k_residual_df4_batched<E, D, long long>, nb, RES_THREADS, 0, s, yy, f, delta_rhs, tb.nt, nx,    \
+                     ny, nz, k, omega_df, omega64, it, fnorm, bpi, r_out, partials);                           \
+    } while (0)
     if (tb.dim == 1) QBVM_RDB(true, 1);
     else if (tb.dim == 2) { if (eq) QBVM_RDB(true, 2); else QBVM_RDB(false, 2); }
     else { if (eq) QBVM_RDB(true, 3); else QBVM_RDB(false, 3); }
