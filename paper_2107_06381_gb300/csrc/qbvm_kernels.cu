@@ -342,19 +342,21 @@ k_time_solve_batched(const double* in, double* out, long long Nx, int lh, int lw
 // its own threads.  With the delta right-hand side the forward transform of
 // f^0 e_0 is the constant f^0 and is not computed.
 template <int LH> struct TsCfg;
-template <> struct TsCfg<8> { static constexpr int N1 = 16, N2 = 16, BS = 17, FB = 272, RS = 18; };
-template <> struct TsCfg<7> { static constexpr int N1 = 16, N2 = 8, BS = 9, FB = 152, RS = 20; };
-template <> struct TsCfg<6> { static constexpr int N1 = 8, N2 = 8, BS = 9, FB = 72, RS = 20; };
-template <> struct TsCfg<5> { static constexpr int N1 = 8, N2 = 4, BS = 5, FB = 52, RS = 24; };
-constexpr int TS_MODES = 16;     // spatial modes per CTA
+// TS_MODES spatial modes per CTA: 32 (128-byte row segments in the load and
+// store phases) up to H = 64, where it measured 9 % faster on 127^3 x 128 than
+// 16; 16 for H = 128, 256, where 32 measured 3 % slower on 255^2 x 256.
+template <> struct TsCfg<8> { static constexpr int N1 = 16, N2 = 16, BS = 17, FB = 272, RS = 18, TS_MODES = 16; };
+template <> struct TsCfg<7> { static constexpr int N1 = 16, N2 = 8, BS = 9, FB = 152, RS = 20, TS_MODES = 16; };
+template <> struct TsCfg<6> { static constexpr int N1 = 8, N2 = 8, BS = 9, FB = 72, RS = 36, TS_MODES = 32; };
+template <> struct TsCfg<5> { static constexpr int N1 = 8, N2 = 4, BS = 5, FB = 52, RS = 40, TS_MODES = 32; };
 
 // The staging tile [nt][RS] and the per-mode transpose buffers share one
 // region: the tile is free between the first reads and the final writes.
 template <int LH>
 constexpr size_t ts_region_bytes() {
-    return (size_t)(2 << LH) * TsCfg<LH>::RS * sizeof(float) > (size_t)TS_MODES * TsCfg<LH>::FB * sizeof(float2)
+    return (size_t)(2 << LH) * TsCfg<LH>::RS * sizeof(float) > (size_t)TsCfg<LH>::TS_MODES * TsCfg<LH>::FB * sizeof(float2)
                ? (size_t)(2 << LH) * TsCfg<LH>::RS * sizeof(float)
-               : (size_t)TS_MODES * TsCfg<LH>::FB * sizeof(float2);
+               : (size_t)TsCfg<LH>::TS_MODES * TsCfg<LH>::FB * sizeof(float2);
 }
 template <int LH>
 constexpr size_t ts_reg_smem() { return (size_t)4 * (1 << LH) * sizeof(float2) + ts_region_bytes<LH>(); }
@@ -368,8 +370,8 @@ __device__ __forceinline__ void time_solve_reg_tile(const float* in, float* out,
                                                     const float* __restrict__ lamtau, float cnorm, float rho_h,
                                                     float rho_hinv, int delta_rhs, int n0_only, long long tile) {
     using G = TsCfg<LH>;
-    constexpr int H = 1 << LH, NT = 2 * H, N1 = G::N1, N2 = G::N2, T = N2, NTH = TS_MODES * T, Q = N1 / T;
-    constexpr int RS = G::RS, RSTEP = NTH / TS_MODES;
+    constexpr int H = 1 << LH, NT = 2 * H, N1 = G::N1, N2 = G::N2, T = N2, NTH = TsCfg<LH>::TS_MODES * T, Q = N1 / T;
+    constexpr int RS = G::RS, RSTEP = NTH / TsCfg<LH>::TS_MODES;
     extern __shared__ __align__(16) unsigned char smem_raw[];
     float2* stw = reinterpret_cast<float2*>(smem_raw);
     float2* sgp = stw + H;
@@ -386,9 +388,9 @@ __device__ __forceinline__ void time_solve_reg_tile(const float* in, float* out,
         sak[i] = ak[i];
     }
     pdl_wait();                                                        // the input is a predecessor's output
-    const long long l0 = tile * TS_MODES;
+    const long long l0 = tile * TsCfg<LH>::TS_MODES;
     {   // load phase: rows of TS_MODES consecutive modes, a batch of loads in flight per thread
-        const int cc = tid % TS_MODES, r0 = tid / TS_MODES;
+        const int cc = tid % TsCfg<LH>::TS_MODES, r0 = tid / TsCfg<LH>::TS_MODES;
         const bool ok = l0 + cc < Nx;
         const float* src = in + l0 + cc;
         const int rows = delta_rhs ? 1 : NT;
@@ -493,7 +495,7 @@ __device__ __forceinline__ void time_solve_reg_tile(const float* in, float* out,
     }
     __syncthreads();
     {   // store phase
-        const int cc = tid % TS_MODES, r0 = tid / TS_MODES;
+        const int cc = tid % TsCfg<LH>::TS_MODES, r0 = tid / TsCfg<LH>::TS_MODES;
         if (l0 + cc < Nx) {
             float* dst = out + l0 + cc;
             const int rows = n0_only ? 1 : NT;
@@ -503,7 +505,7 @@ __device__ __forceinline__ void time_solve_reg_tile(const float* in, float* out,
 }
 
 template <int LH>
-__global__ void __launch_bounds__(TS_MODES * TsCfg<LH>::N2, LH == 8 ? 4 : LH == 7 ? 8 : LH == 6 ? 10 : 20)
+__global__ void __launch_bounds__(TsCfg<LH>::TS_MODES * TsCfg<LH>::N2, LH == 8 ? 4 : LH == 7 ? 8 : LH == 6 ? 5 : 10)
 k_time_solve_reg(const float* in, float* out, long long Nx, const float2* __restrict__ tw,
                  const float2* __restrict__ gpow, const float2* __restrict__ gipw, const float2* __restrict__ ak,
                  const float* __restrict__ lamtau, float cnorm, float rho_h, float rho_hinv, int delta_rhs,
@@ -517,7 +519,7 @@ k_time_solve_reg(const float* in, float* out, long long Nx, const float2* __rest
 // in + b in_stride, writes out + b out_stride and takes the rows b of the
 // [count][H] tables gpow, gipw, ak and of cnorm, rho_h, rho_hinv.
 template <int LH>
-__global__ void __launch_bounds__(TS_MODES * TsCfg<LH>::N2, LH == 8 ? 4 : LH == 7 ? 8 : LH == 6 ? 10 : 20)
+__global__ void __launch_bounds__(TsCfg<LH>::TS_MODES * TsCfg<LH>::N2, LH == 8 ? 4 : LH == 7 ? 8 : LH == 6 ? 5 : 10)
 k_time_solve_reg_batched(const float* in, float* out, long long Nx, long long tiles, long long in_stride,
                          long long out_stride, const float2* __restrict__ tw, const float2* __restrict__ gpow,
                          const float2* __restrict__ gipw, const float2* __restrict__ ak,
@@ -537,8 +539,8 @@ static cudaError_t launch_time_solve_reg(const float* in, float* out, const Tabl
     constexpr size_t smem = ts_reg_smem<LH>();
     cudaError_t e = set_smem(kern, smem);
     if (e != cudaSuccess) return e;
-    const long long blocks = (tb.Nx + TS_MODES - 1) / TS_MODES;
-    QBVM_PDL(kern, (unsigned)blocks, TS_MODES * TsCfg<LH>::N2, smem, s, 
+    const long long blocks = (tb.Nx + TsCfg<LH>::TS_MODES - 1) / TsCfg<LH>::TS_MODES;
+    QBVM_PDL(kern, (unsigned)blocks, TsCfg<LH>::TS_MODES * TsCfg<LH>::N2, smem, s, 
         in, out, tb.Nx, reinterpret_cast<const float2*>(tb.tw_t32), reinterpret_cast<const float2*>(tb.gpow32),
         reinterpret_cast<const float2*>(tb.gipw32), reinterpret_cast<const float2*>(tb.ak32),
         reinterpret_cast<const float*>(tb.lamtau32), cnorm, (float)tb.rho_h, (float)tb.rho_hinv, delta_rhs, n0_only);
@@ -733,9 +735,9 @@ static cudaError_t launch_time_solve_reg_batched_lh(const float* in, float* out,
     constexpr size_t smem = ts_reg_smem<LH>();
     cudaError_t e = set_smem(kern, smem);
     if (e != cudaSuccess) return e;
-    const long long tiles = (tb.Nx + TS_MODES - 1) / TS_MODES;
+    const long long tiles = (tb.Nx + TsCfg<LH>::TS_MODES - 1) / TsCfg<LH>::TS_MODES;
     if (count < 1 || tiles * count > 0x7fffffffLL) return cudaErrorInvalidValue;
-    QBVM_PDL(kern, (unsigned)(tiles * count), TS_MODES * TsCfg<LH>::N2, smem, s, in, out, tb.Nx, tiles, in_stride,
+    QBVM_PDL(kern, (unsigned)(tiles * count), TsCfg<LH>::TS_MODES * TsCfg<LH>::N2, smem, s, in, out, tb.Nx, tiles, in_stride,
              out_stride, reinterpret_cast<const float2*>(tb.tw_t32), gpow, gipw, ak,
              reinterpret_cast<const float*>(tb.lamtau32), cnorm, rho_h, rho_hinv, delta_rhs, n0_only);
     return cudaGetLastError();
