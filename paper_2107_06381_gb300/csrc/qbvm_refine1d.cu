@@ -23,9 +23,12 @@
 //     path: qbvm_regdst.cuh);
 //   time solve of every sine mode (column), the half-length DFT split
 //     N1 x N2 over T = N2 threads;
-//   inverse x-DST, then y += W in double-float.
-// Then the residual overwrites W with r rounded to FP32 and a block sum of
-// ||r||^2 decides the next step.
+//   inverse x-DST, whose outputs are added to the iterate y in double-float.
+// Then the residual overwrites W with r rounded to FP32 (each thread walking
+// one column down a chunk of levels, the backward difference from registers),
+// and a block sum of ||r||^2 decides, in one thread, whether to go on.  The
+// first solve of a delta right-hand side has one nonzero level, whose DST is
+// taken by its definition over the whole CTA.
 #include <cuda_runtime.h>
 
 #include <cmath>
