@@ -359,8 +359,9 @@ int qbvm_multi_destroy(qbvm_multi_t* multi);
  * [2, 1024]; n_alpha in [1, 64].  precision: QBVM_FP64 (every stage in FP64)
  * or QBVM_FP32_REFINE (the alpha scan in FP32; the picked alpha's y^0 summed in
  * double-float, about 2^-44 per term, and the DSTs in FP64).  The FP64 scan
- * forms each 1/|d_{2m} + tau Lambda_l|^2 from an FP32 seed and two FP64
- * Newton steps (a few units in the last place; qbvm_selftest_newton_rcp).
+ * forms each 1/|d_{2m} + tau Lambda_l|^2 from an FP32 seed and one
+ * third-order FP64 step x (1 + e + e^2), e = 1 - d x (a few units in the last
+ * place; qbvm_selftest_newton_rcp).
  * The sweep holds device copies of its tables; g, z0 and y0 are caller-owned
  * device arrays that must stay valid while the sweep is used. */
 typedef struct qbvm_sweep_instance {
@@ -423,9 +424,9 @@ int qbvm_sweep_destroy(qbvm_sweep_t* sweep);
  * usable afterwards. */
 int qbvm_selftest_bounded_wait(int ctas, double* seconds, void* stream);
 /* Diagnostic of the FP64 scan's reciprocal: for n positive FP64 values d
- * (device array), the largest relative difference between the Newton
- * reciprocal the FP64 sweep uses (an FP32 seed and two FP64 Newton steps)
- * and the IEEE quotient 1/d.  Synchronises `stream`. */
+ * (device array), the largest relative difference between the reciprocal
+ * the FP64 sweep uses (an FP32 seed and one third-order FP64 step) and the
+ * IEEE quotient 1/d.  Synchronises `stream`. */
 int qbvm_selftest_newton_rcp(const double* d, long long n, double* max_rel_diff, void* stream);
 
 /* ------------------------------------------------------------------------

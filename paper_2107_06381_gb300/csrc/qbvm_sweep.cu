@@ -113,15 +113,17 @@ __device__ double block_sum_d(double v, double* sh) {
     return v;
 }
 
-// 1/d for a positive normal FP64 d, from an FP32 seed and two FP64 Newton
-// steps (Newton-Raphson on f(x) = 1/x - d: x <- x + x (1 - d x), each step
-// squaring the relative error).  The seed is the approximate FP32 reciprocal
-// of d truncated to FP32 -- the exponent rebased and the top 23 significand
-// bits kept, on the integer pipes -- widened back to FP64 exactly from its
-// bits: relative error below 2^-21, so two steps leave the rounding of the
-// last fused multiply-add (a few units in the last place).  Four FP64
-// operations instead of a division; d outside FP32's normal range (never
-// for the scan's |d_{2m} + tau Lambda|^2) takes the division.
+// 1/d for a positive normal FP64 d, from an FP32 seed and one third-order
+// FP64 step of the Newton-type iteration for f(x) = 1/x - d: with
+// e = 1 - d x, x' = x (1 + e + e^2) has 1 - d x' = e^3 (the Newton step
+// x (1 + e) squares e; one more term of the series cubes it).  The seed is the
+// approximate FP32 reciprocal of d truncated to FP32 -- the exponent rebased
+// and the top 23 significand bits kept, on the integer pipes -- widened back
+// to FP64 exactly from its bits: relative error below 2^-21, so the step leaves
+// the rounding of its last fused multiply-adds (a few units in the last
+// place).  Three FP64 operations instead of a division (two Newton steps took
+// four); d outside FP32's normal range (never for the scan's
+// |d_{2m} + tau Lambda|^2) takes the division.
 __device__ __forceinline__ double rcp_newton(double d) {
     const unsigned int H = (unsigned int)__double2hiint(d);
     const int fe = (int)((H >> 20) & 0x7FFu) - 1023 + 127;
@@ -132,10 +134,10 @@ __device__ __forceinline__ double rcp_newton(double d) {
     asm("rcp.approx.ftz.f32 %0, %1;" : "=f"(r) : "f"(f));
     const unsigned int rb = __float_as_uint(r);
     double x = __hiloint2double((int)((((rb >> 23) & 0xFFu) + 896u) << 20 | ((rb & 0x7FFFFFu) >> 3)), (int)(rb << 29));
-    double e = fma(-d, x, 1.0);
-    x = fma(x, e, x);
-    e = fma(-d, x, 1.0);
-    return fma(x, e, x);
+    // one third-order step: with e = 1 - d x, x (1 + e + e^2) leaves 1 - d x' = e^3
+    // (below 2^-63) and the roundings of the last two fused multiply-adds
+    const double e = fma(-d, x, 1.0);
+    return fma(x, fma(e, e, e), x);
 }
 
 // Diagnostic: the largest relative difference of rcp_newton from the IEEE
@@ -188,7 +190,7 @@ __device__ void spectral_tile(const SwInst& I, int tile, unsigned char* smem) {
                 R zr = d.x + lam[q];
                 if (std::is_same<R, float>::value)      // the FP32 scan: the 2-ulp fast division
                     s[q] += __fdividef((float)zr, fmaf((float)zr, (float)zr, (float)(d.y * d.y)));
-                else                                    // FP64: Newton reciprocal (4 FP64 operations)
+                else                                    // FP64: third-order reciprocal (3 FP64 operations)
                     s[q] = fma((double)zr, rcp_newton(fma((double)zr, (double)zr, (double)(d.y * d.y))), (double)s[q]);
             }
         }
