@@ -296,10 +296,11 @@ int qbvm_batch_info(const qbvm_batch_t* batch, double* alphas, long long* unknow
 int qbvm_batch_refine_info(const qbvm_batch_t* batch, int* iters, double* max_rel_residual);
 /* FP32_REFINE batches: *fused = 1 when the batch runs the whole refinement
  * in one launch, 0 when it runs the staged passes above.  The one-launch
- * form takes 1D space-first batches with (m, nt) in {(64, 64), (64, 128),
- * (128, 64)}: one CTA per instance keeps the instance's double-float iterate
- * and FP32 work array in shared memory for every step, and each instance
- * stops on its own relative residual (<= refine_tol, or DIVERGED as above);
+ * form takes 1D space-first batches with (m, nt) in {(64, 32), (64, 64),
+ * (64, 128), (128, 32), (128, 64), (256, 32)}: one CTA per instance keeps the
+ * instance's double-float iterate and FP32 work array in shared memory for
+ * every step, and each instance stops on its own relative residual
+ * (<= refine_tol, or DIVERGED as above);
  * refine_info then reports the most steps any instance took and the largest
  * final residual.  The call synchronises `stream` once, after the launch. */
 int qbvm_batch_refine_fused(const qbvm_batch_t* batch, int* fused);

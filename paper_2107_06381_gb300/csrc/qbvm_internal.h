@@ -143,7 +143,8 @@ struct Refine1dArgs {
     int* status = nullptr;
 };
 // 1 when the fused kernel takes tb's shape (1D space-first, power-of-two nt,
-// (m, nt) in {(64, 64), (64, 128), (128, 64)}, within the device's shared memory).
+// (m, nt) in {(64, 32), (64, 64), (64, 128), (128, 32), (128, 64), (256, 32)}, within
+// the device's shared memory).
 int refine1d_supported(const Tables& tb);
 cudaError_t launch_refine1d(const Tables& tb, long long count, const Refine1dArgs& a, cudaStream_t s);
 // y[l] = fac[l] * x[l], l < n

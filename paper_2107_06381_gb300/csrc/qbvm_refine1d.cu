@@ -49,6 +49,7 @@ constexpr int NTH = 256;            // threads per CTA (one instance)
 // per mode, transpose row stride BS; FB complex per mode: the stride between
 // modes' buffers that makes the transposes bank-conflict free).
 template <int LH> struct TCfg;
+template <> struct TCfg<4> { static constexpr int N1 = 4, N2 = 4, BS = 5, FB = 52; };
 template <> struct TCfg<5> { static constexpr int N1 = 8, N2 = 4, BS = 5, FB = 52; };
 template <> struct TCfg<6> { static constexpr int N1 = 8, N2 = 8, BS = 9, FB = 72; };
 
@@ -591,9 +592,12 @@ cudaError_t launch_lm_lh(long long count, const Refine1dArgs& a, cudaStream_t s)
 
 // Shared memory of a shape the kernel is built for, else 0.
 size_t shape_bytes(int lm, int lh) {
+    if (lm == 6 && lh == 4) return Layout<6, 4>::bytes;
     if (lm == 6 && lh == 5) return Layout<6, 5>::bytes;
     if (lm == 6 && lh == 6) return Layout<6, 6>::bytes;
+    if (lm == 7 && lh == 4) return Layout<7, 4>::bytes;
     if (lm == 7 && lh == 5) return Layout<7, 5>::bytes;
+    if (lm == 8 && lh == 4) return Layout<8, 4>::bytes;
     return 0;
 }
 
@@ -617,9 +621,12 @@ int refine1d_supported(const Tables& tb) {
 cudaError_t launch_refine1d(const Tables& tb, long long count, const Refine1dArgs& a, cudaStream_t s) {
     if (count < 1 || count > 0x7fffffffLL || !refine1d_supported(tb)) return cudaErrorInvalidValue;
     const int lm = tb.lpd[0], lh = tb.lnt - 1;
+    if (lm == 6 && lh == 4) return r1::launch_lm_lh<6, 4>(count, a, s);
     if (lm == 6 && lh == 5) return r1::launch_lm_lh<6, 5>(count, a, s);
     if (lm == 6 && lh == 6) return r1::launch_lm_lh<6, 6>(count, a, s);
-    return r1::launch_lm_lh<7, 5>(count, a, s);
+    if (lm == 7 && lh == 4) return r1::launch_lm_lh<7, 4>(count, a, s);
+    if (lm == 7 && lh == 5) return r1::launch_lm_lh<7, 5>(count, a, s);
+    return r1::launch_lm_lh<8, 4>(count, a, s);
 }
 
 }  // namespace qbvm

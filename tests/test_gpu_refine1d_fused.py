@@ -33,7 +33,8 @@ def gid(g):
     return f"m{g.M[0]}-nt{g.nt}"
 
 
-FUSED = [bi.Grid(1, (64,), 1.0, 0.1, 64), bi.Grid(1, (64,), 1.0, 0.1, 128), bi.Grid(1, (128,), 1.0, 0.1, 64)]
+FUSED = [bi.Grid(1, (64,), 1.0, 0.1, 64), bi.Grid(1, (64,), 1.0, 0.1, 128), bi.Grid(1, (128,), 1.0, 0.1, 64),
+         bi.Grid(1, (64,), 1.0, 0.1, 32), bi.Grid(1, (128,), 1.0, 0.1, 32), bi.Grid(1, (256,), 1.0, 0.1, 32)]
 
 
 def run(grid, form, alphas, rhs, rhs_kind, n0_only=False, tol=0.0, host=False):
@@ -61,9 +62,10 @@ def oracle(grid, form, a, rhs_b, rhs_kind):
 
 
 def test_which_shapes_take_the_fused_kernel():
-    for grid, fused in [(FUSED[0], True), (FUSED[1], True), (FUSED[2], True),
-                        (bi.Grid(1, (32,), 1.0, 0.1, 64), False), (bi.Grid(1, (64,), 1.0, 0.1, 32), False),
-                        (bi.Grid(1, (128,), 1.0, 0.1, 128), False), (bi.Grid(2, (64, 64), 1.0, 0.1, 64), False)]:
+    for grid, fused in [(g, True) for g in FUSED] + [
+            (bi.Grid(1, (32,), 1.0, 0.1, 64), False), (bi.Grid(1, (64,), 1.0, 0.1, 16), False),
+            (bi.Grid(1, (128,), 1.0, 0.1, 128), False), (bi.Grid(1, (256,), 1.0, 0.1, 64), False),
+            (bi.Grid(2, (64, 64), 1.0, 0.1, 64), False)]:
         with Q.Batch(grid.dim, grid.M, grid.L, grid.T, grid.nt, Q.FORM_PQ, alphas=[1e-3, 1e-2],
                      rhs_kind=Q.RHS_GENERAL, precision=Q.FP32_REFINE) as bt:
             assert bt.refine_fused is fused, grid
