@@ -478,10 +478,10 @@ int solve_batched_r1(qbvm_batch* bt, const double* in, double* y, int n0_only, c
     double rel = 0.0;
     for (long long b = 0; b < B; ++b) {
         const int sb = st[(size_t)b];
-        if (sb == 1) nonfinite_in = true;
-        if (sb == 1 || sb == 2) unusable = true;
-        if (sb == 3) diverged = true;
-        if (sb == 4) nonfinite = true;
+        if (sb == qbvm::R1_NONFINITE_IN) nonfinite_in = true;
+        if (sb == qbvm::R1_NONFINITE_IN || sb == qbvm::R1_RANGE) unusable = true;
+        if (sb == qbvm::R1_DIVERGED) diverged = true;
+        if (sb == qbvm::R1_NONFINITE) nonfinite = true;
         iters = std::max(iters, st[(size_t)(B + b)]);
         rel = std::max(rel, rl[(size_t)b]);
     }

@@ -123,6 +123,7 @@ int residual_blocks_per_instance(const Tables& tb);
 // final relative residual and a status (0 ok, 1 NaN / Inf in f, 2 f outside
 // the FP32 range, 3 no contraction above 1e-10 or the step cap, 4 NaN / Inf
 // residual); instances with status 1 or 2 write no y.
+enum Refine1dStatus : int { R1_OK = 0, R1_NONFINITE_IN = 1, R1_RANGE = 2, R1_DIVERGED = 3, R1_NONFINITE = 4 };
 struct Refine1dArgs {
     const double* f = nullptr;
     double* y = nullptr;

@@ -348,8 +348,10 @@ __device__ __forceinline__ void time_modes(float* W, int WS, int nmodes, float2*
     }
 }
 
-// Per-instance status written by the kernel (the host maps it to the batch's).
-enum : int { ST_OK = 0, ST_NONFINITE_IN = 1, ST_RANGE = 2, ST_DIVERGED = 3, ST_NONFINITE = 4 };
+// Per-instance status written by the kernel (Refine1dStatus; the host maps it
+// to the batch's).
+constexpr int ST_OK = R1_OK, ST_NONFINITE_IN = R1_NONFINITE_IN, ST_RANGE = R1_RANGE, ST_DIVERGED = R1_DIVERGED,
+              ST_NONFINITE = R1_NONFINITE;
 
 // FP32 sum over the CTA, returned in thread 0 (warp shuffles, then one thread
 // over the warps' sums).
