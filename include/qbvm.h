@@ -440,8 +440,11 @@ int qbvm_selftest_newton_rcp(const double* d, long long n, double* max_rel_diff,
  * per axis, 67 FP32 values: 64 bins of the radial sine spectrum of g_delta
  * (bin b = floor(64 |k| / (sqrt(2) m)) over modes k = (k_x, k_y), value
  * log10 of the mean squared sine-series coefficient in the bin), then
- * log10 delta, T and log2 nt.  g is a device array [B][m-1][m-1] (FP64),
- * delta a host array of B values, feats a device array [B][67].
+ * log10 delta, T and log2 nt; the bin values are log10(mean square +
+ * 1e-30).  The FP32 spectrum is taken of g 2^k, 2^k the power of two nearest
+ * 1/delta, and the bins corrected by the exact 2^-2k, so data of any magnitude
+ * FP64 holds gives its own features.  g is a device array [B][m-1][m-1]
+ * (FP64), delta a host array of B values, feats a device array [B][67].
  *
  * Network (qbvm_mlp_*): x -> relu(W1 x' + b1) -> relu(W2 h1 + b2) -> w3.h2 + b3,
  * x' = (x - mean)/sd (qbvm_mlp_set_norm), bfloat16 weights in the products,

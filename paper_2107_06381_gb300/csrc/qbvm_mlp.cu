@@ -28,6 +28,30 @@ namespace {
 constexpr int MLP_THREADS = 256;
 
 // ------------------------------------------------------------------ features
+//
+// The spectrum is taken of g_b 2^k_b, 2^k_b the power of two nearest 1/delta_b,
+// so that data of any magnitude FP64 holds stays inside FP32's range through
+// the FP32 DSTs and the squares; the bins are then corrected by the exact
+// log10 2^(-2 k_b), so the features are those of g_b itself.
+
+// The instance's scaling exponent k_b (0 for delta not positive and finite).
+__device__ __forceinline__ int feat_scale_exp(double d) {
+    if (!(d > 0.0) || !isfinite(d)) return 0;
+    const int k = -(int)rint(log2(d));
+    return k < -1000 ? -1000 : (k > 1000 ? 1000 : k);
+}
+
+// w[b][i] = FP32 rounding of g[b][i] 2^k_b (the scaling is exact in FP64).
+__global__ void k_scaled_to_f32(const double* __restrict__ g, long long Nx, int B, const double* __restrict__ delta,
+                                float* __restrict__ w) {
+    const long long total = (long long)B * Nx;
+    for (long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x; i < total;
+         i += (long long)gridDim.x * blockDim.x) {
+        const int b = (int)(i / Nx);
+        w[i] = __double2float_rn(ldexp(g[i], feat_scale_exp(delta[b])));
+    }
+}
+
 __global__ void k_spectrum_bins(const float* __restrict__ ghat, long long Nx, const unsigned char* __restrict__ bin,
                                 const float* __restrict__ inv_count, float coef_scale2, const double* __restrict__ delta,
                                 float T, float lg_nt, int in_dim, float* __restrict__ feats) {
@@ -42,7 +66,19 @@ __global__ void k_spectrum_bins(const float* __restrict__ ghat, long long Nx, co
     }
     __syncthreads();
     float* f = feats + (long long)b * in_dim;
-    for (int i = threadIdx.x; i < 64; i += blockDim.x) f[i] = log10f(acc[i] * inv_count[i] + 1e-30f);
+    // log10(mean square + 1e-30) of g_b's own coefficients from the scaled mean
+    // square m: a = log10 m - 2 k_b log10 2 (which may lie beyond FP64's range
+    // as a power of ten), then log10(10^a + 10^-30) = max + log10(1 + 10^-|a + 30|)
+    const int k = feat_scale_exp(delta[b]);
+    for (int i = threadIdx.x; i < 64; i += blockDim.x) {
+        const double m = (double)(acc[i] * inv_count[i]);
+        double v = -30.0;
+        if (m > 0.0) {
+            const double a = log10(m) - 2.0 * k * 0.30102999566398119521;
+            v = a >= -30.0 ? a + log10(1.0 + exp10(-30.0 - a)) : -30.0 + log10(1.0 + exp10(a + 30.0));
+        }
+        f[i] = (float)v;
+    }
     if (threadIdx.x == 0) {
         f[64] = (float)log10(delta[b]);
         f[65] = T;
@@ -597,8 +633,14 @@ int qbvm_features_run(qbvm_features_t* f, const double* g, const double* delta_h
     const long long n = f->n;
     if (cudaMemcpyAsync(f->delta, delta_host, sizeof(double) * B, cudaMemcpyHostToDevice, s) != cudaSuccess)
         return QBVM_ERR_CUDA;
-    // unnormalised DST-I along x then y of every instance, FP32
-    if (qbvm::launch_dst<float, double, 0>(g, f->work, f->n, f->lm, (long long)B * n, 1, f->tw, f->sn, s) != cudaSuccess)
+    // g_b 2^k_b in FP32, then the unnormalised DST-I along x then y of every instance
+    {
+        const long long total = (long long)B * f->Nx;
+        const unsigned blocks = (unsigned)std::min<long long>((total + MLP_THREADS - 1) / MLP_THREADS, 152LL * 16);
+        k_scaled_to_f32<<<blocks, MLP_THREADS, 0, s>>>(g, f->Nx, B, f->delta, f->work);
+        if (cudaGetLastError() != cudaSuccess) return QBVM_ERR_CUDA;
+    }
+    if (qbvm::launch_dst<float, float, 0>(f->work, f->work, f->n, f->lm, (long long)B * n, 1, f->tw, f->sn, s) != cudaSuccess)
         return QBVM_ERR_CUDA;
     if (qbvm::launch_dst<float, float, 0>(f->work, f->work, f->n, f->lm, (long long)B, n, f->tw, f->sn, s) != cudaSuccess)
         return QBVM_ERR_CUDA;

@@ -83,6 +83,29 @@ def test_features_match_direct_spectrum():
         np.testing.assert_allclose(got[b, 64:], [np.log10(delta[b]), grid.T, np.log2(grid.nt)], rtol=1e-6)
 
 
+@pytest.mark.parametrize("scale", [2.0 ** -1000, 2.0 ** -80, 2.0 ** 60, 2.0 ** 600], ids=["1e-301", "1e-24", "1e18", "4e180"])
+def test_features_at_any_data_scale(scale):
+    """The spectrum is taken of g scaled by the power of two nearest 1/delta, so
+    the FP32 DSTs and squares stay in range: the features of s g (with s delta)
+    are those of g with the bins moved by log10 s^2, down to the 1e-30 floor of
+    their definition."""
+    grid, z0, gd, delta = bi.alpha_training_batch(2, seed=8, M=64, nt=32)
+    fp = Q.Features(64, grid.T, grid.nt, 8)
+    out = []
+    for sc in (1.0, scale):
+        g = torch.as_tensor(gd.reshape(2, -1) * sc, dtype=torch.float64).cuda()
+        feats = torch.empty((2, LA.IN_DIM), dtype=torch.float32, device="cuda")
+        fp.run(g, np.asarray(delta) * sc, feats)
+        out.append(feats.cpu().numpy().astype(np.float64))
+    fp.close()
+    base, got = out
+    want = np.maximum(base[:, :64] + 2 * np.log10(scale), -30.0)
+    occupied = base[:, :64] > -29.0                      # bins holding modes (bin 0 holds none)
+    assert np.isfinite(got).all()
+    np.testing.assert_allclose(got[:, :64][occupied], want[occupied], rtol=0, atol=1e-3)
+    np.testing.assert_allclose(got[:, 64], np.log10(np.asarray(delta) * scale), rtol=1e-6)
+
+
 def test_training_beats_the_a_priori_rule(tmp_path):
     """Trained on 8192 method-labelled instances (2D 127^2 x 128), the network's
     alpha reconstructs 1024 held-out instances better than alpha = delta."""
