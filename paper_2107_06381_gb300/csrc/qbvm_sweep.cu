@@ -195,18 +195,23 @@ __device__ void spectral_tile(const SwInst& I, int tile, unsigned char* smem) {
             }
         }
         const R cna = R(I.cn[a]);
-        double dsum = 0.0, esum = 0.0;
+        // the thread's squares in its own precision (the FP32 scan's values are of
+        // the data scaled to about 1/delta), widened once for the block sum: FP64
+        // conversions and adds per term had kept the FP64 pipe a third busy in the
+        // FP32 scan
+        R ds = R(0), es = R(0);
 #pragma unroll
         for (int q = 0; q < MPT; ++q) {
             if (!valid[q]) continue;
             R y = cna * gh[q] * s[q];
             R dv = (R(1) + lam[q]) * y;
-            dsum += (double)dv * (double)dv;
+            ds = fma(dv, dv, ds);
             if (I.has_z0) {
                 R e = y - zh[q];
-                esum += (double)e * (double)e;
+                es = fma(e, e, es);
             }
         }
+        double dsum = (double)ds, esum = (double)es;
         dsum = block_sum_d(dsum, sh);
         esum = block_sum_d(esum, sh);
         if (threadIdx.x == 0) {
