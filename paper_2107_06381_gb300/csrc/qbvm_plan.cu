@@ -899,8 +899,9 @@ static int solve_fp64_host(qbvm_plan_t* p, const double* hin, double* hout, int 
     auto cst = [&](int c) { return (c & 1) ? as : s; };
     // chunks start at even levels: the x-DST packs rows in pairs from its first
     // row, so the pairs (and the rounding) are those of the whole-array pass.
-    // (Measured on 255^2 x 256: 8 equal chunks beat 16 equal ones and chunks
-    // growing 7/5 per step with the output ones shrinking.)
+    // (Measured on 255^2 x 256: 8 equal chunks beat 16 equal ones, chunks
+    // growing 7/5 per step with the output ones shrinking, and a one-level-pair
+    // first input and last output chunk with the rest split evenly.)
     const int nch = (int)std::max(1LL, std::min((long long)HOST_CHUNKS, nt / 2));
     auto lev0 = [&](int c) { return c == nch ? nt : ((nt * c / nch) & ~1LL); };
     double *din = p->stage_in, *dy = p->stage_out;
