@@ -647,7 +647,7 @@ def c4_leg(args, device, stream, with_oracle=True):
     relative noise log-uniform in [1e-4, 1e-2]) x 16 alphas, one persistent
     launch per run from a captured CUDA graph, launch shape autotuned.  The
     FP32 mode scans alpha in FP32 and sums y^0 at the picked alpha in
-    double-float; the FP64 mode does both in FP64.  With the oracle: the
+    double-float; the FP64 mode sums both in double-float (its DSTs in FP64).  With the oracle: the
     discrepancies of the four smallest instances at all 16 alphas, the pick,
     and y^0 at the pick, against the oracle's full solves."""
     import numpy as np
@@ -691,7 +691,8 @@ def c4_leg(args, device, stream, with_oracle=True):
             if with_oracle:
                 out[name].update(_c4_oracle_check(keep, al, disc, pick))
     out["fp32_scan"]["mode"] = "alpha scan in FP32, y0 at the pick summed in double-float"
-    out["fp64_scan"]["mode"] = "alpha scan and y0 at the pick in FP64"
+    out["fp64_scan"]["mode"] = ("alpha scan and y0 at the pick summed in double-float on the FP32 pipes "
+                                "(about 2^-46 per term), DSTs in FP64")
     return out
 
 

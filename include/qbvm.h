@@ -357,12 +357,18 @@ int qbvm_multi_destroy(qbvm_multi_t* multi);
  * graph and replayed by every qbvm_sweep_run; its launch shape (modes per
  * thread, CTAs per SM) is picked by qbvm_sweep_autotune.
  * Supported: dim 1 or 2; m a power of two in [4, 2048]; nt a power of two in
- * [2, 1024]; n_alpha in [1, 64].  precision: QBVM_FP64 (every stage in FP64)
- * or QBVM_FP32_REFINE (the alpha scan in FP32; the picked alpha's y^0 summed in
- * double-float, about 2^-44 per term, and the DSTs in FP64).  The FP64 scan
- * forms each 1/|d_{2m} + tau Lambda_l|^2 from an FP32 seed and one
- * third-order FP64 step x (1 + e + e^2), e = 1 - d x (a few units in the last
- * place; qbvm_selftest_newton_rcp).
+ * [2, 1024]; n_alpha in [1, 64].  precision:
+ *   QBVM_FP64: the DSTs in FP64; the spectral sums over the even frequencies
+ *     (of the scan and of y^0 at the pick) in double-float arithmetic on the
+ *     FP32 pipes, each term to about 2^-46 (discrepancies within 3e-12 of the
+ *     oracle's on 512 mixed instances), since this GPU's FP64 pipe issues
+ *     under 2 operations per SM per clock against 128 FP32 ones.  Instances
+ *     whose |Re d_{2m}|, |Im d_{2m}| or tau Lambda leave [2^-30, 2^30] sum in
+ *     FP64, each 1/|d_{2m} + tau Lambda_l|^2 from an FP32 seed and one
+ *     third-order FP64 step x (1 + e + e^2), e = 1 - d x (a few units in the
+ *     last place; qbvm_selftest_newton_rcp).
+ *   QBVM_FP32_REFINE: the alpha scan in FP32; the picked alpha's y^0 summed in
+ *     double-float, about 2^-44 per term; the DSTs in FP64.
  * The sweep holds device copies of its tables; g, z0 and y0 are caller-owned
  * device arrays that must stay valid while the sweep is used. */
 typedef struct qbvm_sweep_instance {

@@ -16,7 +16,9 @@
 //      ||y^N - g|| <= tau_dp * delta (else the smallest discrepancy);
 //   D-F  y^0 at the picked alpha in FP64: the spectral values, then the
 //      inverse DST along y and x.
-// Stage B runs in the sweep precision (FP64 or FP32); A and D-F in FP64.
+// Stage B runs in FP32 for the FP32 sweep; for the FP64 sweep its sums, and
+// those of stage D, run in double-float on the FP32 pipes (FP64 where the
+// instance's tables leave FP32's comfortable range); A and E-F in FP64.
 //
 // Work items are queued in topological order and claimed with an atomic
 // ticket; an item whose inputs come from earlier stages waits on per-instance
@@ -48,6 +50,8 @@ struct SwInst {
     long long Nx;
     int tiles_gx, tiles_gy, tiles_spec, tiles_fin, tiles_iy, tiles_ix;
     int has_z0, has_y0;
+    int df_sums;                 // FP64 sweep: the spectral sums of stages B and D in
+                                 // double-float (tables inside [2^-30, 2^30]), else FP64
     double delta, tau_dp, tau, wnorm, zscale;
     double sscale, sinv;         // 2^-floor(log2 delta) and its inverse: the scan runs on
                                  // g, z0 scaled so that delta ~ 1 (exact; any data scale)
@@ -221,6 +225,108 @@ __device__ void spectral_tile(const SwInst& I, int tile, unsigned char* smem) {
     }
 }
 
+// Stage B of the FP64 sweep in double-float on the FP32 pipes: on GB300 the
+// FP64 pipe issues under two operations per SM per clock against 128 FP32
+// ones, so the six FP64 operations per term of spectral_tile<double> cost as
+// much as ~450 FP32 ones.  Per term Re 1/z = z_r / (z_r^2 + z_i^2) with
+// z = d_{2m} + tau Lambda_l:
+//   z_r  two-sum of the high words, the low words added, renormalised (its
+//        absolute error ~2^-48 (|Re d| + tau Lambda), as FP64's rounding of the
+//        same sum is 2^-53 of it);
+//   den  z_r^2 + z_i^2, the products' errors recovered by fused multiply-adds
+//        (z_i^2 once per frequency for all the thread's modes);
+//   q1   z_r.hi / den.hi through the approximate FP32 reciprocal r;
+//   c    the remainder z_r - den q1 -- about 2^-22 |z_r|, which fused
+//        multiply-adds give to about 2^-46 |z_r| -- times r;
+//   sum  q1 two-summed into the high word, its rounding error and c added to
+//        the low word.
+// About 2^-46 relative per term (6e-15 in a CPU emulation over the sweep's
+// ranges), the sum to about 2e-14.  The squares of the discrepancy and error
+// sums are FP64, as in spectral_tile<double>.
+template <int MPT>
+__device__ void spectral_tile_df(const SwInst& I, int tile, unsigned char* smem) {
+    __shared__ double sh[32];
+    float4* sd = reinterpret_cast<float4*>(smem);
+    qbvm::dfloat lam[MPT];
+    double w[MPT], gh[MPT], zh[MPT];
+    bool valid[MPT];
+#pragma unroll
+    for (int q = 0; q < MPT; ++q) {
+        const long long l = (long long)tile * SW_THREADS * MPT + q * SW_THREADS + threadIdx.x;
+        valid[q] = l < I.Nx;
+        lam[q] = {0.f, 0.f};
+        w[q] = gh[q] = zh[q] = 0.0;
+        if (valid[q]) {
+            const int lx = (int)(l % I.nx), ly = (int)(l / I.nx);
+            const double lt = __ldcg(I.lamx + lx) + (I.dim == 2 ? __ldcg(I.lamy + ly) : 0.0);
+            lam[q] = qbvm::df_from_double(lt);
+            gh[q] = __ldcg(I.ghat + l) * I.sscale;
+            w[q] = (1.0 + lt) * gh[q];
+            if (I.has_z0) zh[q] = __ldcg(I.zhat + l) * I.zscale * I.sscale;
+        }
+    }
+    for (int a = 0; a < I.n_alpha; ++a) {
+        __syncthreads();
+        for (int m = threadIdx.x; m < I.H; m += blockDim.x) sd[m] = I.dtabdf[(long long)a * I.H + m];
+        __syncthreads();
+        float shi[MPT], slo[MPT];
+#pragma unroll
+        for (int q = 0; q < MPT; ++q) shi[q] = slo[q] = 0.f;
+        for (int m0 = 0; m0 < I.H; m0 += 4) {
+            const int m1 = min(m0 + 4, I.H);
+            for (int m = m0; m < m1; ++m) {
+                const float4 d = sd[m];                         // (Re.hi, Re.lo, Im.hi, Im.lo)
+                const float ip = d.z * d.z;
+                const float ie = fmaf(d.z + d.z, d.w, fmaf(d.z, d.z, -ip));
+#pragma unroll
+                for (int q = 0; q < MPT; ++q) {
+                    qbvm::dfloat zr = qbvm::df_two_sum(d.x, lam[q].hi);
+                    zr = qbvm::df_fast_two_sum(zr.hi, zr.lo + (d.y + lam[q].lo));
+                    const float rp = zr.hi * zr.hi;
+                    const float re = fmaf(zr.hi + zr.hi, zr.lo, fmaf(zr.hi, zr.hi, -rp));
+                    const qbvm::dfloat den = qbvm::df_two_sum(rp, ip);
+                    const float dlo = den.lo + (re + ie);
+                    float r;
+                    asm("rcp.approx.ftz.f32 %0, %1;" : "=f"(r) : "f"(den.hi));
+                    const float q1 = zr.hi * r;
+                    const float t = fmaf(-dlo, q1, fmaf(-den.hi, q1, zr.hi) + zr.lo);
+                    const qbvm::dfloat u = qbvm::df_two_sum(shi[q], q1);
+                    shi[q] = u.hi;
+                    slo[q] += fmaf(t, r, u.lo);
+                }
+            }
+            // fold the low word into the high one every four terms: a low word
+            // left to grow over all H terms rounds at its own, growing size
+            // (1e-13 relative at H = 256 against 2e-14 folded)
+#pragma unroll
+            for (int q = 0; q < MPT; ++q) {
+                const qbvm::dfloat f = qbvm::df_fast_two_sum(shi[q], slo[q]);
+                shi[q] = f.hi;
+                slo[q] = f.lo;
+            }
+        }
+        const double cna = I.cn[a];
+        double ds = 0.0, es = 0.0;
+#pragma unroll
+        for (int q = 0; q < MPT; ++q) {
+            if (!valid[q]) continue;
+            const double sq = qbvm::qbvm_join_df_dadd(shi[q], slo[q]);
+            const double dv = w[q] * sq;                        // (1 + tau Lambda) yhat / cna
+            ds = fma(dv, dv, ds);
+            if (I.has_z0) {
+                const double e = fma(cna * gh[q], sq, -zh[q]);
+                es = fma(e, e, es);
+            }
+        }
+        double dsum = block_sum_d(cna * cna * ds, sh);
+        double esum = block_sum_d(es, sh);
+        if (threadIdx.x == 0) {
+            atomicAdd(I.stats + 2 * a, dsum);
+            if (I.has_z0) atomicAdd(I.stats + 2 * a + 1, esum);
+        }
+    }
+}
+
 // Stage C: discrepancy principle on one instance (single thread).
 __device__ void pick_alpha(const SwInst& I) {
     if (threadIdx.x != 0) return;
@@ -300,11 +406,17 @@ __device__ __noinline__ void dst_stage(const double* in, double* out, int n, int
 }
 template <typename R, int MPT>
 __device__ __noinline__ void spectral_stage(const SwInst& I, int tile, unsigned char* smem) {
-    spectral_tile<R, MPT>(I, tile, smem);
+    if (std::is_same<R, double>::value && I.df_sums)
+        spectral_tile_df<MPT>(I, tile, smem);
+    else
+        spectral_tile<R, MPT>(I, tile, smem);
 }
 template <typename R>
 __device__ __noinline__ void final_stage(const SwInst& I, int tile) {
-    final_tile<R>(I, tile);
+    if (std::is_same<R, double>::value && I.df_sums)
+        final_tile<float>(I, tile);              // y^0 summed in double-float
+    else
+        final_tile<R>(I, tile);
 }
 
 struct SwRun {
@@ -744,6 +856,21 @@ int qbvm_sweep_plan(const qbvm_sweep_desc* d, qbvm_sweep_t** out) {
             // 2 cnorm with cnorm = -omega * prod(2/M) / nt (the delta right-hand side)
             cn[a] = 2.0 * (-omega) * I.zscale / in.nt;
             coef[a] = in.form == QBVM_FORM_PQ ? alpha : alpha / I.tau;
+        }
+        {
+            // the FP64 sweep sums in double-float where |Re d|, |Im d| and
+            // tau Lambda stay inside [2^-30, 2^30] (|Im d| and tau Lambda away
+            // from zero): squares, products and low words then stay normal FP32
+            const double lo = std::ldexp(1.0, -30), hi = std::ldexp(1.0, 30);
+            double lmin = *std::min_element(lx.begin(), lx.end()), lmax = *std::max_element(lx.begin(), lx.end());
+            if (in.dim == 2) {
+                lmin += *std::min_element(ly.begin(), ly.end());
+                lmax += *std::max_element(ly.begin(), ly.end());
+            }
+            bool ok = p->precision == QBVM_FP64 && lmin >= lo && lmax <= hi;
+            for (const double2& v : dtab)
+                ok = ok && std::fabs(v.x) <= hi && std::fabs(v.y) >= lo && std::fabs(v.y) <= hi;
+            I.df_sums = ok ? 1 : 0;
         }
         Offs& o = offs[i];
         o.lamx = put(lx.data(), lx.size() * sizeof(double));

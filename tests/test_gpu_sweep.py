@@ -102,6 +102,30 @@ def test_sweep_matches_oracle(precision, tol):
         sw.close()
 
 
+def test_fp64_sweep_double_float_and_fp64_instances_in_one_launch():
+    """The FP64 sweep sums in double-float where the instance's tables (Re d,
+    Im d, tau Lambda) lie inside [2^-30, 2^30] and in FP64 elsewhere: here
+    T = 1e-12 puts tau Lambda near 1e-10, so that instance takes the FP64 sums
+    inside the same persistent launch as two double-float ones.  All three at
+    the FP64 sweep's 1e-9 against the oracle."""
+    problems = _problems()[:2]
+    grid = bi.Grid(1, (32,), 1.0, 1e-12, 16)
+    rng = np.random.default_rng(190)
+    z0 = bi.sine_field(grid, [(1,), (2,), (5,)], rng.uniform(0.3, 1.0, 3))
+    gd, delta = bi.add_noise_gaussian(grid, bi.forward_discrete(grid, z0), 1e-3, rng)
+    assert grid.tau * 4.0 * grid.M[0] ** 2 < 2.0 ** -30
+    problems.append((grid, Q.FORM_PQ, z0, gd, delta))
+    sw, (alphas, disc, err, pick), y0s, _ = _run_sweep(problems, Q.FP64)
+    try:
+        for i, (grid, form, z0, gd, delta) in enumerate(problems):
+            odisc, oerr, opick, oys = _oracle_sweep(grid, form, z0, gd, delta, alphas[i])
+            np.testing.assert_allclose(disc[i], odisc, rtol=1e-9)
+            np.testing.assert_allclose(err[i], oerr, rtol=1e-9)
+            assert O.rel_l2(y0s[i], oys[int(pick[i, 0])].ravel()) <= 1e-10
+    finally:
+        sw.close()
+
+
 def test_sweep_graph_replay_and_autotune_are_consistent():
     problems = _problems()
     sw, (alphas, disc, err, pick), y0s, dev = _run_sweep(problems, Q.FP32_REFINE)
