@@ -228,9 +228,10 @@ def test_n0_only_and_host_pointers(grid, rhs_kind):
 @pytest.mark.parametrize("grid", [bi.Grid(2, (64, 32), 1.0, 0.1, 50), bi.Grid(3, (16, 8, 8), 1.0, 0.1, 64),
                                   bi.Grid(2, (256, 256), 1.0, 0.1, 32)],
                          ids=["2d-nt50", "3d-nt64", "2d-255sq-nt32"])
-def test_host_pointers_chunked_pinned(grid):
-    """Pinned host buffers: the level chunks' copies overlap DSTs that alternate
-    between two compute streams; the result is bitwise the device-pointer solve."""
+def test_host_pointers_pinned_and_pageable(grid):
+    """Pinned, pageable and mixed host buffers: the level chunks' copies overlap
+    DSTs that alternate between two compute streams; every result is bitwise
+    the device-pointer solve."""
     F = bi.random_general_rhs(grid, seed=14)
     dev = gpu_solve(grid, Q.FORM_PM, 1e-3, F, Q.RHS_GENERAL)
     dev0 = gpu_solve(grid, Q.FORM_PM, 1e-3, F, Q.RHS_GENERAL, n0_only=True)
@@ -243,6 +244,14 @@ def test_host_pointers_chunked_pinned(grid):
         h0 = torch.full((grid.Nx,), float("nan"), dtype=torch.float64).pin_memory()
         plan.solve(hin, h0, n0_only=True)
         np.testing.assert_array_equal(h0.numpy().reshape((1,) + grid.shape), dev0)
+        pin = np.ascontiguousarray(F.ravel())
+        for _ in range(2):
+            pout = np.full(grid.unknowns, np.nan)
+            plan.solve(pin, pout)                            # pageable: chunked copies
+            np.testing.assert_array_equal(pout.reshape(grid.full_shape), dev)
+        pout = np.full(grid.unknowns, np.nan)
+        plan.solve(hin, pout)                                # pinned in, pageable out
+        np.testing.assert_array_equal(pout.reshape(grid.full_shape), dev)
 
 
 def test_inplace_general_rhs():
