@@ -360,9 +360,11 @@ int qbvm_multi_destroy(qbvm_multi_t* multi);
  * [2, 1024]; n_alpha in [1, 64].  precision:
  *   QBVM_FP64: the DSTs in FP64; the spectral sums over the even frequencies
  *     (of the scan and of y^0 at the pick) in double-float arithmetic on the
- *     FP32 pipes, each term to about 2^-46 (discrepancies within 3e-12 of the
- *     oracle's on 512 mixed instances), since this GPU's FP64 pipe issues
- *     under 2 operations per SM per clock against 128 FP32 ones.  Instances
+ *     FP32 pipes, since this GPU's FP64 pipe issues under 2 operations per
+ *     SM per clock against 128 FP32 ones: a mode's sum to about 6e-14 of the
+ *     sum of its terms' magnitudes (FP64 summation: about 1e-16), so sums
+ *     whose terms cancel keep fewer digits than in FP64; the discrepancies
+ *     were within 3e-12 of the oracle's on 512 mixed instances.  Instances
  *     whose |Re d_{2m}|, |Im d_{2m}| or tau Lambda leave [2^-30, 2^30] sum in
  *     FP64, each 1/|d_{2m} + tau Lambda_l|^2 from an FP32 seed and one
  *     third-order FP64 step x (1 + e + e^2), e = 1 - d x (a few units in the

@@ -33,6 +33,7 @@
 #include <vector>
 
 #include "qbvm.h"
+#include "qbvm_dfsum.cuh"
 #include "qbvm_dst.cuh"
 #include "qbvm_internal.h"
 
@@ -228,21 +229,11 @@ __device__ void spectral_tile(const SwInst& I, int tile, unsigned char* smem) {
 // Stage B of the FP64 sweep in double-float on the FP32 pipes: on GB300 the
 // FP64 pipe issues under two operations per SM per clock against 128 FP32
 // ones, so the six FP64 operations per term of spectral_tile<double> cost as
-// much as ~450 FP32 ones.  Per term Re 1/z = z_r / (z_r^2 + z_i^2) with
-// z = d_{2m} + tau Lambda_l:
-//   z_r  two-sum of the high words, the low words added, renormalised (its
-//        absolute error ~2^-48 (|Re d| + tau Lambda), as FP64's rounding of the
-//        same sum is 2^-53 of it);
-//   den  z_r^2 + z_i^2, the products' errors recovered by fused multiply-adds
-//        (z_i^2 once per frequency for all the thread's modes);
-//   q1   z_r.hi / den.hi through the approximate FP32 reciprocal r;
-//   c    the remainder z_r - den q1 -- about 2^-22 |z_r|, which fused
-//        multiply-adds give to about 2^-46 |z_r| -- times r;
-//   sum  q1 two-summed into the high word, its rounding error and c added to
-//        the low word.
-// About 2^-46 relative per term (6e-15 in a CPU emulation over the sweep's
-// ranges), the sum to about 2e-14.  The squares of the discrepancy and error
-// sums are FP64, as in spectral_tile<double>.
+// much as ~450 FP32 ones.  Each term Re 1/(d_{2m} + tau Lambda_l) is
+// df_scan_term (qbvm_dfsum.cuh: about 35 FP32 operations and one approximate
+// reciprocal, about 2^-44 of the term's scale), the thread's accumulators folded every
+// four frequencies.  The squares of the discrepancy and error sums are FP64,
+// as in spectral_tile<double>.
 template <int MPT>
 __device__ void spectral_tile_df(const SwInst& I, int tile, unsigned char* smem) {
     __shared__ double sh[32];
@@ -276,34 +267,14 @@ __device__ void spectral_tile_df(const SwInst& I, int tile, unsigned char* smem)
             const int m1 = min(m0 + 4, I.H);
             for (int m = m0; m < m1; ++m) {
                 const float4 d = sd[m];                         // (Re.hi, Re.lo, Im.hi, Im.lo)
-                const float ip = d.z * d.z;
-                const float ie = fmaf(d.z + d.z, d.w, fmaf(d.z, d.z, -ip));
+                const qbvm::DfSq im2 = qbvm::df_scan_im2(d.z, d.w);
 #pragma unroll
-                for (int q = 0; q < MPT; ++q) {
-                    qbvm::dfloat zr = qbvm::df_two_sum(d.x, lam[q].hi);
-                    zr = qbvm::df_fast_two_sum(zr.hi, zr.lo + (d.y + lam[q].lo));
-                    const float rp = zr.hi * zr.hi;
-                    const float re = fmaf(zr.hi + zr.hi, zr.lo, fmaf(zr.hi, zr.hi, -rp));
-                    const qbvm::dfloat den = qbvm::df_two_sum(rp, ip);
-                    const float dlo = den.lo + (re + ie);
-                    float r;
-                    asm("rcp.approx.ftz.f32 %0, %1;" : "=f"(r) : "f"(den.hi));
-                    const float q1 = zr.hi * r;
-                    const float t = fmaf(-dlo, q1, fmaf(-den.hi, q1, zr.hi) + zr.lo);
-                    const qbvm::dfloat u = qbvm::df_two_sum(shi[q], q1);
-                    shi[q] = u.hi;
-                    slo[q] += fmaf(t, r, u.lo);
-                }
+                for (int q = 0; q < MPT; ++q) qbvm::df_scan_term(d.x, d.y, im2, lam[q].hi, lam[q].lo, shi[q], slo[q]);
             }
             // fold the low word into the high one every four terms: a low word
             // left to grow over all H terms rounds at its own, growing size
-            // (1e-13 relative at H = 256 against 2e-14 folded)
 #pragma unroll
-            for (int q = 0; q < MPT; ++q) {
-                const qbvm::dfloat f = qbvm::df_fast_two_sum(shi[q], slo[q]);
-                shi[q] = f.hi;
-                slo[q] = f.lo;
-            }
+            for (int q = 0; q < MPT; ++q) qbvm::df_scan_fold(shi[q], slo[q]);
         }
         const double cna = I.cn[a];
         double ds = 0.0, es = 0.0;
