@@ -18,7 +18,7 @@ import os
 import tempfile
 
 
-_SWEEP_SOURCES = ("qbvm_sweep.cu", "qbvm_dst.cuh", "qbvm_fft.cuh", "qbvm_internal.h")
+_SWEEP_SOURCES = ("qbvm_sweep.cu", "qbvm_dfsum.cuh", "qbvm_dst.cuh", "qbvm_fft.cuh", "qbvm_internal.h")
 
 
 def build_id() -> str:

@@ -148,6 +148,28 @@ def test_sweep_graph_replay_and_autotune_are_consistent():
         sw.close()
 
 
+def test_fp64_sweep_every_launch_shape_agrees():
+    """The FP64 sweep's double-float scan at 1, 2 and 4 modes per thread and 1
+    or 2 CTAs per SM: the same picks, discrepancies to 1e-12 (only the order of
+    the block sums differs) and the same y^0 bit for bit (its stage does not
+    depend on the shape)."""
+    problems = _problems()
+    sw, (alphas, disc, err, pick), y0s, dev = _run_sweep(problems, Q.FP64)
+    try:
+        for mpt in (1, 2, 4):
+            for ctas in (1, 2):
+                sw.set_config(mpt, ctas)
+                sw.run()
+                a2, d2, e2, p2 = sw.read()
+                np.testing.assert_array_equal(p2, pick)
+                np.testing.assert_allclose(d2, disc, rtol=1e-12)
+                np.testing.assert_allclose(e2, err, rtol=1e-12)
+                for d, v in zip(dev, y0s):
+                    np.testing.assert_array_equal(d[2].cpu().numpy(), v)
+    finally:
+        sw.close()
+
+
 def test_c4_style_batch_sampled():
     """A slice of the uneven 512-instance batch: sizes from the batch recipe,
     16 alphas; every instance's discrepancies checked against the oracle."""
