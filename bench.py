@@ -63,7 +63,7 @@ def traffic_source_hash() -> str:
     return h.hexdigest()[:16]
 
 
-def survey_flops(name, grid):
+def flop_budget(name, grid):
     """Algorithmic FP64 flops of one launch by the per-element counts of the
     path's flop budget: a DST-I pass ~22 flops per element; the time solve
     2 x 5 log2(nt) (FFT + inverse FFT) + ~11 (Step (b) divide) + ~10 (omega
@@ -277,7 +277,7 @@ def roofline(kstats, grid, rhs, value, device, stream):
     bound "alu": the FP64 pipe, against the DFMA rate measured in this run;
     `frac` counts the kernel's own FP64 instructions (DADD, DMUL, DFMA one
     each, kernel_model).  Beside it: the same launch by the path's flop budget
-    (survey_flops, over twice the FMA rate), and the HBM fraction of its
+    (flop_budget, over twice the FMA rate), and the HBM fraction of its
     algorithmic bytes over the measured copy peak."""
     hbm_peak, hbm_src = _peaks()
     dname, (dl, dms) = max(kstats.items(), key=lambda kv: kv[1][1])
@@ -294,7 +294,7 @@ def roofline(kstats, grid, rhs, value, device, stream):
     t_alu = ops / fma_rate
     ach_ops = ops / avg_s / 1e12
     hbm_ach = byts / avg_s / 1e9
-    fl = survey_flops(dname, grid)
+    fl = flop_budget(dname, grid)
     roof = {"bound": "alu" if t_alu > t_hbm else "hbm", "kernel": dname,
             "launches_traced": dl, "avg_ms": round(dms / dl, 4)}
     if t_alu > t_hbm:
@@ -311,10 +311,10 @@ def roofline(kstats, grid, rhs, value, device, stream):
         "fp64_peak_derived_tops": round(FP64_PEAK_DERIVED_TOPS, 4),
         "fractions": {
             "fp64_ops_of_measured": round(ach_ops / peak_tops, 4),
-            "survey_flops_of_measured": round(fl / avg_s / (2 * fma_rate), 4) if fl else None,
+            "flop_budget_of_measured": round(fl / avg_s / (2 * fma_rate), 4) if fl else None,
             "hbm_algorithmic_of_measured": round(hbm_ach / hbm_peak, 4),
         },
-        "kernel_fp64_ops_per_launch": ops, "survey_flops_per_launch": fl,
+        "kernel_fp64_ops_per_launch": ops, "flop_budget_per_launch": fl,
         "algorithmic_bytes_per_launch": byts,
         "hbm_achieved_gbs": round(hbm_ach, 1), "hbm_peak_gbs": hbm_peak, "hbm_peak_source": hbm_src,
         "traffic": traffic,

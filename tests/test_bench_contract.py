@@ -56,8 +56,8 @@ def test_kernel_model_of_the_headline_passes():
     byts_d, _ = bench.kernel_model("time_solve", grid, "delta")
     assert byts_d == byts - 8 * (nt - 1) * Nx            # the delta right-hand side reads one level
     assert bench.kernel_model("residual_df", grid, "general") == (None, None)
-    assert bench.survey_flops("dst_x", grid) == pytest.approx(22 * nt * Nx)
-    assert bench.survey_flops("time_solve", grid) == pytest.approx((10 * math.log2(nt) + 21) * nt * Nx)
+    assert bench.flop_budget("dst_x", grid) == pytest.approx(22 * nt * Nx)
+    assert bench.flop_budget("time_solve", grid) == pytest.approx((10 * math.log2(nt) + 21) * nt * Nx)
 
 
 def test_recorded_traffic_matches_the_tile_sources():
