@@ -365,10 +365,10 @@ int qbvm_multi_destroy(qbvm_multi_t* multi);
  *     sum of its terms' magnitudes (FP64 summation: about 1e-16), so sums
  *     whose terms cancel keep fewer digits than in FP64; the discrepancies
  *     were within 3e-12 of the oracle's on 512 mixed instances.  Instances
- *     whose |Re d_{2m}|, |Im d_{2m}| or tau Lambda leave [2^-30, 2^30] sum in
- *     FP64, each 1/|d_{2m} + tau Lambda_l|^2 from an FP32 seed and one
- *     third-order FP64 step x (1 + e + e^2), e = 1 - d x (a few units in the
- *     last place; qbvm_selftest_newton_rcp).
+ *     with |Re d_{2m}| above 2^30, or |Im d_{2m}| or tau Lambda outside
+ *     [2^-30, 2^30], sum in FP64, each 1/|d_{2m} + tau Lambda_l|^2 from an
+ *     FP32 seed and one third-order FP64 step x (1 + e + e^2), e = 1 - d x
+ *     (a few units in the last place; qbvm_selftest_newton_rcp).
  *   QBVM_FP32_REFINE: the alpha scan in FP32; the picked alpha's y^0 summed in
  *     double-float, about 2^-44 per term; the DSTs in FP64.
  * The sweep holds device copies of its tables; g, z0 and y0 are caller-owned
